@@ -1,0 +1,94 @@
+/*
+ * gpz_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of the GPZ particle
+ * compressor (Li et al., "GPZ: GPU-Accelerated Lossy Compressor for Particle
+ * Data", arXiv 2508.10305).  It exists to check the CUDA library bit for bit.
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load it; the product path never does.  It shares no code, header,
+ * table or constant with the CUDA library: everything below is defined here
+ * again, from the paper and from the stream-format readings documented in
+ * the repository's design notes.
+ *
+ * All entry points are synchronous, take host pointers, allocate only host
+ * memory, and return one of the GPZO_* status codes.
+ */
+#ifndef GPZ_ORACLE_H
+#define GPZ_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GPZO_OK = 0,
+    GPZO_ERR_INVALID_ARG = 1,
+    GPZO_ERR_CAPACITY = 2,
+    GPZO_ERR_CORRUPT = 3,
+    GPZO_ERR_UNSUPPORTED = 7
+};
+
+/* Per-field quantisation constants (Section 4.1 and Section 5.1):
+ * eb = error bound, s = the quantisation step (2*eb less 1/64, see the
+ * source), inv = 1/s rounded once to fp32 (the "precomputed reciprocal"),
+ * ebchk = the fp32 threshold used by the per-value verification. */
+typedef struct {
+    float eb;
+    float s;
+    float inv;
+    float ebchk;
+} gpzo_field_params;
+
+/* Finalise the constants of one field from an absolute bound eb (> 0). */
+int gpzo_params_abs(double eb, gpzo_field_params* out);
+
+/* Relative bound: eb = rel * (max - min) over the non-NaN values of x[0..n). */
+int gpzo_params_rel(double rel, const float* x, uint64_t n, gpzo_field_params* out);
+
+/* Worst-case stream size in bytes for n particles of n_fields fields. */
+uint64_t gpzo_bound_size(uint64_t n, int n_fields);
+
+/* Encode one block of n_b (1..1024) particles.  fields[f] points at the
+ * block's n_b values of field f.  Writes the block's words to out
+ * (capacity cap_words), their count to *nwords, and, if perm_b is not NULL,
+ * the block-local permutation (perm_b[j] = input index of output slot j). */
+int gpzo_encode_block(const float* const* fields, int n_fields, int n_b, int seg_bits,
+                      const gpzo_field_params* params, uint32_t* out, uint32_t cap_words,
+                      uint32_t* nwords, uint32_t* perm_b);
+
+/* The intermediate results of encoding one block, exposed so that tests can
+ * pin each step on its own.  Arrays are sized by the caller:
+ *   mins[F], bits[F], q[F*n_b] (field-major), seg_id[F*n_b], seg_off[F*n_b],
+ *   key[n_b], perm_b[n_b], uniq[n_b], counts[n_b].
+ * *is_raw is 1 when the block falls back to raw storage; in that case only
+ * the fields computed before the fallback are meaningful.  *n_unique = U. */
+int gpzo_block_stages(const float* const* fields, int n_fields, int n_b, int seg_bits,
+                      const gpzo_field_params* params, int* is_raw, float* mins,
+                      uint32_t* bits, uint32_t* q, uint32_t* seg_id, uint32_t* seg_off,
+                      uint32_t* key, uint32_t* perm_b, uint32_t* n_unique, uint32_t* uniq,
+                      uint32_t* counts);
+
+/* Fixed-length code of len values at a uniform width w (0..32): value j
+ * occupies stream bits [j*w, j*w+w), least significant bit first, stream bit
+ * t being bit (t mod 32) of word t/32.  Writes ceil(len*w/32) words. */
+uint32_t gpzo_pack_fixed(const uint32_t* values, uint32_t len, uint32_t w, uint32_t* out);
+void gpzo_unpack_fixed(const uint32_t* words, uint32_t len, uint32_t w, uint32_t* values);
+
+/* Whole-array compression.  fields[f] -> n values (host).  mode 0 = absolute
+ * bound, 1 = relative bound; eb[f] per field.  perm may be NULL, else it
+ * receives n entries: perm[i] = input index of output particle i. */
+int gpzo_compress(const float* const* fields, uint64_t n, int n_fields, int mode,
+                  const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
+                  uint64_t* out_size, uint32_t* perm);
+
+/* Inverse.  Writes n values per field, in the stream's (block-sorted) order. */
+int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int n_fields,
+                    uint64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPZ_ORACLE_H */

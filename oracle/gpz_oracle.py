@@ -1,0 +1,202 @@
+"""ctypes wrapper of the CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy marshalling around oracle/libgpz_oracle.so (built by
+oracle/build.py).  Only tests/, the smoke check and the benchmark's CPU
+baseline import this module; the product path must never reach it.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_UNSUPPORTED = 0, 1, 2, 3, 7
+BLOCK = 1024
+
+
+class FieldParams(C.Structure):
+    _fields_ = [("eb", C.c_float), ("s", C.c_float), ("inv", C.c_float), ("ebchk", C.c_float)]
+
+    def as_tuple(self):
+        return (self.eb, self.s, self.inv, self.ebchk)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER
+        u32p, f32p, u8p = P(C.c_uint32), P(C.c_float), P(C.c_uint8)
+        L.gpzo_params_abs.argtypes = [C.c_double, P(FieldParams)]
+        L.gpzo_params_rel.argtypes = [C.c_double, f32p, C.c_uint64, P(FieldParams)]
+        L.gpzo_bound_size.argtypes = [C.c_uint64, C.c_int]
+        L.gpzo_bound_size.restype = C.c_uint64
+        L.gpzo_encode_block.argtypes = [P(f32p), C.c_int, C.c_int, C.c_int, P(FieldParams), u32p,
+                                        C.c_uint32, u32p, u32p]
+        L.gpzo_block_stages.argtypes = [P(f32p), C.c_int, C.c_int, C.c_int, P(FieldParams),
+                                        P(C.c_int), f32p, u32p, u32p, u32p, u32p, u32p, u32p, u32p,
+                                        u32p, u32p]
+        L.gpzo_pack_fixed.argtypes = [u32p, C.c_uint32, C.c_uint32, u32p]
+        L.gpzo_pack_fixed.restype = C.c_uint32
+        L.gpzo_unpack_fixed.argtypes = [u32p, C.c_uint32, C.c_uint32, u32p]
+        L.gpzo_compress.argtypes = [P(f32p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
+                                    u8p, C.c_uint64, P(C.c_uint64), u32p]
+        L.gpzo_decompress.argtypes = [u8p, C.c_uint64, P(f32p), C.c_int, C.c_uint64]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _field_ptrs(fields):
+    """fields: 2-D float32 C-contiguous array [F, n] -> (F-array of float*, keepalive)."""
+    arr = (C.POINTER(C.c_float) * fields.shape[0])()
+    for f in range(fields.shape[0]):
+        arr[f] = _ptr(fields[f], C.c_float)
+    return arr
+
+
+def _as_fields(x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if x.ndim == 1:
+        x = x[None, :]
+    return x
+
+
+def params_abs(eb):
+    p = FieldParams()
+    rc = lib().gpzo_params_abs(float(eb), C.byref(p))
+    if rc != OK:
+        raise ValueError("gpzo_params_abs failed: %d" % rc)
+    return p
+
+
+def params_rel(rel, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    p = FieldParams()
+    rc = lib().gpzo_params_rel(float(rel), _ptr(x, C.c_float), x.size, C.byref(p))
+    if rc != OK:
+        raise ValueError("gpzo_params_rel failed: %d" % rc)
+    return p
+
+
+def bound_size(n, n_fields):
+    return int(lib().gpzo_bound_size(n, n_fields))
+
+
+def _params_array(params):
+    arr = (FieldParams * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p
+    return arr
+
+
+def encode_block(fields, seg_bits, params, want_perm=True):
+    """Encode one block: fields [F, n_b] float32; params: list of FieldParams."""
+    x = _as_fields(fields)
+    F, n_b = x.shape
+    cap = 1 + F * n_b + 64
+    out = np.zeros(cap, dtype=np.uint32)
+    nw = C.c_uint32(0)
+    perm = np.zeros(n_b, dtype=np.uint32) if want_perm else None
+    rc = lib().gpzo_encode_block(_field_ptrs(x), F, n_b, seg_bits, _params_array(params),
+                                 _ptr(out, C.c_uint32), cap, C.byref(nw),
+                                 _ptr(perm, C.c_uint32) if want_perm else None)
+    if rc != OK:
+        raise ValueError("gpzo_encode_block failed: %d" % rc)
+    return out[:nw.value].copy(), perm
+
+
+def block_stages(fields, seg_bits, params):
+    """All intermediate results of one block, as a dict of numpy arrays."""
+    x = _as_fields(fields)
+    F, n_b = x.shape
+    is_raw = C.c_int(0)
+    mins = np.zeros(F, np.float32)
+    bits = np.zeros(F, np.uint32)
+    q = np.zeros((F, n_b), np.uint32)
+    seg_id = np.zeros((F, n_b), np.uint32)
+    seg_off = np.zeros((F, n_b), np.uint32)
+    key = np.zeros(n_b, np.uint32)
+    perm = np.zeros(n_b, np.uint32)
+    nu = C.c_uint32(0)
+    uniq = np.zeros(n_b, np.uint32)
+    counts = np.zeros(n_b, np.uint32)
+    u32 = C.c_uint32
+    rc = lib().gpzo_block_stages(_field_ptrs(x), F, n_b, seg_bits, _params_array(params),
+                                 C.byref(is_raw), _ptr(mins, C.c_float), _ptr(bits, u32),
+                                 _ptr(q, u32), _ptr(seg_id, u32), _ptr(seg_off, u32),
+                                 _ptr(key, u32), _ptr(perm, u32), C.byref(nu), _ptr(uniq, u32),
+                                 _ptr(counts, u32))
+    if rc != OK:
+        raise ValueError("gpzo_block_stages failed: %d" % rc)
+    U = nu.value
+    return dict(raw=bool(is_raw.value), mins=mins, bits=bits, q=q, seg_id=seg_id,
+                seg_off=seg_off, key=key, perm=perm, uniq=uniq[:U].copy(),
+                counts=counts[:U].copy())
+
+
+def pack_fixed(values, w):
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    out = np.zeros((v.size * w + 31) // 32 + 1, dtype=np.uint32)
+    nw = lib().gpzo_pack_fixed(_ptr(v, C.c_uint32), v.size, w, _ptr(out, C.c_uint32))
+    return out[:nw].copy()
+
+
+def unpack_fixed(words, length, w):
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    out = np.zeros(length, dtype=np.uint32)
+    lib().gpzo_unpack_fixed(_ptr(words, C.c_uint32), length, w, _ptr(out, C.c_uint32))
+    return out
+
+
+def compress(fields, eb, mode=0, seg_bits=3, want_perm=True):
+    """Compress [F, n] float32 -> (stream bytes as np.uint8, perm or None)."""
+    x = _as_fields(fields)
+    F, n = x.shape
+    ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
+    cap = bound_size(n, F)
+    out = np.zeros(max(cap, 4), dtype=np.uint8)
+    size = C.c_uint64(0)
+    perm = np.zeros(n, dtype=np.uint32) if want_perm else None
+    rc = lib().gpzo_compress(_field_ptrs(x), n, F, mode, _ptr(ebs, C.c_double), seg_bits,
+                             _ptr(out, C.c_uint8), cap, C.byref(size),
+                             _ptr(perm, C.c_uint32) if want_perm else None)
+    if rc != OK:
+        raise RuntimeError("gpzo_compress failed: %d" % rc)
+    return out[:size.value].copy(), perm
+
+
+def compress_status(fields, eb, mode=0, seg_bits=3, cap=None):
+    """Return only the status code (for argument-error tests)."""
+    x = _as_fields(fields)
+    F, n = x.shape
+    ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
+    cap = bound_size(n, F) if cap is None else cap
+    out = np.zeros(max(cap, 4), dtype=np.uint8)
+    size = C.c_uint64(0)
+    return lib().gpzo_compress(_field_ptrs(x), n, F, mode, _ptr(ebs, C.c_double), seg_bits,
+                               _ptr(out, C.c_uint8), cap, C.byref(size), None)
+
+
+def decompress(stream, n_fields, n):
+    """Stream bytes -> [F, n] float32 in block-sorted order."""
+    s = np.ascontiguousarray(stream, dtype=np.uint8)
+    out = np.zeros((n_fields, n), dtype=np.float32)
+    rc = lib().gpzo_decompress(_ptr(s, C.c_uint8), s.size, _field_ptrs(out), n_fields, n)
+    if rc != OK:
+        raise RuntimeError("gpzo_decompress failed: %d" % rc)
+    return out
+
+
+def decompress_status(stream, n_fields, n):
+    s = np.ascontiguousarray(stream, dtype=np.uint8)
+    out = np.zeros((n_fields, n), dtype=np.float32)
+    return lib().gpzo_decompress(_ptr(s, C.c_uint8), s.size, _field_ptrs(out), n_fields, n)

@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against things other than itself.
+
+The GPU path is checked against the oracle, so the oracle must first be tied
+to what the paper and mathematics fix:
+  * hand-worked fixtures (tests/golden/*.txt, each with its derivation);
+  * the error-bound invariant |x - x_hat| <= eb on every value (Section 3.1
+    goal iii, Section 4.1), in exact arithmetic;
+  * the stable sort against numpy's stable argsort, the run-length code
+    against numpy.unique, the widths against int.bit_length, the
+    fixed-length code against Python big-integer concatenation;
+  * the reconstruction against exact rational arithmetic rounded once;
+  * closed forms for uniform data (bits per axis, unique segments, ratio,
+    PSNR of a uniform quantisation error);
+  * special cases: empty, ragged, all-equal, non-finite, out-of-range.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from tests import _golden as gold
+
+
+# ----------------------------------------------------------------------------- goldens
+
+BLOCK_GOLDENS = [n for n in gold.all_names() if "block_words" in gold.load(n)]
+STREAM_GOLDENS = [n for n in gold.all_names() if "stream_words" in gold.load(n)]
+
+
+def _params(oracle, g):
+    return [oracle.params_abs(g["eb"]) for _ in range(g["n_fields"])]
+
+
+@pytest.mark.parametrize("name", BLOCK_GOLDENS)
+def test_golden_block_words(oracle, name):
+    g = gold.load(name)
+    words, perm = oracle.encode_block(g["fields"], g["seg_bits"], _params(oracle, g))
+    assert words.tolist() == g["block_words"].tolist()
+    assert perm.tolist() == g["perm"].tolist()
+
+
+@pytest.mark.parametrize("name", STREAM_GOLDENS)
+def test_golden_stream_words(oracle, name):
+    g = gold.load(name)
+    stream, _ = oracle.compress(g["fields"], g["eb"], g["mode"], g["seg_bits"])
+    assert stream.view(np.uint32).tolist() == g["stream_words"].tolist()
+
+
+@pytest.mark.parametrize("name", [n for n in gold.all_names() if "out" in gold.load(n)])
+def test_golden_decompress(oracle, name):
+    g = gold.load(name)
+    stream, perm = oracle.compress(g["fields"], g["eb"], g["mode"], g["seg_bits"])
+    out = oracle.decompress(stream, g["n_fields"], g["fields"].shape[1])
+    assert out.view(np.uint32).tolist() == g["out"].view(np.uint32).tolist()
+    assert perm.tolist() == g["perm"].tolist()
+
+
+# ----------------------------------------------------------------------------- parameters
+
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4, 0.5, 0.75, 3e-7, 123.456, 2.0 ** -130])
+def test_params_abs_exact(oracle, eb):
+    p = oracle.params_abs(eb)
+    assert np.float32(p.eb) == gold.rn32(Fraction(eb))
+    assert np.float32(p.s) == gold.rn32(Fraction(eb * 1.96875))  # one double product
+    if p.s != 0:
+        assert np.float32(p.inv) == gold.rn32(1 / Fraction(float(np.float32(p.s))))
+    target = Fraction(eb * (1.0 - 2.0 ** -22))  # one double product, as the reading states
+    assert np.float32(p.ebchk) == gold.rd32(target)
+    # the step leaves room for rounding: half a step is below eb
+    assert Fraction(float(np.float32(p.s))) / 2 < Fraction(eb) or p.s == 0 or not np.isfinite(p.s)
+    # the verification threshold keeps the exact error strictly inside eb:
+    # |RN(x - xh)| <= ebchk implies |x - xh| <= ebchk * (1 + 2^-23) < eb
+    assert Fraction(float(np.float32(p.ebchk))) * (1 + Fraction(1, 2 ** 23)) < Fraction(eb)
+
+
+def test_params_abs_rejects(oracle):
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(ValueError):
+            oracle.params_abs(bad)
+
+
+def test_params_rel(oracle):
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(10001) * 37.0 + 5.0).astype(np.float32)
+    x[17] = np.nan
+    p = oracle.params_rel(1e-4, x)
+    rng_ = float(np.nanmax(x)) - float(np.nanmin(x))
+    assert np.float32(p.eb) == gold.rn32(Fraction(1e-4 * rng_))
+    # constant field, all-NaN field and an infinite range fall back to eb = rel
+    for y in (np.full(10, 3.0, np.float32), np.full(10, np.nan, np.float32),
+              np.array([1.0, np.inf], np.float32)):
+        assert np.float32(oracle.params_rel(1e-3, y).eb) == np.float32(1e-3)
+
+
+# ----------------------------------------------------------------------------- error bound
+
+def _inverse_perm(perm):
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size, dtype=perm.dtype)
+    return inv
+
+
+def _check_bound(x, out, perm, ebs):
+    """|x - x_hat| <= eb on every value, in exact arithmetic (float32 values
+    are exact in double; their difference is exact when exponents are close,
+    and Fractions settle the rest)."""
+    xs = x[:, perm]
+    for f in range(x.shape[0]):
+        a = xs[f].astype(np.float64)
+        b = out[f].astype(np.float64)
+        finite = np.isfinite(a)
+        # non-finite values only occur in raw blocks and come back bit-exact
+        assert np.array_equal(xs[f][~finite].view(np.uint32), out[f][~finite].view(np.uint32))
+        d = np.abs(a[finite] - b[finite])
+        assert np.all(d <= ebs[f]), (f, d.max(), ebs[f])
+        worst = np.argsort(d)[-8:]
+        for k in worst:
+            assert abs(Fraction(float(a[finite][k])) - Fraction(float(b[finite][k]))) <= Fraction(ebs[f])
+
+
+def _gen(kind, n, rng):
+    if kind == "uniform":
+        return (rng.random((3, n)) * 256).astype(np.float32), 1e-2
+    if kind == "clustered":
+        c = rng.random((3, 40)) * 256
+        lab = rng.integers(0, 40, n)
+        return (c[:, lab] + rng.standard_normal((3, n)) * 0.5).astype(np.float32), 1e-3
+    if kind == "lidar":  # |x| ~ 1e4 m with eb 1e-3 m: float spacing ~ eb
+        x = np.cumsum(np.full(n, 0.5)) % 10000 + 2000
+        y = np.repeat(np.arange(n // 2000 + 1), 2000)[:n] * 1.0 + 5000
+        z = 40 * np.sin(x / 700.0) + rng.standard_normal(n) * 0.05
+        return np.stack([x, y, z]).astype(np.float32), 1e-3
+    if kind == "negative_mixed":
+        return (rng.standard_normal((4, n)) * np.array([[1e3], [1e-2], [1.0], [300.0]])).astype(np.float32), 1e-4
+    if kind == "tiny_eb":
+        return (rng.random((3, n)) * 2 - 1).astype(np.float32), 1e-7
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "lidar", "negative_mixed", "tiny_eb"])
+def test_error_bound_abs(oracle, kind):
+    rng = np.random.default_rng(11)
+    x, eb = _gen(kind, 20000 + 333, rng)
+    stream, perm = oracle.compress(x, eb, 0, 3)
+    out = oracle.decompress(stream, x.shape[0], x.shape[1])
+    _check_bound(x, out, perm, [eb] * x.shape[0])
+
+
+def test_error_bound_rel(oracle):
+    rng = np.random.default_rng(12)
+    x, _ = _gen("negative_mixed", 12345, rng)
+    stream, perm = oracle.compress(x, 1e-4, 1, 3)
+    out = oracle.decompress(stream, x.shape[0], x.shape[1])
+    ebs = [float(oracle.params_rel(1e-4, x[f]).eb) for f in range(x.shape[0])]
+    _check_bound(x, out, perm, ebs)
+
+
+@pytest.mark.parametrize("name", [n for n in gold.all_names() if "codes" in gold.load(n)])
+def test_golden_quantiser_codes(oracle, name):
+    """Hand-worked cases where the first candidate fails the fp32 check and
+    the next one is kept (Reading R5)."""
+    g = gold.load(name)
+    st = oracle.block_stages(g["fields"], g["seg_bits"], _params(oracle, g))
+    assert not st["raw"]
+    assert st["q"].tolist() == g["codes"].tolist()
+
+
+def test_lidar_like_has_no_raw_blocks(oracle):
+    """|x| ~ 1e4 m with eb = 1e-3 m (float spacing ~ eb): every block still
+    encodes, every value within the bound."""
+    rng = np.random.default_rng(13)
+    x, eb = _gen("lidar", 8192, rng)
+    x[0] += 7000.0
+    stream, perm = oracle.compress(x, eb, 0, 3)
+    w = stream.view(np.uint32)
+    table = w[22:22 + 9].astype(np.int64)
+    assert not np.any(w[22 + 9 + table[:-1]] & 1)
+    _check_bound(x, oracle.decompress(stream, 3, 8192), perm, [eb] * 3)
+
+
+def test_coarse_spacing_block_goes_raw(oracle):
+    """eb below half the float spacing (x ~ 2e4, spacing 2^-9 ~ 2e-3 > eb =
+    1e-3): most values cannot be coded, the block is stored raw, bit-exact."""
+    x = (np.float32(20000.0) + np.arange(1024, dtype=np.float32) * np.float32(0.37)).astype(np.float32)[None, :]
+    stream, perm = oracle.compress(x, 1e-3, 0, 3)
+    assert np.array_equal(perm, np.arange(1024))
+    assert np.array_equal(oracle.decompress(stream, 1, 1024).view(np.uint32), x.view(np.uint32))
+
+
+# ----------------------------------------------------------------------------- per-stage pins
+
+def _random_block(rng, F, n_b, kind):
+    if kind == "clustered":
+        c = rng.random((F, 5)) * 10
+        lab = rng.integers(0, 5, n_b)
+        return (c[:, lab] + rng.standard_normal((F, n_b)) * 0.3).astype(np.float32)
+    return (rng.random((F, n_b)) * 100).astype(np.float32)
+
+
+@pytest.mark.parametrize("F,G,n_b,kind", [(3, 3, 1024, "uniform"), (3, 3, 1024, "clustered"),
+                                          (6, 3, 1000, "clustered"), (2, 2, 77, "uniform"),
+                                          (1, 3, 1, "uniform"), (8, 1, 512, "clustered"),
+                                          (3, 0, 300, "uniform")])
+def test_stage_pins(oracle, F, G, n_b, kind):
+    rng = np.random.default_rng(F * 100 + G * 10 + n_b)
+    x = _random_block(rng, F, n_b, kind)
+    p = [oracle.params_abs(1e-2) for _ in range(F)]
+    st = oracle.block_stages(x, G, p)
+    assert not st["raw"]
+    P = min(F, 3)
+    # block minimum
+    assert np.array_equal(st["mins"], x.min(axis=1))
+    # widths are the minimal ones
+    for f in range(F):
+        assert st["bits"][f] == int(st["q"][f].max()).bit_length()
+    # m * segId + segOffset = q, m = 2^o, at most 2^G segments per axis
+    gs = []
+    for f in range(P):
+        g = min(G, int(st["bits"][f]))
+        o = int(st["bits"][f]) - g
+        gs.append(g)
+        q = st["q"][f].astype(np.int64)
+        assert np.array_equal(st["seg_id"][f].astype(np.int64) * (1 << o) + st["seg_off"][f], q)
+        assert st["seg_id"][f].max() < (1 << g) or g == 0 and st["seg_id"][f].max() == 0
+        assert st["seg_off"][f].max() < (1 << o)
+    # row-major linearisation, axis 0 most significant
+    key = np.zeros(n_b, np.int64)
+    for f in range(P):
+        key = key * (1 << gs[f]) + st["seg_id"][f]
+    assert np.array_equal(key, st["key"])
+    # stable sort by key == numpy's stable argsort
+    assert np.array_equal(st["perm"], np.argsort(st["key"], kind="stable"))
+    # run-length code == numpy.unique on the sorted keys
+    u, c = np.unique(st["key"][st["perm"]], return_counts=True)
+    assert np.array_equal(st["uniq"], u) and np.array_equal(st["counts"], c)
+    # every value within the bound of its code
+    for f in range(F):
+        xh = np.array([gold.rn32(Fraction(int(q)) * Fraction(float(p[f].s)) + Fraction(float(st["mins"][f])))
+                       for q in st["q"][f][:64]])
+        assert np.all(np.abs(xh.astype(np.float64) - x[f][:64].astype(np.float64)) <= 1e-2)
+
+
+@pytest.mark.parametrize("w", list(range(0, 33)))
+def test_pack_fixed_is_concatenation(oracle, w):
+    rng = np.random.default_rng(w)
+    for length in (0, 1, 31, 32, 33, 100, 1024):
+        v = rng.integers(0, 1 << w, length, dtype=np.uint64).astype(np.uint32) if w else np.zeros(length, np.uint32)
+        words = oracle.pack_fixed(v, w)
+        big = 0
+        for j, val in enumerate(v.tolist()):
+            big |= int(val) << (j * w)
+        nwords = (length * w + 31) // 32
+        expect = np.frombuffer(big.to_bytes(4 * nwords, "little"), dtype="<u4") if nwords else np.zeros(0, np.uint32)
+        assert words.tolist() == expect.tolist()
+        assert np.array_equal(oracle.unpack_fixed(words, length, w), v)
+
+
+def test_reconstruction_exact(oracle):
+    """Decompressed value = RN32(q * 2eb + min), one rounding (Section 5.1 FMA)."""
+    rng = np.random.default_rng(3)
+    x = _random_block(rng, 4, 1024, "clustered")
+    p = [oracle.params_abs(1e-3) for _ in range(4)]
+    st = oracle.block_stages(x, 3, p)
+    stream, perm = oracle.compress(x, 1e-3, 0, 3)
+    out = oracle.decompress(stream, 4, 1024)
+    for f in range(4):
+        for j in range(0, 1024, 37):
+            q = int(st["q"][f][perm[j]])
+            expect = gold.rn32(Fraction(q) * Fraction(float(p[f].s)) + Fraction(float(st["mins"][f])))
+            assert out[f][j] == expect
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+def test_uniform_closed_forms(oracle):
+    """1e6 particles uniform in [0,256)^3, eb = 1e-2 (the small configuration):
+    a block spans ~255.5/(2eb) ~ 12775 steps -> 14 bits per axis; with G = 3
+    the segment size is 2^11, giving 6 full segments and one of ~0.24 width per
+    axis; unique segments per block follow 1 - (1 - p)^1024 summed over the
+    cells; ratio ~2.6; the error is uniform on [-s/2, s/2] with the step
+    s = 2 eb * 63/64, so PSNR = 20 log10(sqrt(3) * 256 / (s/2)) = 93.07 dB
+    (Section 3.1 goal iii).  No block may fall back to raw."""
+    rng = np.random.default_rng(0)
+    n = 1_000_000
+    x = (rng.random((3, n)) * 256).astype(np.float32)
+    stream, perm = oracle.compress(x, 1e-2, 0, 3)
+    out = oracle.decompress(stream, 3, n)
+    cr = x.nbytes / stream.size
+    assert 2.5 < cr < 2.75, cr
+    xs = x[:, perm].astype(np.float64)
+    nrmse = [np.sqrt(np.mean((xs[f] - out[f]) ** 2)) / (xs[f].max() - xs[f].min()) for f in range(3)]
+    psnr = -20 * np.log10(np.sqrt(np.mean(np.square(nrmse))))
+    half_step = float(np.float32(1e-2 * 1.96875)) / 2
+    assert abs(psnr - 20 * np.log10(np.sqrt(3) * 256 / half_step)) < 0.15, psnr
+    w = stream.view(np.uint32)
+    table = w[22:22 + 978].astype(np.int64)
+    assert not np.any(w[22 + 978 + table[:-1]] & 1)  # no raw block
+    # per-block stages on a sample
+    p = [oracle.params_abs(1e-2)] * 3
+    us = []
+    for b in range(0, 977, 61):
+        st = oracle.block_stages(x[:, b * 1024:(b + 1) * 1024], 3, p)
+        assert st["bits"].tolist() == [14, 14, 14]
+        us.append(len(st["uniq"]))
+    step = float(np.float32(1e-2 * 1.96875))
+    extent = 255.5 / step
+    probs = [2048 / extent] * 6 + [1 - 6 * 2048 / extent]
+    expect_u = sum(1 - (1 - a * b * c) ** 1024 for a in probs for b in probs for c in probs)
+    assert abs(np.mean(us) - expect_u) < 8, (np.mean(us), expect_u)
+
+
+# ----------------------------------------------------------------------------- special cases
+
+def test_empty(oracle):
+    x = np.zeros((3, 0), np.float32)
+    stream, perm = oracle.compress(x, 1e-2, 0, 3)
+    w = stream.view(np.uint32)
+    assert w.size == 16 + 6 + 1 and w[8] == 0 and w[9] == 0 and w[-1] == 0
+    assert oracle.decompress(stream, 3, 0).shape == (3, 0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 1023, 1024, 1025, 2049, 5000])
+def test_sizes_roundtrip(oracle, n):
+    rng = np.random.default_rng(n)
+    x = (rng.random((3, n)) * 10).astype(np.float32)
+    stream, perm = oracle.compress(x, 1e-3, 0, 3)
+    assert stream.size <= oracle.bound_size(n, 3)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    out = oracle.decompress(stream, 3, n)
+    _check_bound(x, out, perm, [1e-3] * 3)
+    # the offset table is monotone and ends at the payload size
+    w = stream.view(np.uint32)
+    nb = (n + 1023) // 1024
+    table = w[16 + 6:16 + 6 + nb + 1]
+    assert table[0] == 0 and np.all(np.diff(table.astype(np.int64)) >= 1) and table[-1] == w[9]
+    assert w.size == 16 + 6 + nb + 1 + int(w[9])
+
+
+def test_nonfinite_and_out_of_range_blocks_are_raw(oracle):
+    x = (np.arange(3 * 2048, dtype=np.float32).reshape(3, 2048) * 0.01)
+    x[1, 5] = np.inf
+    x[2, 1500] = -np.inf
+    stream, perm = oracle.compress(x, 1e-3, 0, 3)
+    out = oracle.decompress(stream, 3, 2048)
+    assert np.array_equal(perm, np.arange(2048))  # both blocks raw
+    assert np.array_equal(out.view(np.uint32), x.view(np.uint32))
+    # a range too wide for 31-bit codes is stored raw, bit-exact
+    y = np.array([[0.0, 3e38, -3e38]], np.float32)
+    s2, _ = oracle.compress(y, 1e-6, 0, 3)
+    assert np.array_equal(oracle.decompress(s2, 1, 3).view(np.uint32), y.view(np.uint32))
+
+
+def test_signed_zero_minimum(oracle):
+    x = np.array([[-0.0, 0.0, 1.0, 2.0] * 4], np.float32)
+    p = [oracle.params_abs(32 / 63)]  # step exactly 1
+    st = oracle.block_stages(x, 3, p)
+    assert st["mins"].view(np.uint32)[0] == 0  # stored as +0
+    stream, perm = oracle.compress(x, 32 / 63, 0, 3)
+    out = oracle.decompress(stream, 1, x.shape[1])
+    assert np.array_equal(out[0], x[0][perm])  # numerically equal
+
+
+def test_constant_field_exact(oracle):
+    x = np.full((3, 3000), 7.25, np.float32)
+    x[0] = np.linspace(0, 1, 3000, dtype=np.float32)
+    stream, perm = oracle.compress(x, 1e-4, 0, 3)
+    out = oracle.decompress(stream, 3, 3000)
+    assert np.all(out[1] == 7.25) and np.all(out[2] == 7.25)
+
+
+def test_invalid_arguments(oracle):
+    x = np.zeros((3, 10), np.float32)
+    assert oracle.compress_status(x, 0.0) == oracle.ERR_INVALID_ARG
+    assert oracle.compress_status(x, float("nan")) == oracle.ERR_INVALID_ARG
+    assert oracle.compress_status(x, 1e-3, mode=2) == oracle.ERR_INVALID_ARG
+    assert oracle.compress_status(x, 1e-3, seg_bits=4) == oracle.ERR_INVALID_ARG
+    assert oracle.compress_status(np.zeros((9, 10), np.float32), 1e-3) == oracle.ERR_INVALID_ARG
+    assert oracle.compress_status(x, 1e-3, cap=10) == oracle.ERR_CAPACITY
+
+
+def test_corrupt_streams_rejected(oracle):
+    rng = np.random.default_rng(9)
+    x = _random_block(rng, 3, 3000, "clustered")
+    stream, _ = oracle.compress(x, 1e-3, 0, 3)
+    w = stream.view(np.uint32).copy()
+
+    def status(words):
+        return oracle.decompress_status(words.view(np.uint8), 3, 3000)
+
+    assert status(w) == oracle.OK
+    for idx, val in [(0, 0), (1, 2), (2, 4), (4, 512), (6, 2999), (10, 1)]:
+        bad = w.copy()
+        bad[idx] = val
+        assert status(bad) == oracle.ERR_CORRUPT, idx
+    assert status(w[:-1]) == oracle.ERR_CORRUPT  # truncated
+    bad = w.copy()
+    bad[22 + 1], bad[22 + 2] = bad[22 + 2], bad[22 + 1]  # offsets out of order
+    assert status(bad) == oracle.ERR_CORRUPT
+    bad = w.copy()
+    payload = 22 + 3 + 1
+    bad[payload] |= np.uint32(1 << 30)  # reserved bits of block 0's mode word
+    assert status(bad) == oracle.ERR_CORRUPT
+    # random single-bit flips: never crash, result is OK or CORRUPT
+    for _ in range(300):
+        bad = w.copy()
+        k = rng.integers(0, w.size)
+        bad[k] ^= np.uint32(1 << int(rng.integers(0, 32)))
+        assert status(bad) in (oracle.OK, oracle.ERR_CORRUPT)
