@@ -1,0 +1,151 @@
+/*
+ * gpz.h -- C ABI of libgpz, a GB300 (sm_103a) implementation of GPZ, the
+ * error-bounded lossy compressor for particle data of Li et al., "GPZ:
+ * GPU-Accelerated Lossy Compressor for Particle Data" (arXiv 2508.10305).
+ *
+ * The library compresses n particles of F fp32 fields (structure of arrays,
+ * one device array per field) into a byte stream, and back.  It runs the
+ * paper's four-stage pipeline (Section 3.2): spatial quantisation into a
+ * per-axis segment id and offset (Section 4.1), a stable per-block sort by
+ * segment id (Section 4.2), run-length + delta + fixed-length coding
+ * (Section 4.3), and compaction of the per-block outputs through a device-wide
+ * prefix sum (Section 4.4).  Decompression undoes them without sorting, so
+ * its output is the input permuted within each 1024-particle block; the
+ * permutation can be returned by compression.
+ *
+ * Conventions for every entry point:
+ *   - pointers named d_* are device pointers (cudaMalloc'ed or equivalent,
+ *     on the current device); h_* are host pointers;
+ *   - the caller owns every buffer; the library allocates device memory only
+ *     when a workspace argument is NULL (stream-ordered, freed before return);
+ *   - `stream` is a cudaStream_t handle (NULL = the legacy default stream);
+ *     work is enqueued on it and the call returns without synchronising,
+ *     unless a host-side result (h_*) is requested or the workspace is
+ *     allocated by the library;
+ *   - argument errors are returned at once and enqueue nothing; errors found
+ *     by the kernels (corrupt stream, a timed-out wait) are recorded in the
+ *     workspace's status word, which each call clears when it starts, and
+ *     are read with gpz_sync_status();
+ *   - no entry point aborts, traps or prints.
+ */
+#ifndef GPZ_H
+#define GPZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPZ_OK = 0,
+    GPZ_ERR_INVALID_ARG = 1, /* a NULL where a pointer is required, a size or a bound out of range */
+    GPZ_ERR_CAPACITY = 2,    /* output or workspace smaller than gpz_bound_size / *_workspace_size */
+    GPZ_ERR_CORRUPT = 3,     /* the stream fails a format check (decompression) */
+    GPZ_ERR_CUDA = 4,        /* a CUDA runtime call failed (launch, copy, stream) */
+    GPZ_ERR_OOM = 5,         /* the library could not allocate its workspace */
+    GPZ_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (never expected) */
+    GPZ_ERR_UNSUPPORTED = 7  /* n too large for 32-bit word offsets: n_blocks + F*n >= 2^32 */
+} gpz_status;
+
+typedef enum {
+    GPZ_EB_ABS = 0, /* eb[f] is the absolute bound of field f */
+    GPZ_EB_REL = 1  /* eb[f] is relative to field f's value range (max - min over non-NaN values) */
+} gpz_eb_mode;
+
+#define GPZ_MAX_FIELDS 8
+#define GPZ_BLOCK 1024 /* particles per block: one warp, 32 threads x 32 points (Section 4.2) */
+
+/* Compression parameters.
+ *   mode:     gpz_eb_mode.
+ *   n_fields: F in 1..8.  Fields 0..min(F,3)-1 are the position axes that
+ *             are segmented and sorted (Section 4.1); fields 3.. are carried
+ *             along in sorted order with their own codes.
+ *   seg_bits: G in 0..3, the segment-id bits per axis (at most 2^G segments
+ *             per axis and block; the segment size m scales with the block's
+ *             extent, Section 4.1).  3 is the default.
+ *   eb[f]:    error bound of field f, > 0 and finite.  Every decompressed
+ *             value is within eb (absolute) of its input value. */
+typedef struct {
+    int mode;
+    int n_fields;
+    int seg_bits;
+    double eb[GPZ_MAX_FIELDS];
+} gpz_params;
+
+/* Worst-case size in bytes of the stream for n particles of n_fields fields
+ * (every block stored raw).  Returns 0 for n_fields outside 1..8. */
+uint64_t gpz_bound_size(uint64_t n, int n_fields);
+
+/* Device workspace in bytes needed by gpz_compress for n particles of
+ * n_fields fields: per-block temporary outputs (at most the input size) plus
+ * the prefix-sum state.  Returns 0 for n_fields outside 1..8. */
+uint64_t gpz_compress_workspace_size(uint64_t n, int n_fields);
+
+/* Device workspace in bytes needed by gpz_decompress (its status word). */
+uint64_t gpz_decompress_workspace_size(void);
+
+/* Compress (Sections 4.1-4.4).
+ *   d_fields:     host array of n_fields device pointers, field f's n fp32
+ *                 values at d_fields[f]; each 4-byte aligned (16-byte
+ *                 alignment enables bulk-copy staging).
+ *   n:            particles (0 allowed: the stream is then a bare header).
+ *   p:            parameters (host).
+ *   d_out:        device buffer for the stream, 16-byte aligned, of
+ *                 out_capacity bytes >= gpz_bound_size(n, F).
+ *   d_out_size:   device uint64_t receiving the stream size in bytes, or NULL.
+ *   h_out_size:   host uint64_t receiving the stream size, or NULL.  When
+ *                 not NULL the call synchronises `stream` and returns the
+ *                 device-side status.
+ *   d_perm:       device array of n uint32 receiving the permutation
+ *                 (d_perm[i] = input index of output particle i), or NULL.
+ *   d_ws/ws_size: workspace (256-byte aligned) of at least
+ *                 gpz_compress_workspace_size(n, F) bytes, or NULL to let the
+ *                 library allocate and free it (the call then synchronises).
+ * The stream is identical for every launch configuration and device. */
+gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_params* p,
+                        void* d_out, uint64_t out_capacity, uint64_t* d_out_size,
+                        uint64_t* h_out_size, uint32_t* d_perm, void* d_ws, uint64_t ws_size,
+                        void* stream);
+
+/* Decompress (Section 3.2, last paragraph: the inverse without sorting).
+ *   d_in/in_size: the stream (device, 4-byte aligned) and its size in bytes.
+ *   d_fields:     host array of n_fields device pointers, each receiving n
+ *                 fp32 values in the stream's block-sorted order.
+ *   n_fields, n:  must match the stream header, else GPZ_ERR_CORRUPT.
+ *   d_ws/ws_size: workspace of gpz_decompress_workspace_size() bytes, or
+ *                 NULL (the call then allocates, synchronises and returns the
+ *                 device-side status).
+ * A stream that fails a format check sets GPZ_ERR_CORRUPT in the workspace
+ * status; the kernels never read outside [d_in, d_in + in_size) and never
+ * write outside the n values of each output field. */
+gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fields, int n_fields,
+                          uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
+
+/* Synchronise `stream`, return the status recorded in the workspace d_ws by
+ * the kernels of earlier calls (GPZ_OK if none), and clear it. */
+gpz_status gpz_sync_status(void* d_ws, void* stream);
+
+/* Parse a stream header held in host memory (at least 64 bytes). */
+gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_fields,
+                       int* seg_bits, int* mode);
+
+/* Static text for a status code. */
+const char* gpz_status_str(gpz_status s);
+
+/* Measurement hooks.  When enabled (per process), every later call records
+ * CUDA events on its stream around each of its kernels.  gpz_stage_times
+ * synchronises on the last recorded event and writes, for the most recent
+ * call, up to max stage names and elapsed milliseconds; it returns the count. */
+void gpz_set_stage_timing(int enable);
+int gpz_stage_times(const char** names, float* ms, int max);
+
+/* Kernel launches enqueued by this process since the last reset. */
+uint64_t gpz_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPZ_H */

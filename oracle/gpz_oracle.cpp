@@ -521,6 +521,13 @@ void gpzo_unpack_fixed(const uint32_t* words, uint32_t len, uint32_t w, uint32_t
     for (uint32_t j = 0; j < len; ++j) values[j] = get_bits(words, (uint64_t)j * w, w);
 }
 
+int gpzo_decode_block(const uint32_t* words, uint32_t nwords, int F, int n_b, int G, const float* s,
+                      float* const* out) {
+    if (!words || !s || !out || !valid_shape(F, G) || n_b < 1 || n_b > (int)BLOCK)
+        return GPZO_ERR_INVALID_ARG;
+    return decode_block(words, nwords, F, n_b, G, s, out) ? GPZO_OK : GPZO_ERR_CORRUPT;
+}
+
 int gpzo_compress(const float* const* fields, uint64_t n, int F, int mode, const double* eb,
                   int G, uint8_t* out, uint64_t cap, uint64_t* out_size, uint32_t* perm) {
     if (!valid_shape(F, G) || (mode != 0 && mode != 1) || !eb || !out || !out_size)

@@ -58,6 +58,11 @@ int gpzo_encode_block(const float* const* fields, int n_fields, int n_b, int seg
                       const gpzo_field_params* params, uint32_t* out, uint32_t cap_words,
                       uint32_t* nwords, uint32_t* perm_b);
 
+/* Decode one block's words (encoded or raw) into out[f][0..n_b), given the
+ * segment bits G and the per-field steps s[f] from the stream header. */
+int gpzo_decode_block(const uint32_t* words, uint32_t nwords, int n_fields, int n_b, int seg_bits,
+                      const float* s, float* const* out);
+
 /* The intermediate results of encoding one block, exposed so that tests can
  * pin each step on its own.  Arrays are sized by the caller:
  *   mins[F], bits[F], q[F*n_b] (field-major), seg_id[F*n_b], seg_off[F*n_b],

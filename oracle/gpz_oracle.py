@@ -38,6 +38,7 @@ def lib():
         L.gpzo_bound_size.restype = C.c_uint64
         L.gpzo_encode_block.argtypes = [P(f32p), C.c_int, C.c_int, C.c_int, P(FieldParams), u32p,
                                         C.c_uint32, u32p, u32p]
+        L.gpzo_decode_block.argtypes = [u32p, C.c_uint32, C.c_int, C.c_int, C.c_int, f32p, P(f32p)]
         L.gpzo_block_stages.argtypes = [P(f32p), C.c_int, C.c_int, C.c_int, P(FieldParams),
                                         P(C.c_int), f32p, u32p, u32p, u32p, u32p, u32p, u32p, u32p,
                                         u32p, u32p]
@@ -112,6 +113,18 @@ def encode_block(fields, seg_bits, params, want_perm=True):
     if rc != OK:
         raise ValueError("gpzo_encode_block failed: %d" % rc)
     return out[:nw.value].copy(), perm
+
+
+def decode_block(words, n_fields, n_b, seg_bits, steps):
+    """One block's words -> [F, n_b] float32 (block-sorted order)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    s = np.ascontiguousarray(steps, dtype=np.float32)
+    out = np.zeros((n_fields, n_b), dtype=np.float32)
+    rc = lib().gpzo_decode_block(_ptr(w, C.c_uint32), w.size, n_fields, n_b, seg_bits,
+                                 _ptr(s, C.c_float), _field_ptrs(out))
+    if rc != OK:
+        raise RuntimeError("gpzo_decode_block failed: %d" % rc)
+    return out
 
 
 def block_stages(fields, seg_bits, params):

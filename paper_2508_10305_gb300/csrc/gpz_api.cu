@@ -1,0 +1,378 @@
+// gpz_api.cu -- host side of libgpz: the C ABI declared in include/gpz.h.
+// Validates arguments, lays out the workspace, finalises the per-field
+// constants and enqueues the kernels on the caller's stream:
+//   compress:   [range (relative bound)] -> Q.S.E. -> look-back scan -> copy
+//   decompress: decode
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gpz.h"
+#include "gpz_internal.cuh"
+
+using namespace gpz;
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+constexpr int kRangeGridMax = 152 * 4;
+constexpr uint64_t kCtrlBytes = 256;    // status, tile counter, range counter, out size
+constexpr uint64_t kParamBytes = 256;   // FieldParams[8]
+
+std::atomic<uint64_t> g_launches{0};
+
+uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+uint64_t nblocks_of(uint64_t n) { return (n + kBlock - 1) / kBlock; }
+
+uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * kBlock, 4); }
+
+uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kScanTile; }
+
+struct WsLayout {
+    uint64_t ctrl, params, states, partials, sizes, temp, total, zero_bytes;
+};
+
+WsLayout layout_of(uint64_t n, int F) {
+    WsLayout L{};
+    const uint64_t nb = nblocks_of(n);
+    uint64_t o = 0;
+    L.ctrl = o;
+    o += kCtrlBytes;
+    L.params = o;
+    o += kParamBytes;
+    L.states = o;
+    o += align_up(ntiles_of(nb) * 8, kAlign);
+    L.zero_bytes = o;  // ctrl + params + look-back states are cleared per call
+    L.partials = o;
+    o += align_up((uint64_t)kRangeGridMax * F * sizeof(float2), kAlign);
+    L.sizes = o;
+    o += align_up(nb * 4, kAlign);
+    L.temp = o;
+    o += align_up(nb * slot_words_of(F) * 4ull, kAlign);
+    L.total = o;
+    return L;
+}
+
+// The constants of one field from its bound eb: step eb * 63/32 (2 eb less
+// 1/64), reciprocal, and the verification threshold RD32(eb * (1 - 2^-22)).
+FieldParams finalise(double eb) {
+    FieldParams p;
+    p.eb = (float)eb;
+    p.s = (float)(eb * 1.96875);
+    p.inv = (float)(1.0 / (double)p.s);
+    const double t = eb * (1.0 - std::ldexp(1.0, -22));
+    float c = (float)t;
+    if ((double)c > t) c = std::nextafterf(c, -INFINITY);
+    p.ebchk = c;
+    return p;
+}
+
+// ---------------------------------------------------------------- stage timing
+
+struct StageTimer {
+    std::mutex mu;
+    bool enabled = false;
+    int count = 0;
+    const char* names[8] = {};
+    cudaEvent_t ev[9] = {};
+    bool created = false;
+} g_timer;
+
+struct Recorder {
+    bool on;
+    cudaStream_t s;
+    int k = 0;
+    Recorder(cudaStream_t stream) : s(stream) {
+        std::lock_guard<std::mutex> g(g_timer.mu);
+        on = g_timer.enabled;
+        if (on) {
+            if (!g_timer.created) {
+                for (auto& e : g_timer.ev) cudaEventCreate(&e);
+                g_timer.created = true;
+            }
+            g_timer.count = 0;
+            cudaEventRecord(g_timer.ev[0], s);
+        }
+    }
+    void mark(const char* name) {
+        ++g_launches;
+        if (!on) return;
+        std::lock_guard<std::mutex> g(g_timer.mu);
+        if (g_timer.count < 8) {
+            g_timer.names[g_timer.count] = name;
+            cudaEventRecord(g_timer.ev[g_timer.count + 1], s);
+            ++g_timer.count;
+        }
+    }
+};
+
+gpz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GPZ_OK : GPZ_ERR_CUDA; }
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+gpz_status read_status(void* d_ws, cudaStream_t s, bool clear) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GPZ_ERR_CUDA;
+    uint32_t st = 0;
+    if (cudaMemcpy(&st, d_ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GPZ_ERR_CUDA;
+    if (clear && st != 0 && cudaMemset(d_ws, 0, 4) != cudaSuccess) return GPZ_ERR_CUDA;
+    return (gpz_status)st;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t gpz_bound_size(uint64_t n, int F) {
+    if (F < 1 || F > kMaxFields) return 0;
+    const uint64_t nb = nblocks_of(n);
+    return 4ull * (kHeaderWords + 2ull * F + (nb + 1) + nb + (uint64_t)F * n);
+}
+
+uint64_t gpz_compress_workspace_size(uint64_t n, int F) {
+    if (F < 1 || F > kMaxFields) return 0;
+    return layout_of(n, F).total;
+}
+
+uint64_t gpz_decompress_workspace_size(void) { return kCtrlBytes; }
+
+const char* gpz_status_str(gpz_status s) {
+    switch (s) {
+        case GPZ_OK: return "ok";
+        case GPZ_ERR_INVALID_ARG: return "invalid argument";
+        case GPZ_ERR_CAPACITY: return "buffer too small";
+        case GPZ_ERR_CORRUPT: return "corrupt stream";
+        case GPZ_ERR_CUDA: return "CUDA error";
+        case GPZ_ERR_OOM: return "out of device memory";
+        case GPZ_ERR_TIMEOUT: return "device wait timed out";
+        case GPZ_ERR_UNSUPPORTED: return "unsupported size";
+    }
+    return "unknown status";
+}
+
+void gpz_set_stage_timing(int enable) {
+    std::lock_guard<std::mutex> g(g_timer.mu);
+    g_timer.enabled = enable != 0;
+}
+
+int gpz_stage_times(const char** names, float* ms, int max) {
+    std::lock_guard<std::mutex> g(g_timer.mu);
+    if (!g_timer.created || g_timer.count == 0) return 0;
+    if (cudaEventSynchronize(g_timer.ev[g_timer.count]) != cudaSuccess) return 0;
+    int k = 0;
+    for (; k < g_timer.count && k < max; ++k) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, g_timer.ev[k], g_timer.ev[k + 1]);
+        if (names) names[k] = g_timer.names[k];
+        if (ms) ms[k] = t;
+    }
+    return k;
+}
+
+uint64_t gpz_launch_count(int reset) {
+    return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+gpz_status gpz_sync_status(void* d_ws, void* stream) {
+    if (!d_ws) return GPZ_ERR_INVALID_ARG;
+    return read_status(d_ws, (cudaStream_t)stream, true);
+}
+
+gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_fields, int* seg_bits,
+                       int* mode) {
+    if (!h_header || len < 4ull * kHeaderWords) return GPZ_ERR_INVALID_ARG;
+    uint32_t w[kHeaderWords];
+    std::memcpy(w, h_header, sizeof(w));
+    if (w[0] != kMagic || w[1] != kVersion || w[2] < 1 || w[2] > (uint32_t)kMaxFields ||
+        w[3] > (uint32_t)kMaxSegBits || w[4] != (uint32_t)kBlock || w[5] > 1)
+        return GPZ_ERR_CORRUPT;
+    const uint64_t nn = (uint64_t)w[6] | ((uint64_t)w[7] << 32);
+    if (w[8] != nblocks_of(nn)) return GPZ_ERR_CORRUPT;
+    if (n) *n = nn;
+    if (n_fields) *n_fields = (int)w[2];
+    if (seg_bits) *seg_bits = (int)w[3];
+    if (mode) *mode = (int)w[5];
+    return GPZ_OK;
+}
+
+gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                        uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                        void* d_ws, uint64_t ws_size, void* stream) {
+    if (!p || !d_out || !aligned(d_out, 4)) return GPZ_ERR_INVALID_ARG;
+    const int F = p->n_fields;
+    if (F < 1 || F > kMaxFields || p->seg_bits < 0 || p->seg_bits > kMaxSegBits ||
+        (p->mode != GPZ_EB_ABS && p->mode != GPZ_EB_REL))
+        return GPZ_ERR_INVALID_ARG;
+    for (int f = 0; f < F; ++f)
+        if (!(p->eb[f] > 0.0) || !std::isfinite(p->eb[f])) return GPZ_ERR_INVALID_ARG;
+    if (n > 0) {
+        if (!d_fields) return GPZ_ERR_INVALID_ARG;
+        for (int f = 0; f < F; ++f)
+            if (!d_fields[f] || !aligned(d_fields[f], 4)) return GPZ_ERR_INVALID_ARG;
+    }
+    if (d_perm && !aligned(d_perm, 4)) return GPZ_ERR_INVALID_ARG;
+    const uint64_t nb = nblocks_of(n);
+    if (nb + (uint64_t)F * n >= (1ull << 32)) return GPZ_ERR_UNSUPPORTED;
+    if (out_capacity < gpz_bound_size(n, F)) return GPZ_ERR_CAPACITY;
+    const WsLayout L = layout_of(n, F);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own_ws = false;
+    if (d_ws) {
+        if (ws_size < L.total) return GPZ_ERR_CAPACITY;
+        if (!aligned(d_ws, kAlign)) return GPZ_ERR_INVALID_ARG;
+    } else {
+        if (cudaMallocAsync(&d_ws, L.total, s) != cudaSuccess) return GPZ_ERR_OOM;
+        own_ws = true;
+    }
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.ctrl);
+    uint32_t* tile_counter = status + 1;
+    uint32_t* range_counter = status + 2;
+    unsigned long long* ws_out_size = reinterpret_cast<unsigned long long*>(ws + L.ctrl + 16);
+    FieldParams* d_params = reinterpret_cast<FieldParams*>(ws + L.params);
+
+    gpz_status rc = GPZ_OK;
+    Recorder rec(s);
+    do {
+        if ((rc = cuda_status(cudaMemsetAsync(ws, 0, L.zero_bytes, s))) != GPZ_OK) break;
+        FieldParams hp[kMaxFields] = {};
+        const bool rel = p->mode == GPZ_EB_REL;
+        if (!rel)
+            for (int f = 0; f < F; ++f) hp[f] = finalise(p->eb[f]);
+        bool vec_ok = true;
+        for (int f = 0; f < F && n > 0; ++f) vec_ok = vec_ok && aligned(d_fields[f], 16);
+
+        if (rel) {
+            RangeArgs ra{};
+            for (int f = 0; f < F; ++f) {
+                ra.fields[f] = n ? d_fields[f] : nullptr;
+                ra.rel[f] = p->eb[f];
+            }
+            ra.n = n;
+            ra.F = F;
+            ra.vec_ok = vec_ok ? 1 : 0;
+            ra.partials = reinterpret_cast<float2*>(ws + L.partials);
+            ra.done_counter = range_counter;
+            ra.d_params = d_params;
+            uint64_t want = (n / 4 + kRangeThreads - 1) / kRangeThreads;
+            const int grid = (int)(want < 1 ? 1 : (want > (uint64_t)kRangeGridMax ? kRangeGridMax : want));
+            if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
+            rec.mark("range");
+        }
+
+        QseArgs qa{};
+        for (int f = 0; f < F; ++f) {
+            qa.fields[f] = n ? d_fields[f] : nullptr;
+            qa.params[f] = hp[f];
+        }
+        qa.n = n;
+        qa.nblocks = (uint32_t)nb;
+        qa.F = F;
+        qa.G = p->seg_bits;
+        qa.bulk_ok = vec_ok ? 1 : 0;
+        qa.d_params = rel ? d_params : nullptr;
+        qa.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
+        qa.slot_words = slot_words_of(F);
+        qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
+        qa.perm = d_perm;
+        qa.status = status;
+        qa.warp_bytes = qse_warp_bytes(F, &qa.tile_bytes);
+        if (nb > 0) {
+            if ((rc = cuda_status(launch_qse(qa, s))) != GPZ_OK) break;
+            rec.mark("qse");
+        }
+
+        uint32_t* stream_words = static_cast<uint32_t*>(d_out);
+        const uint32_t table_start = (uint32_t)(kHeaderWords + 2 * F);
+        ScanArgs sa{};
+        sa.sizes = qa.sizes;
+        sa.nblocks = (uint32_t)nb;
+        sa.table = stream_words + table_start;
+        sa.tile_state = reinterpret_cast<unsigned long long*>(ws + L.states);
+        sa.tile_counter = tile_counter;
+        sa.status = status;
+        if ((rc = cuda_status(launch_scan(sa, s))) != GPZ_OK) break;
+        rec.mark("scan");
+
+        CompactArgs ca{};
+        ca.temp = qa.temp;
+        ca.slot_words = qa.slot_words;
+        ca.sizes = qa.sizes;
+        ca.table = sa.table;
+        ca.stream = stream_words;
+        ca.payload_start = (uint32_t)(table_start + nb + 1);
+        ca.nblocks = (uint32_t)nb;
+        ca.n = n;
+        ca.F = F;
+        ca.G = p->seg_bits;
+        ca.mode = p->mode;
+        for (int f = 0; f < F; ++f) ca.params[f] = hp[f];
+        ca.d_params = rel ? d_params : nullptr;
+        ca.d_out_size = d_out_size ? reinterpret_cast<unsigned long long*>(d_out_size) : ws_out_size;
+        if ((rc = cuda_status(launch_compact(ca, s))) != GPZ_OK) break;
+        rec.mark("compact");
+
+        if (h_out_size || own_ws) {
+            if (h_out_size) {
+                if ((rc = cuda_status(cudaMemcpyAsync(h_out_size, ca.d_out_size, 8, cudaMemcpyDeviceToHost, s))) !=
+                    GPZ_OK)
+                    break;
+            }
+            rc = read_status(status, s, !own_ws);
+        }
+    } while (false);
+    if (own_ws) {
+        cudaFreeAsync(d_ws, s);
+        if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
+    }
+    return rc;
+}
+
+gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fields, int F, uint64_t n,
+                          void* d_ws, uint64_t ws_size, void* stream) {
+    if (!d_in || !aligned(d_in, 4) || F < 1 || F > kMaxFields) return GPZ_ERR_INVALID_ARG;
+    if (n > 0) {
+        if (!d_fields) return GPZ_ERR_INVALID_ARG;
+        for (int f = 0; f < F; ++f)
+            if (!d_fields[f] || !aligned(d_fields[f], 4)) return GPZ_ERR_INVALID_ARG;
+    }
+    if (in_size % 4 != 0 || in_size < 4ull * kHeaderWords) return GPZ_ERR_CORRUPT;
+    const uint64_t nb = nblocks_of(n);
+    if (nb + (uint64_t)F * n >= (1ull << 32)) return GPZ_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own_ws = false;
+    if (d_ws) {
+        if (ws_size < gpz_decompress_workspace_size()) return GPZ_ERR_CAPACITY;
+        if (!aligned(d_ws, 16)) return GPZ_ERR_INVALID_ARG;
+    } else {
+        if (cudaMallocAsync(&d_ws, gpz_decompress_workspace_size(), s) != cudaSuccess) return GPZ_ERR_OOM;
+        own_ws = true;
+    }
+    uint32_t* status = static_cast<uint32_t*>(d_ws);
+    gpz_status rc = GPZ_OK;
+    Recorder rec(s);
+    do {
+        if ((rc = cuda_status(cudaMemsetAsync(status, 0, 4, s))) != GPZ_OK) break;
+        DecArgs da{};
+        da.stream = static_cast<const uint32_t*>(d_in);
+        da.total_words = in_size / 4;
+        for (int f = 0; f < F; ++f) da.out[f] = n ? d_fields[f] : nullptr;
+        da.n = n;
+        da.F = F;
+        da.nblocks = (uint32_t)nb;
+        da.status = status;
+        if (nb > 0) {
+            if ((rc = cuda_status(launch_decompress(da, s))) != GPZ_OK) break;
+            rec.mark("decompress");
+        }
+        if (own_ws) rc = read_status(status, s, false);
+    } while (false);
+    if (own_ws) {
+        cudaFreeAsync(d_ws, s);
+        if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
+    }
+    return rc;
+}
+
+}  // extern "C"

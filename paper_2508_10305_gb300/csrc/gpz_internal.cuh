@@ -1,0 +1,244 @@
+// gpz_internal.cuh -- device-side constants, kernel argument blocks and warp
+// helpers of libgpz (sm_103a).  The stream format implemented here is the one
+// of include/gpz.h: a 16-word header, (eb, step) per field, a table of block
+// word offsets, then one encoded or raw block per 1024 particles.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpz {
+
+constexpr int kBlock = 1024;             // particles per block (Section 4.2: 32 threads x 32 points)
+constexpr uint32_t kMagic = 0x315A5047u; // 'G','P','Z','1'
+constexpr uint32_t kVersion = 1;
+constexpr int kHeaderWords = 16;
+constexpr int kMaxFields = 8;
+constexpr int kMaxSegBits = 3;
+constexpr int kMaxBins = 512;            // 2^(3 * kMaxSegBits) linearised segment ids
+constexpr int kRow = 33;                 // padded shared-memory row of 32 values
+constexpr int kPadWords = 32 * kRow;     // 1056: 1024 values in padded rows
+constexpr int kQseWarps = 4;             // warps (= particle blocks) per CTA of the fused kernel
+constexpr int kDecWarps = 8;             // warps per CTA of the decompression kernel
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kRangeThreads = 256;
+constexpr int kCompactWarps = 8;
+
+// Status codes written to the workspace status word (values of gpz_status).
+constexpr uint32_t kStCorrupt = 3;
+constexpr uint32_t kStTimeout = 6;
+
+struct FieldParams {
+    float eb;    // RN32(eb), stored in the header
+    float s;     // quantisation step RN32(eb * 63/32)
+    float inv;   // RN32(1 / s): the precomputed reciprocal (Section 5.1)
+    float ebchk; // RD32(eb * (1 - 2^-22)): the verification threshold
+};
+
+// Argument blocks (passed by value).
+struct RangeArgs {
+    const float* fields[kMaxFields];
+    uint64_t n;
+    int F;
+    int vec_ok;                 // every field pointer 16-byte aligned
+    double rel[kMaxFields];
+    float2* partials;           // [gridDim.x][F] (min, max)
+    uint32_t* done_counter;
+    FieldParams* d_params;      // out
+};
+
+struct QseArgs {
+    const float* fields[kMaxFields];
+    uint64_t n;
+    uint32_t nblocks;
+    int F;
+    int G;
+    int bulk_ok;                // every field pointer 16-byte aligned: stage tiles with bulk copies
+    FieldParams params[kMaxFields];
+    const FieldParams* d_params; // device constants (relative bound) or nullptr
+    uint32_t* temp;             // [nblocks][slot_words]
+    uint32_t slot_words;
+    uint32_t* sizes;            // [nblocks] words per block
+    uint32_t* perm;             // [n] or nullptr
+    uint32_t* status;
+    uint32_t tile_bytes;        // per-warp tile bytes
+    uint32_t warp_bytes;        // per-warp shared memory bytes
+};
+
+struct ScanArgs {
+    const uint32_t* sizes;      // [nblocks]
+    uint32_t nblocks;
+    uint32_t* table;            // [nblocks + 1] in the stream
+    unsigned long long* tile_state; // [ntiles], zeroed
+    uint32_t* tile_counter;     // zeroed
+    uint32_t* status;
+};
+
+struct CompactArgs {
+    const uint32_t* temp;
+    uint32_t slot_words;
+    const uint32_t* sizes;
+    const uint32_t* table;      // [nblocks + 1]
+    uint32_t* stream;           // stream base
+    uint32_t payload_start;     // words
+    uint32_t nblocks;
+    uint64_t n;
+    int F;
+    int G;
+    int mode;
+    FieldParams params[kMaxFields];
+    const FieldParams* d_params;
+    unsigned long long* d_out_size; // nullable
+};
+
+struct DecArgs {
+    const uint32_t* stream;
+    uint64_t total_words;
+    float* out[kMaxFields];
+    uint64_t n;
+    int F;
+    uint32_t nblocks;
+    uint32_t* status;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
+    atomicCAS(st, 0u, code);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t lanemask_le() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int pad_idx(int j) { return (j >> 5) * kRow + (j & 31); }
+
+__device__ __forceinline__ uint32_t bit_width(uint32_t v) { return 32u - (uint32_t)__clz(v); }
+
+__device__ __forceinline__ uint32_t ceil_words(uint32_t bits) { return (bits + 31u) >> 5; }
+
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+    return __reduce_max_sync(0xffffffffu, v);
+}
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+    return __reduce_add_sync(0xffffffffu, v);
+}
+
+__device__ __forceinline__ float warp_min_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Inclusive prefix sum over the warp.
+__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Inclusive prefix maximum over the warp (signed).
+__device__ __forceinline__ int warp_incl_max(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = max(v, t);
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------- mbarrier + bulk copy (sm_90+)
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM cycles (about a second), records
+// kStTimeout, and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) {
+            set_status(status, kStTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// One-dimensional bulk copy global -> shared, completing on the mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------- acquire / release (look-back scan)
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- launch wrappers (defined in the .cu files)
+
+cudaError_t launch_range(const RangeArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
+cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);
+uint32_t qse_warp_bytes(int F, uint32_t* tile_bytes);
+
+}  // namespace gpz

@@ -1,0 +1,222 @@
+"""Python binding of libgpz (include/gpz.h): the same entry points, argument
+marshalling only.  Every step of compression and decompression runs in the
+library's CUDA kernels; this module only turns torch tensors into pointers
+and streams into handles.
+
+There is no fallback: if libgpz.so has not been built, importing this module
+raises.  Build it with ``python -c "import __graft_entry__ as g; g.build()"``
+or ``python paper_2508_10305_gb300/build.py``.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpz.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+EB_ABS, EB_REL = 0, 1
+MAX_FIELDS = 8
+BLOCK = 1024
+
+
+class gpz_params(C.Structure):
+    _fields_ = [("mode", C.c_int), ("n_fields", C.c_int), ("seg_bits", C.c_int),
+                ("eb", C.c_double * MAX_FIELDS)]
+
+
+class GpzError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, gpz_status_str(status), status))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgpz.so is not built (%s); run paper_2508_10305_gb300/build.py" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P, u64, vp = C.POINTER, C.c_uint64, C.c_void_p
+    L.gpz_bound_size.argtypes = [u64, C.c_int]
+    L.gpz_bound_size.restype = u64
+    L.gpz_compress_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_compress_workspace_size.restype = u64
+    L.gpz_decompress_workspace_size.argtypes = []
+    L.gpz_decompress_workspace_size.restype = u64
+    L.gpz_compress.argtypes = [P(vp), u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp, u64, vp]
+    L.gpz_compress.restype = C.c_int
+    L.gpz_decompress.argtypes = [vp, u64, P(vp), C.c_int, u64, vp, u64, vp]
+    L.gpz_decompress.restype = C.c_int
+    L.gpz_sync_status.argtypes = [vp, vp]
+    L.gpz_sync_status.restype = C.c_int
+    L.gpz_inspect.argtypes = [vp, u64, P(u64), P(C.c_int), P(C.c_int), P(C.c_int)]
+    L.gpz_inspect.restype = C.c_int
+    L.gpz_status_str.argtypes = [C.c_int]
+    L.gpz_status_str.restype = C.c_char_p
+    L.gpz_set_stage_timing.argtypes = [C.c_int]
+    L.gpz_set_stage_timing.restype = None
+    L.gpz_stage_times.argtypes = [P(C.c_char_p), P(C.c_float), C.c_int]
+    L.gpz_stage_times.restype = C.c_int
+    L.gpz_launch_count.argtypes = [C.c_int]
+    L.gpz_launch_count.restype = u64
+    return L
+
+
+lib = _load()
+
+
+# ----------------------------------------------------------------------------- raw entry points
+
+def gpz_bound_size(n, n_fields):
+    return int(lib.gpz_bound_size(n, n_fields))
+
+
+def gpz_compress_workspace_size(n, n_fields):
+    return int(lib.gpz_compress_workspace_size(n, n_fields))
+
+
+def gpz_decompress_workspace_size():
+    return int(lib.gpz_decompress_workspace_size())
+
+
+def gpz_status_str(status):
+    return lib.gpz_status_str(status).decode()
+
+
+def gpz_set_stage_timing(enable):
+    lib.gpz_set_stage_timing(1 if enable else 0)
+
+
+def gpz_stage_times(max_stages=8):
+    names = (C.c_char_p * max_stages)()
+    ms = (C.c_float * max_stages)()
+    k = lib.gpz_stage_times(names, ms, max_stages)
+    return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+
+def gpz_launch_count(reset=False):
+    return int(lib.gpz_launch_count(1 if reset else 0))
+
+
+def gpz_inspect(header_bytes):
+    """Parse a stream header held in host memory (bytes-like, >= 64 bytes)."""
+    buf = (C.c_uint8 * len(header_bytes)).from_buffer_copy(bytes(header_bytes))
+    n, F, G, mode = C.c_uint64(), C.c_int(), C.c_int(), C.c_int()
+    st = lib.gpz_inspect(C.cast(buf, C.c_void_p), len(header_bytes), C.byref(n), C.byref(F), C.byref(G),
+                         C.byref(mode))
+    if st != OK:
+        raise GpzError(st, "gpz_inspect")
+    return dict(n=n.value, n_fields=F.value, seg_bits=G.value, mode=mode.value)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def make_params(n_fields, eb, mode=EB_ABS, seg_bits=3):
+    p = gpz_params()
+    p.mode, p.n_fields, p.seg_bits = mode, n_fields, seg_bits
+    ebs = list(eb) if hasattr(eb, "__len__") else [eb] * n_fields
+    if len(ebs) != n_fields:
+        raise ValueError("need one error bound per field")
+    for f, e in enumerate(ebs):
+        p.eb[f] = float(e)
+    return p
+
+
+def gpz_compress(fields, n, params, out, out_capacity, d_out_size=None, h_out_size=None, perm=None, ws=None,
+                 ws_size=0, stream=None):
+    """Mirror of the C entry point.  fields: list of CUDA float32 tensors (or a
+    2-D [F, n] tensor); out/d_out_size/perm/ws: CUDA tensors or None;
+    h_out_size: a ctypes.c_uint64 or None.  Returns the status code."""
+    if isinstance(fields, torch.Tensor):
+        fields = [fields[f] for f in range(fields.shape[0])]
+    return lib.gpz_compress(_ptr_array(fields), n, C.byref(params), out.data_ptr(), out_capacity,
+                            d_out_size.data_ptr() if d_out_size is not None else None,
+                            C.byref(h_out_size) if h_out_size is not None else None,
+                            perm.data_ptr() if perm is not None else None,
+                            ws.data_ptr() if ws is not None else None, ws_size, _stream_handle(stream))
+
+
+def gpz_decompress(stream_buf, in_size, fields, n_fields, n, ws=None, ws_size=0, stream=None):
+    """Mirror of the C entry point; fields: list of CUDA float32 tensors or a 2-D tensor."""
+    if isinstance(fields, torch.Tensor):
+        fields = [fields[f] for f in range(fields.shape[0])]
+    return lib.gpz_decompress(stream_buf.data_ptr(), in_size, _ptr_array(fields), n_fields, n,
+                              ws.data_ptr() if ws is not None else None, ws_size, _stream_handle(stream))
+
+
+def gpz_sync_status(ws, stream=None):
+    return lib.gpz_sync_status(ws.data_ptr(), _stream_handle(stream))
+
+
+# ----------------------------------------------------------------------------- convenience wrappers
+
+class Compressor:
+    """Holds the device buffers for one (n, F) shape so that repeated calls
+    allocate nothing: out (bound size), workspace, size word and optional
+    permutation."""
+
+    def __init__(self, n, n_fields, eb, mode=EB_ABS, seg_bits=3, want_perm=False, device=None):
+        device = device or torch.device("cuda")
+        self.n, self.F = n, n_fields
+        self.params = make_params(n_fields, eb, mode, seg_bits)
+        self.capacity = gpz_bound_size(n, n_fields)
+        self.out = torch.empty(max(self.capacity, 16), dtype=torch.uint8, device=device)
+        self.ws_size = gpz_compress_workspace_size(n, n_fields)
+        self.ws = torch.empty(max(self.ws_size, 256), dtype=torch.uint8, device=device)
+        self.d_size = torch.zeros(1, dtype=torch.int64, device=device)
+        self.perm = torch.empty(max(n, 1), dtype=torch.int32, device=device) if want_perm else None
+
+    def __call__(self, fields, stream=None, sync=True):
+        """Compress; returns the stream size in bytes (sync=True) or None."""
+        h = C.c_uint64(0) if sync else None
+        st = gpz_compress(fields, self.n, self.params, self.out, self.capacity, self.d_size, h,
+                          self.perm, self.ws, self.ws_size, stream)
+        if st != OK:
+            raise GpzError(st, "gpz_compress")
+        return h.value if sync else None
+
+
+class Decompressor:
+    def __init__(self, n, n_fields, device=None):
+        device = device or torch.device("cuda")
+        self.n, self.F = n, n_fields
+        self.out = torch.empty((n_fields, max(n, 1)), dtype=torch.float32, device=device)
+        self.ws = torch.zeros(gpz_decompress_workspace_size(), dtype=torch.uint8, device=device)
+
+    def __call__(self, stream_buf, size, stream=None, check=True):
+        st = gpz_decompress(stream_buf, size, [self.out[f] for f in range(self.F)], self.F, self.n, self.ws,
+                            self.ws.numel(), stream)
+        if st != OK:
+            raise GpzError(st, "gpz_decompress")
+        if check:
+            st = gpz_sync_status(self.ws, stream)
+            if st != OK:
+                raise GpzError(st, "gpz_decompress (device)")
+        return self.out[:, :self.n]
+
+
+def compress(x, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
+    """One-shot: x is a CUDA float32 tensor [F, n].  Returns (stream bytes as a
+    CUDA uint8 tensor of the exact size, perm or None)."""
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    F, n = x.shape
+    c = Compressor(n, F, eb, mode, seg_bits, want_perm, x.device)
+    size = c([x[f] for f in range(F)], stream)
+    return c.out[:size], (c.perm[:n] if want_perm else None)
+
+
+def decompress(stream_buf, n_fields, n, stream=None):
+    d = Decompressor(n, n_fields, stream_buf.device)
+    return d(stream_buf, stream_buf.numel(), stream).clone()

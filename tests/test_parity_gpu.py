@@ -1,0 +1,244 @@
+"""GPU (sm_103a, through the C ABI) against the CPU oracle, bit for bit:
+the compressed stream, the permutation and the decompressed fp32 values.
+
+Small cases are compared whole (sizes spanning several blocks and a ragged
+tail, every field count, segment width, bound mode and distribution kind).
+The full-size workloads -- 2^26 x 6 cosmology-like with a relative bound
+(the benchmark's workload, in the benchmark's launch configuration) and
+2e8 x 3 LiDAR-like with an absolute bound -- are compared on sampled blocks,
+which the oracle encodes and decodes one by one, plus properties that hold at
+any size (every value within eb, the offset table, the size bound)."""
+import numpy as np
+import pytest
+import torch
+
+from tests import _golden as gold
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpz():
+    from paper_2508_10305_gb300 import build
+    build.build()
+    from paper_2508_10305_gb300 import gpz as g
+    return g
+
+
+def run_gpu(gpz, x, eb, mode, G, offset=0):
+    """Compress + decompress x [F, n] on the GPU; `offset` shifts every field
+    by that many floats from a 16-byte boundary (exercises the plain-load
+    staging path)."""
+    F, n = x.shape
+    buf = torch.zeros((F, n + 8), dtype=torch.float32, device="cuda")
+    buf[:, offset:offset + n] = torch.from_numpy(x).cuda()
+    fields = [buf[f, offset:offset + n] for f in range(F)]
+    c = gpz.Compressor(n, F, eb, mode, G, want_perm=True)
+    size = c(fields)
+    stream = c.out[:size].clone()
+    d = gpz.Decompressor(n, F)
+    out = d(stream, size)
+    torch.cuda.synchronize()
+    return stream.cpu().numpy(), c.perm[:n].cpu().numpy().astype(np.uint32), out.cpu().numpy().copy()
+
+
+def assert_parity(gpz, oracle, x, eb, mode=0, G=3, offset=0):
+    F, n = x.shape
+    s, p, o = run_gpu(gpz, x, eb, mode, G, offset)
+    rs, rp = oracle.compress(x, eb, mode, G)
+    if s.size != rs.size or not np.array_equal(s, rs):
+        w, rw = s.view(np.uint32), rs.view(np.uint32)
+        m = min(w.size, rw.size)
+        first = int(np.argmax(w[:m] != rw[:m])) if np.any(w[:m] != rw[:m]) else m
+        raise AssertionError("stream differs: sizes %d vs %d, first differing word %d" % (s.size, rs.size, first))
+    assert np.array_equal(p, rp), "permutation differs"
+    ro = oracle.decompress(rs, F, n)
+    assert np.array_equal(o.view(np.uint32), ro.view(np.uint32)), "decompressed values differ"
+    return s, p, o
+
+
+# ----------------------------------------------------------------------------- fixtures
+
+@pytest.mark.parametrize("name", [n for n in gold.all_names() if "out" in gold.load(n) or "stream_words" in gold.load(n)])
+def test_golden(gpz, oracle, name):
+    g = gold.load(name)
+    s, p, o = assert_parity(gpz, oracle, g["fields"], g["eb"], g["mode"], g["seg_bits"])
+    if "stream_words" in g:
+        assert s.view(np.uint32).tolist() == g["stream_words"].tolist()
+    if "block_words" in g:
+        F = g["n_fields"]
+        assert s.view(np.uint32)[16 + 2 * F + 2:].tolist() == g["block_words"].tolist()
+    if "out" in g:
+        assert o.view(np.uint32).tolist() == g["out"].view(np.uint32).tolist()
+
+
+# ----------------------------------------------------------------------------- randomised sweep
+
+def gen(kind, F, n, rng):
+    if kind == "uniform":
+        return (rng.random((F, n)) * 256).astype(np.float32)
+    if kind == "clustered":
+        c = rng.random((F, 30)) * 200
+        lab = np.sort(rng.integers(0, 30, n))
+        return (c[:, lab] + rng.standard_normal((F, n)) * rng.uniform(0.05, 3.0)).astype(np.float32)
+    if kind == "lidar":
+        base = np.array([9000.0, 5000.0, 120.0, 3.0, 1.0, 0.5, 7.0, 2.0])[:F, None]
+        walk = np.cumsum(rng.standard_normal((F, n)) * 0.3, axis=1)
+        return (base + walk).astype(np.float32)
+    if kind == "mixed":
+        scale = np.array([1e3, 1e-2, 1.0, 300.0, 5.0, 1e4, 0.1, 50.0])[:F, None]
+        return (rng.standard_normal((F, n)) * scale).astype(np.float32)
+    raise ValueError(kind)
+
+
+SIZES = [1, 2, 31, 32, 33, 1000, 1023, 1024, 1025, 2047, 3000, 4113, 5000]
+CASES = []
+_r = np.random.default_rng(2024)
+for _i in range(48):
+    CASES.append((int(_r.choice(SIZES)), int(_r.choice([1, 2, 3, 4, 6, 8])), int(_r.integers(0, 4)),
+                  int(_r.integers(0, 2)), str(_r.choice(["uniform", "clustered", "lidar", "mixed"])),
+                  float(_r.choice([1e-1, 1e-2, 1e-3, 1e-4])), int(_r.integers(0, 10**6))))
+
+
+@pytest.mark.parametrize("n,F,G,mode,kind,eb,seed", CASES)
+def test_random_parity(gpz, oracle, n, F, G, mode, kind, eb, seed):
+    rng = np.random.default_rng(seed)
+    x = gen(kind, F, n, rng)
+    assert_parity(gpz, oracle, x, eb, mode, G)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_unaligned_fields(gpz, oracle, offset):
+    rng = np.random.default_rng(offset)
+    x = gen("clustered", 3, 4100, rng)
+    assert_parity(gpz, oracle, x, 1e-3, 0, 3, offset=offset)
+
+
+def test_wide_records(gpz, oracle):
+    """Records wider than 64 bits take the field-by-field packer."""
+    rng = np.random.default_rng(7)
+    x = (rng.random((8, 3000)) * 1000).astype(np.float32)
+    s, _, _ = assert_parity(gpz, oracle, x, 1e-3, 0, 3)
+    assert s.size < x.nbytes
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_empty(gpz, oracle):
+    x = np.zeros((3, 0), np.float32)
+    c = gpz.Compressor(0, 3, 1e-2)
+    dummy = [torch.zeros(4, device="cuda") for _ in range(3)]
+    size = c(dummy)
+    rs, _ = oracle.compress(x, 1e-2)
+    assert size == rs.size and np.array_equal(c.out[:size].cpu().numpy(), rs)
+
+
+def test_nonfinite_blocks(gpz, oracle):
+    x = (np.arange(3 * 3000, dtype=np.float32).reshape(3, 3000) * 0.01)
+    x[0, 7] = np.nan
+    x[1, 1500] = np.inf
+    x[2, 2999] = -np.inf
+    assert_parity(gpz, oracle, x, 1e-3)
+
+
+def test_out_of_range_and_coarse(gpz, oracle):
+    y = np.array([[0.0, 3e38, -3e38] * 400], np.float32)
+    assert_parity(gpz, oracle, y, 1e-6)
+    z = (np.float32(20000.0) + np.arange(2048, dtype=np.float32) * np.float32(0.37))[None, :]
+    assert_parity(gpz, oracle, z.astype(np.float32), 1e-3)
+
+
+def test_constant_and_signed_zero(gpz, oracle):
+    x = np.full((4, 2500), 7.25, np.float32)
+    x[0] = np.linspace(0, 1, 2500, dtype=np.float32)
+    x[3, ::2] = -0.0
+    x[3, 1::2] = 0.0
+    assert_parity(gpz, oracle, x, 1e-4)
+    assert_parity(gpz, oracle, x, 1e-4, mode=1)
+
+
+def test_incompressible_goes_raw(gpz, oracle):
+    rng = np.random.default_rng(1)
+    x = (rng.random((3, 2048)) * 1e6).astype(np.float32)
+    s, _, _ = assert_parity(gpz, oracle, x, 1e-7)
+    assert s.size == oracle.bound_size(2048, 3)
+
+
+def test_repeatable(gpz):
+    rng = np.random.default_rng(3)
+    x = gen("clustered", 6, 9000, rng)
+    a = run_gpu(gpz, x, 1e-3, 1, 3)
+    b = run_gpu(gpz, x, 1e-3, 1, 3)
+    assert all(np.array_equal(u, v) for u, v in zip(a, b))
+
+
+# ----------------------------------------------------------------------------- full-size workloads
+
+def _full_size_check(gpz, oracle, x_dev, eb, mode, G, n_samples, seed):
+    F, n = x_dev.shape
+    c = gpz.Compressor(n, F, eb, mode, G, want_perm=True)
+    size = c([x_dev[f] for f in range(F)])
+    assert size <= gpz.gpz_bound_size(n, F)
+    stream = c.out[:size]
+    d = gpz.Decompressor(n, F)
+    out = d(stream, size)
+    perm = c.perm[:n].long()
+    # every value within its bound (on the device, in double)
+    x = x_dev.cpu().numpy()
+    if mode == 1:
+        params = [oracle.params_rel(eb, x[f]) for f in range(F)]
+    else:
+        params = [oracle.params_abs(eb) for _ in range(F)]
+    for f in range(F):
+        err = (x_dev[f][perm].double() - out[f].double()).abs().max().item()
+        bound = float(np.float32(params[f].eb)) if mode == 1 else eb
+        assert err <= bound, (f, err, bound)
+    # header constants equal the oracle's
+    w = stream.cpu().numpy().view(np.uint32)
+    for f in range(F):
+        assert w[16 + 2 * f] == np.float32(params[f].eb).view(np.uint32)
+        assert w[16 + 2 * f + 1] == np.float32(params[f].s).view(np.uint32)
+    nb = (n + 1023) // 1024
+    table = w[16 + 2 * F:16 + 2 * F + nb + 1].astype(np.int64)
+    assert table[0] == 0 and np.all(np.diff(table) >= 1) and table[-1] == w[9]
+    payload = 16 + 2 * F + nb + 1
+    # sampled blocks: oracle encodes and decodes them one by one
+    rng = np.random.default_rng(seed)
+    blocks = np.unique(np.concatenate([[0, nb - 1], rng.integers(0, nb, n_samples)]))
+    pm = c.perm[:n].cpu().numpy().astype(np.uint32)
+    o = out.cpu().numpy()
+    steps = np.array([params[f].s for f in range(F)], np.float32)
+    for b in blocks:
+        lo, hi = b * 1024, min(n, b * 1024 + 1024)
+        ref_words, ref_perm = oracle.encode_block(x[:, lo:hi], G, params)
+        got = w[payload + table[b]:payload + table[b + 1]]
+        assert np.array_equal(got, ref_words), "block %d differs" % b
+        assert np.array_equal(pm[lo:hi] - lo, ref_perm), "block %d permutation differs" % b
+        ref_out = oracle.decode_block(ref_words, F, hi - lo, G, steps)
+        assert np.array_equal(o[:, lo:hi].view(np.uint32), ref_out.view(np.uint32)), "block %d output" % b
+    return size
+
+
+def test_small_configuration_whole(gpz, oracle):
+    """1e6 particles uniform in [0,256)^3, seed 0, eb = 1e-2: whole stream."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.uniform_box(1_000_000, seed=0)
+    s, p, o = assert_parity(gpz, oracle, x, 1e-2, 0, 3)
+    err = np.abs(x[:, p].astype(np.float64) - o.astype(np.float64)).max()
+    assert err <= 1e-2
+
+
+def test_cosmology_64m_sampled(gpz, oracle):
+    """2^26 particles x 6 fields, relative bound 1e-4 (the benchmark workload)."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.cosmology(1 << 26, seed=2, device="cuda")
+    size = _full_size_check(gpz, oracle, x, 1e-4, 1, 3, n_samples=300, seed=1)
+    assert x.numel() * 4 / size > 2.0
+
+
+def test_lidar_200m_sampled(gpz, oracle):
+    """2e8 points x 3, absolute bound 1e-3 m, scan order."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.lidar(200_000_000, seed=3, device="cuda")
+    size = _full_size_check(gpz, oracle, x, 1e-3, 0, 3, n_samples=300, seed=2)
+    assert x.numel() * 4 / size > 2.0
