@@ -1,0 +1,426 @@
+"""GPZ on GB300: compress + decompress throughput on the cosmology-like
+snapshot (2^26 particles x 6 fp32 fields, relative error bound 1e-4 of each
+field's range, segment bits G = 3).
+
+A step is one round trip through the whole hot path: gpz_compress (range
+pass, fused quantise/sort/encode, look-back scan, compaction) then
+gpz_decompress, with the input already resident in HBM.  The metric is GB/s
+of input per round trip: 4*n*F bytes / (compress time + decompress time),
+summed over ranks (weak scaling: every rank compresses its own snapshot; no
+collective touches the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line on rank 0.  The reference arm (--impl reference) times the
+plain single-threaded CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Compress+decompress GB/s (% HBM roofline) and ratio; served p50/p99 vs plain"
+N_PARTICLES = 1 << 26
+N_FIELDS = 6
+REL_EB = 1e-4
+SEG_BITS = 3
+SEED = 2
+WORKLOAD = "cosmology-like snapshot: 2^26 particles x 6 fp32 (x,y,z,vx,vy,vz), 20,000 halos + 30% background, relative eb 1e-4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpz", choices=["gpz", "reference"])
+    ap.add_argument("--n", type=int, default=N_PARTICLES, help="particles (profiling runs only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- measurement helpers
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary of `kernel`, or
+    None when the kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel)
+    if not os.path.exists(path):
+        return None
+    info = {}
+    for line in open(path):
+        if ":" in line:
+            k, _, v = line.partition(":")
+            info[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2508_10305_gb300", "csrc", info.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if digest != info.get("source_sha256"):
+        return None
+    try:
+        return float(info["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            ident = ["-i", "GPU-" + uuid if not uuid.startswith("GPU-") else uuid]
+        except Exception:
+            ident = []
+        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"] + ident
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(n, rank, device):
+    from paper_2508_10305_gb300 import synth
+    return synth.cosmology(n, seed=SEED + rank, device=device)
+
+
+def psnr_and_error(x, out, perm, ebs):
+    """Aggregate PSNR (Section 3.1: NRMSE per field, then -20 log10 of the
+    root mean square) and max |x - x_hat| / eb, on the device in double."""
+    import torch
+    nrmse2, worst = [], 0.0
+    for f in range(x.shape[0]):
+        xs = x[f][perm].double()
+        d = xs - out[f].double()
+        rng = (xs.max() - xs.min()).item()
+        rmse = torch.sqrt(torch.mean(d * d)).item()
+        nrmse2.append((rmse / rng) ** 2 if rng > 0 else 0.0)
+        worst = max(worst, d.abs().max().item() / ebs[f])
+    psnr = -20.0 * np.log10(np.sqrt(np.mean(nrmse2))) if np.mean(nrmse2) > 0 else float("inf")
+    return psnr, worst
+
+
+def cpu_oracle_sample(x_host_blocks, n_fields):
+    """Time the CPU oracle (single thread) on a host sample; returns GB/s of input per round trip."""
+    from oracle import gpz_oracle
+    gpz_oracle.lib()
+    t0 = time.perf_counter()
+    stream, _ = gpz_oracle.compress(x_host_blocks, REL_EB, 1, SEG_BITS, want_perm=False)
+    t1 = time.perf_counter()
+    gpz_oracle.decompress(stream, n_fields, x_host_blocks.shape[1])
+    t2 = time.perf_counter()
+    return x_host_blocks.nbytes / (t2 - t0) / 1e9, t1 - t0, t2 - t1
+
+
+def host_sample(x_dev, every=4):
+    """Every `every`-th 1024-particle block of the device workload, on the host."""
+    import torch
+    n = x_dev.shape[1]
+    nb = n // 1024
+    idx = torch.arange(0, nb, every, device=x_dev.device)
+    sel = (idx[:, None] * 1024 + torch.arange(1024, device=x_dev.device)[None, :]).reshape(-1)
+    return x_dev[:, sel].cpu().numpy(), sel.numel()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, single-threaded on the host, on the same
+    workload, metric and unit.  Each step is a bounded sample of whole
+    1024-particle blocks spread over the snapshot (rotating offset), sized so
+    that all steps together take about 90 s."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2508_10305_gb300 import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    x = synth.cosmology(args.n, seed=SEED, device=dev)
+    nb = args.n // 1024
+    per_step = int(max(8, min(nb, 90.0 * 1.4e6 / max(1, args.steps) / 1024)))
+    stride = max(1, nb // per_step)
+
+    def sample(i):
+        blocks = torch.arange(i % stride, nb, stride, device=x.device)[:per_step]
+        sel = (blocks[:, None] * 1024 + torch.arange(1024, device=x.device)[None, :]).reshape(-1)
+        return x[:, sel].cpu().numpy()
+
+    for i in range(args.warmup):
+        cpu_oracle_sample(sample(i)[:, :1 << 14], N_FIELDS)
+    total, nbytes = 0.0, 0
+    for i in range(args.steps):
+        s = sample(i)
+        _, tc, td = cpu_oracle_sample(s, N_FIELDS)
+        total += tc + td
+        nbytes += s.nbytes
+    value = nbytes / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "fields": N_FIELDS, "eb_mode": "rel", "eb": REL_EB,
+                   "seg_bits": SEG_BITS},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step %d whole 1024-particle blocks (every %dth, rotating offset) x 6 "
+                                   "fields; single-threaded C++ oracle compress + decompress; relative eb over "
+                                   "the sample" % (per_step, stride)},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpz(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2508_10305_gb300 import build
+    build.build()
+    from paper_2508_10305_gb300 import gpz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, F = args.n, N_FIELDS
+    x = make_workload(n, rank, dev)
+    fields = [x[f] for f in range(F)]
+    comp = gpz.Compressor(n, F, REL_EB, gpz.EB_REL, SEG_BITS, want_perm=False, device=dev)
+    dec = gpz.Decompressor(n, F, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # one checked round trip with the permutation: ratio, PSNR, error bound
+    chk = gpz.Compressor(n, F, REL_EB, gpz.EB_REL, SEG_BITS, want_perm=True, device=dev)
+    size = chk(fields)
+    out = dec(chk.out, size)
+    perm = chk.perm[:n].long()
+    hdr = chk.out[:4 * (16 + 2 * F)].cpu().numpy().view(np.uint32)
+    ebs = [float(hdr[16 + 2 * f].view(np.float32)) for f in range(F)]
+    psnr, worst = psnr_and_error(x, out, perm, ebs)
+    ratio = x.numel() * 4 / size
+    del chk, perm, out
+    torch.cuda.empty_cache()
+
+    def step():
+        comp(fields, stream, sync=False)
+        dec(comp.out, size, stream, check=False)
+
+    # the stream size is data-dependent but fixed for this input: decompress
+    # reads exactly `size` bytes of the compressor's output buffer
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for ws in (comp.ws, dec.ws):
+        st = gpz.gpz_sync_status(ws)
+        if st != gpz.OK:
+            raise gpz.GpzError(st, "warm-up")
+
+    gpz.gpz_set_stage_timing(True)
+    gpz.gpz_stage_times()  # clear
+    gpz.gpz_launch_count(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gpz.gpz_launch_count()
+    stages = gpz.gpz_stage_times()
+    gpz.gpz_set_stage_timing(False)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    for ws in (comp.ws, dec.ws):
+        st = gpz.gpz_sync_status(ws)
+        if st != gpz.OK:
+            raise gpz.GpzError(st, "timed region")
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    in_bytes = 4.0 * n * F
+    value = world * in_bytes * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    comp_ms = sum(stages[k][0] for k in ("range", "qse", "scan", "compact") if k in stages) / args.steps
+    dec_ms = stages.get("decompress", (0.0, 1))[0] / args.steps
+
+    # roofline of each kernel: algorithmic bytes per launch / mean launch time
+    peak, peak_kind = load_peaks()
+    payload_bytes = size - 4 * (16 + 2 * F + (n + 1023) // 1024 + 1)
+    algo = {
+        "range": in_bytes,                       # one read of every field
+        "qse": in_bytes + payload_bytes,         # read the input, write the encoded blocks
+        "scan": 8.0 * ((n + 1023) // 1024),      # read sizes, write offsets
+        "compact": 2.0 * payload_bytes,          # read temporary blocks, write the stream
+        "decompress": size + in_bytes,           # read the stream, write every value
+    }
+    kernels = {}
+    for k, (tot, cnt) in stages.items():
+        if cnt == 0:
+            continue
+        mean_s = tot / cnt / 1e3
+        ach = algo.get(k, 0.0) / mean_s / 1e9
+        kernels[k] = {"mean_ms": 1e3 * mean_s, "launches": cnt, "algorithmic_bytes": algo.get(k),
+                      "achieved_gbs": ach, "frac": ach / peak}
+    dom = max(kernels, key=lambda k: kernels[k]["mean_ms"])
+    step_bytes = sum(algo[k] for k in ("range", "qse", "decompress")) + size  # stream written once by compaction
+    roofline = {"bound": "hbm", "kernel": "gpz_%s_kernel" % dom, "achieved": kernels[dom]["achieved_gbs"],
+                "peak": peak, "unit": "GB/s", "frac": kernels[dom]["frac"],
+                "traffic": recorded_traffic(dom), "peak_source": peak_kind,
+                "note": "frac of %s copy bandwidth" % peak_kind}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "fields": F, "eb_mode": "rel", "eb": REL_EB,
+                   "seg_bits": SEG_BITS, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs (%.2f GB) larger than L2 (129 MB); no flush" % (in_bytes / 1e9)},
+        "compress_gbs": in_bytes / (comp_ms / 1e3) / 1e9 if comp_ms else None,
+        "decompress_gbs": in_bytes / (dec_ms / 1e3) / 1e9 if dec_ms else None,
+        "ratio": ratio, "psnr_db": psnr, "max_err_over_eb": worst, "stream_bytes": size,
+        "step_roofline_frac": (step_bytes / (elapsed_ms / args.steps / 1e3) / 1e9) / peak,
+        "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the public API with host buffers: H2D input ->
+    # compress -> D2H stream -> H2D stream -> decompress -> D2H output
+    if not args.no_e2e:
+        h_in = torch.empty((F, n), dtype=torch.float32, pin_memory=True)
+        h_in.copy_(x)
+        h_stream = torch.empty(comp.capacity, dtype=torch.uint8, pin_memory=True)
+        h_out = torch.empty((F, n), dtype=torch.float32, pin_memory=True)
+        d_in = torch.empty_like(x)
+        d_stream = torch.empty_like(comp.out)
+
+        def e2e_step():
+            d_in.copy_(h_in, non_blocking=True)
+            sz = comp([d_in[f] for f in range(F)], stream, sync=True)
+            h_stream[:sz].copy_(comp.out[:sz], non_blocking=True)
+            d_stream[:sz].copy_(h_stream[:sz], non_blocking=True)
+            o = dec(d_stream, sz, stream, check=False)
+            h_out.copy_(o, non_blocking=True)
+            return sz
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k = max(3, min(20, args.steps // 10))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            sz = e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        e = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e, op=dist.ReduceOp.MAX)
+        dt = float(e.item())
+        result["e2e"] = {"value": world * in_bytes / dt / 1e9, "unit": "GB/s",
+                         "h2d_bytes_per_step": int(in_bytes + sz), "d2h_bytes_per_step": int(in_bytes + sz + 8),
+                         "ms_per_step": 1e3 * dt}
+        del h_in, h_stream, h_out, d_in, d_stream
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, npart = host_sample(x, every=4)
+        gbs, tc, td = cpu_oracle_sample(sample, F)
+        result["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                  "sample": "every 4th 1024-particle block (%d particles x 6 fields), one "
+                                            "compress + decompress, single-threaded C++ oracle, relative eb "
+                                            "over the sample; %.1f s" % (npart, tc + td)}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpz(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -135,11 +135,14 @@ gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_f
 const char* gpz_status_str(gpz_status s);
 
 /* Measurement hooks.  When enabled (per process), every later call records
- * CUDA events on its stream around each of its kernels.  gpz_stage_times
- * synchronises on the last recorded event and writes, for the most recent
- * call, up to max stage names and elapsed milliseconds; it returns the count. */
+ * CUDA events on its stream before its first kernel and after each kernel
+ * (up to 8192 events between reads).  gpz_stage_times synchronises on the
+ * last recorded event, writes up to max stage names ("range", "qse", "scan",
+ * "compact", "decompress") with their summed elapsed milliseconds and launch
+ * counts since the previous read, returns the number of stages, and clears
+ * the log.  names[] receives static strings. */
 void gpz_set_stage_timing(int enable);
-int gpz_stage_times(const char** names, float* ms, int max);
+int gpz_stage_times(const char** names, float* total_ms, int* launches, int max);
 
 /* Kernel launches enqueued by this process since the last reset. */
 uint64_t gpz_launch_count(int reset);

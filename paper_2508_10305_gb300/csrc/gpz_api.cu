@@ -70,41 +70,54 @@ FieldParams finalise(double eb) {
 }
 
 // ---------------------------------------------------------------- stage timing
+//
+// When enabled, each call records one event on its stream before its first
+// kernel and one after each kernel, from a pool; gpz_stage_times resolves
+// the logged pairs into per-stage totals and recycles the pool.
+
+constexpr int kEventPool = 8192;
 
 struct StageTimer {
     std::mutex mu;
     bool enabled = false;
-    int count = 0;
-    const char* names[8] = {};
-    cudaEvent_t ev[9] = {};
     bool created = false;
+    cudaEvent_t ev[kEventPool] = {};
+    int used = 0;
+    struct Span {
+        const char* name;
+        int a, b;
+    };
+    Span spans[kEventPool];
+    int nspans = 0;
 } g_timer;
 
 struct Recorder {
-    bool on;
+    bool on = false;
     cudaStream_t s;
-    int k = 0;
-    Recorder(cudaStream_t stream) : s(stream) {
+    int last = -1;
+    explicit Recorder(cudaStream_t stream) : s(stream) {}
+    // Start of the call's first kernel (after its memsets).
+    void begin() {
         std::lock_guard<std::mutex> g(g_timer.mu);
-        on = g_timer.enabled;
-        if (on) {
-            if (!g_timer.created) {
-                for (auto& e : g_timer.ev) cudaEventCreate(&e);
-                g_timer.created = true;
-            }
-            g_timer.count = 0;
-            cudaEventRecord(g_timer.ev[0], s);
+        if (!g_timer.enabled) return;
+        if (!g_timer.created) {
+            for (auto& e : g_timer.ev) cudaEventCreate(&e);
+            g_timer.created = true;
         }
+        if (g_timer.used + 8 >= kEventPool) return;  // pool full until the next read
+        on = true;
+        last = g_timer.used++;
+        cudaEventRecord(g_timer.ev[last], s);
     }
     void mark(const char* name) {
         ++g_launches;
         if (!on) return;
         std::lock_guard<std::mutex> g(g_timer.mu);
-        if (g_timer.count < 8) {
-            g_timer.names[g_timer.count] = name;
-            cudaEventRecord(g_timer.ev[g_timer.count + 1], s);
-            ++g_timer.count;
-        }
+        if (g_timer.used >= kEventPool) return;
+        const int e = g_timer.used++;
+        cudaEventRecord(g_timer.ev[e], s);
+        g_timer.spans[g_timer.nspans++] = {name, last, e};
+        last = e;
     }
 };
 
@@ -156,17 +169,32 @@ void gpz_set_stage_timing(int enable) {
     g_timer.enabled = enable != 0;
 }
 
-int gpz_stage_times(const char** names, float* ms, int max) {
+int gpz_stage_times(const char** names, float* total_ms, int* launches, int max) {
     std::lock_guard<std::mutex> g(g_timer.mu);
-    if (!g_timer.created || g_timer.count == 0) return 0;
-    if (cudaEventSynchronize(g_timer.ev[g_timer.count]) != cudaSuccess) return 0;
     int k = 0;
-    for (; k < g_timer.count && k < max; ++k) {
-        float t = 0.0f;
-        cudaEventElapsedTime(&t, g_timer.ev[k], g_timer.ev[k + 1]);
-        if (names) names[k] = g_timer.names[k];
-        if (ms) ms[k] = t;
+    if (g_timer.nspans > 0) {
+        const int lastev = g_timer.spans[g_timer.nspans - 1].b;
+        if (cudaEventSynchronize(g_timer.ev[lastev]) == cudaSuccess) {
+            for (int i = 0; i < g_timer.nspans; ++i) {
+                const auto& sp = g_timer.spans[i];
+                float t = 0.0f;
+                if (cudaEventElapsedTime(&t, g_timer.ev[sp.a], g_timer.ev[sp.b]) != cudaSuccess) continue;
+                int j = 0;
+                while (j < k && std::strcmp(names[j], sp.name) != 0) ++j;
+                if (j == k) {
+                    if (k == max) continue;
+                    names[k] = sp.name;
+                    total_ms[k] = 0.0f;
+                    launches[k] = 0;
+                    ++k;
+                }
+                total_ms[j] += t;
+                launches[j] += 1;
+            }
+        }
     }
+    g_timer.used = 0;
+    g_timer.nspans = 0;
     return k;
 }
 
@@ -236,6 +264,7 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
     Recorder rec(s);
     do {
         if ((rc = cuda_status(cudaMemsetAsync(ws, 0, L.zero_bytes, s))) != GPZ_OK) break;
+        rec.begin();
         FieldParams hp[kMaxFields] = {};
         const bool rel = p->mode == GPZ_EB_REL;
         if (!rel)
@@ -277,7 +306,6 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
         qa.perm = d_perm;
         qa.status = status;
-        qa.warp_bytes = qse_warp_bytes(F, &qa.tile_bytes);
         if (nb > 0) {
             if ((rc = cuda_status(launch_qse(qa, s))) != GPZ_OK) break;
             rec.mark("qse");
@@ -288,6 +316,8 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         ScanArgs sa{};
         sa.sizes = qa.sizes;
         sa.nblocks = (uint32_t)nb;
+        sa.n = n;
+        sa.F = F;
         sa.table = stream_words + table_start;
         sa.tile_state = reinterpret_cast<unsigned long long*>(ws + L.states);
         sa.tile_counter = tile_counter;
@@ -354,6 +384,7 @@ gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fi
     Recorder rec(s);
     do {
         if ((rc = cuda_status(cudaMemsetAsync(status, 0, 4, s))) != GPZ_OK) break;
+        rec.begin();
         DecArgs da{};
         da.stream = static_cast<const uint32_t*>(d_in);
         da.total_words = in_size / 4;

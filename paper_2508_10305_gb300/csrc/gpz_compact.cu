@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(kScanThreads) gpz_scan_kernel(ScanArgs a) {
     const uint32_t tile = s_tile;
     const uint64_t start = (uint64_t)tile * kScanTile + (uint64_t)tid * kScanItems;
 
+    // A block's words never exceed its raw size 1 + F*n_b; clamping keeps the
+    // offsets (and the copy) inside the bound even if a size were corrupt.
+    const uint32_t raw_full = 1u + (uint32_t)a.F * kBlock;
+    const uint32_t raw_last = 1u + (uint32_t)a.F * (uint32_t)(a.n - (uint64_t)(a.nblocks ? a.nblocks - 1 : 0) * kBlock);
     uint32_t v[kScanItems];
     if (start + kScanItems <= a.nblocks) {
         const uint4* src = reinterpret_cast<const uint4*>(a.sizes + start);
@@ -65,7 +69,10 @@ __global__ void __launch_bounds__(kScanThreads) gpz_scan_kernel(ScanArgs a) {
     }
     uint32_t sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) sum += v[k];
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = min(v[k], start + k + 1 == a.nblocks ? raw_last : raw_full);
+        sum += v[k];
+    }
     const uint32_t incl = warp_incl_sum(sum);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
     }
     uint32_t* payload = a.stream + a.payload_start;
     for (uint32_t b = blockIdx.x * kCompactWarps + warp; b < a.nblocks; b += nwarps) {
-        const uint32_t len = min(__ldcg(a.sizes + b), a.slot_words);
+        const uint32_t len = __ldcg(a.table + b + 1) - __ldcg(a.table + b);  // clamped by the scan
         const uint32_t* src = a.temp + (size_t)b * a.slot_words;
         uint32_t* dst = payload + __ldcg(a.table + b);
         uint32_t k = lane;

@@ -18,8 +18,8 @@ constexpr int kMaxSegBits = 3;
 constexpr int kMaxBins = 512;            // 2^(3 * kMaxSegBits) linearised segment ids
 constexpr int kRow = 33;                 // padded shared-memory row of 32 values
 constexpr int kPadWords = 32 * kRow;     // 1056: 1024 values in padded rows
-constexpr int kQseWarps = 4;             // warps (= particle blocks) per CTA of the fused kernel
-constexpr int kDecWarps = 8;             // warps per CTA of the decompression kernel
+constexpr int kQseThreads = 256;         // one CTA per particle block, 4 particles per thread
+constexpr int kDecThreads = 256;         // one CTA per particle block, 4 positions per thread
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -63,13 +63,13 @@ struct QseArgs {
     uint32_t* sizes;            // [nblocks] words per block
     uint32_t* perm;             // [n] or nullptr
     uint32_t* status;
-    uint32_t tile_bytes;        // per-warp tile bytes
-    uint32_t warp_bytes;        // per-warp shared memory bytes
 };
 
 struct ScanArgs {
     const uint32_t* sizes;      // [nblocks]
     uint32_t nblocks;
+    uint64_t n;                 // particles (a block's size never exceeds its raw size)
+    int F;
     uint32_t* table;            // [nblocks + 1] in the stream
     unsigned long long* tile_state; // [ntiles], zeroed
     uint32_t* tile_counter;     // zeroed
@@ -104,6 +104,23 @@ struct DecArgs {
 };
 
 // ---------------------------------------------------------------- helpers
+
+// ceil(2^32 / d) for d = 1..255 (entry 0 unused), built at compile time: with
+// m = ceil(2^32 / d), floor(n / d) = floor(n * m / 2^32) exactly for n < 2^18
+// (the multiply's relative error stays below 2^-14 < 1/d).
+struct DivMagic {
+    unsigned long long m[256];
+    constexpr DivMagic() : m() {
+        for (int d = 1; d < 256; ++d) m[d] = ((1ull << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d;
+    }
+};
+__constant__ DivMagic kDivMagic = DivMagic();
+
+// floor(n / d) for n < 2^18, 1 <= d <= 255.
+__device__ __forceinline__ uint32_t div_small(uint32_t n, uint32_t d) {
+    const unsigned long long m = kDivMagic.m[d];
+    return __umulhi(n, (uint32_t)m) + ((m >> 32) ? n : 0u);
+}
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
     atomicCAS(st, 0u, code);
@@ -239,6 +256,5 @@ cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);
-uint32_t qse_warp_bytes(int F, uint32_t* tile_bytes);
 
 }  // namespace gpz

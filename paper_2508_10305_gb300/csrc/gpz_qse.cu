@@ -1,26 +1,30 @@
 // gpz_qse.cu -- the fused per-block compression kernel (stages 1-3 of GPZ:
-// quantisation, sorting, encoding; Sections 4.1-4.3 and Table 1's "Q.S.E."
-// kernel) and the global range pass of the relative error bound.
+// quantisation, sorting, encoding; Sections 4.1-4.3, the "Q.S.E." kernel of
+// Table 1) and the global range pass of the relative error bound.
 //
-// One warp owns one block of 1024 particles (Section 4: one warp per block),
-// kQseWarps warps per CTA.  Per warp:
-//   1. the block's F field tiles (4 KB each) are staged into shared memory
-//      with one bulk copy per field (cp.async.bulk + mbarrier);
-//   2. per field: exact fp32 minimum (Section 4.1), quantisation
-//      q = floor(fma(x - min, 1/s, 1/2)) with the fp32 verification and
-//      candidate fallback of the stream format, widths;
+// One CTA of 256 threads owns one block of 1024 particles; every thread
+// holds 4 particles of every field in registers (no shared-memory tile).
+// Thread (warp w, lane l) owns elements 128w + 32r + l, r = 0..3, so that each
+// warp covers 128 consecutive particles in storage order.  Per CTA:
+//   1. coalesced streaming loads; per-field exact fp32 minimum (Section 4.1:
+//      per-thread, then warp reduction, then a shared atomic per warp);
+//   2. quantisation q = floor(fma(x - min, 1/s, 1/2)) with the stream
+//      format's fp32 verification and candidate fallback; for codes below
+//      2^23 the floor and the int<->float conversions are one add in
+//      round-down mode against 2^23 (full-rate pipes);
 //   3. segId / segOffset by shift and mask (Section 5.1), the linearised
-//      segId (key) and the per-particle record, in registers;
-//   4. stable counting sort by key (Section 4.2): ranks in storage order from
-//      __match_any_sync groups, a shared histogram, an exclusive scan;
-//      the non-empty histogram bins are exactly the run-length code
-//      (unique ids and counts, Section 4.3), so sort and run-length coding
-//      share one pass;
-//   5. fixed-length coding (Section 4.3): each lane packs 32 consecutive
-//      values serially into a 64-bit accumulator; packed words are staged
-//      in shared memory and written out coalesced;
-//   6. the block's words go to its fixed temporary slot (step 1 of the
-//      three-step compaction, Section 4.4) with its word count.
+//      segId (key) and the per-particle record of offsets and extra-field
+//      codes;
+//   4. stable counting sort by key (Section 4.2): each warp ranks its 128
+//      elements in storage order with __match_any_sync into a per-warp
+//      histogram; a CTA-wide scan over (bin, warp) gives every element its
+//      sorted position.  The non-empty bins are the run-length code (unique
+//      ids and counts, Section 4.3);
+//   5. fixed-length coding (Section 4.3) by word-owner gather: thread k builds
+//      output words k, k+256, ... from the sorted records in shared memory and
+//      stores them coalesced;
+//   6. the block goes to its temporary slot with its word count (step 1 of
+//      the three-step compaction, Section 4.4).
 #include "gpz_internal.cuh"
 
 namespace gpz {
@@ -114,478 +118,529 @@ cudaError_t launch_range(const RangeArgs& a, int grid, cudaStream_t s) {
 
 // ------------------------------------------------------------------ fused Q.S.E. kernel
 
-// Per-warp scalars shared by the lanes (warp-uniform values).
-struct WarpMeta {
-    FieldParams p[kMaxFields];
-    const float* ptr[kMaxFields];
-    float mn[kMaxFields];
-    uint32_t bits[kMaxFields];
-    uint32_t w[kMaxFields];       // record width of the field: o (positions) or bits (extra fields)
-    uint32_t o[kMaxFields];       // segOffset bits of a position axis
-    uint32_t kshift[kMaxFields];  // left shift of the axis' segId within the key
-    uint32_t rshift[kMaxFields];  // bit offset of the field inside the record
+constexpr int kThreads = kQseThreads;        // 256
+constexpr int kWarps = kThreads / 32;        // 8
+constexpr uint32_t kHistBytes = kWarps * kMaxBins * 2u;  // u16 per-warp histograms
+constexpr uint32_t kMagic23 = 0x4B000000u;   // bit pattern of 2^23
+
+__host__ __device__ constexpr uint32_t qse_region_bytes(int F) {
+    const uint32_t rec = kHistBytes + kBlock * 16u;         // histograms + 128-bit sorted records
+    const uint32_t codes = (uint32_t)F * kBlock * 4u;        // u32 sorted codes per field (W > 128)
+    return rec > codes ? rec : codes;
+}
+
+// The whole encoded block of the packed path: header (<= 11 words), deltas
+// (<= 512 x 9 bits), counts (<= 512 x 11 bits), records (<= 1024 x 128 bits).
+constexpr uint32_t kStageWords = 4432u;
+constexpr uint32_t kFastRecordBits = 128u;
+
+__host__ __device__ constexpr uint32_t qse_smem_bytes(int F) {
+    return qse_region_bytes(F) + kMaxBins * 2u /*uniq*/ + kMaxBins * 2u /*counts*/ + kBlock * 2u /*perm*/ +
+           kStageWords * 4u /*packed records*/;
+}
+
+struct QseShared {
+    uint32_t minkey[kMaxFields];
+    uint32_t maxq[kMaxFields];
+    uint32_t flags;                 // bit 0: non-finite value, bit 1: no code within the bound
+    uint32_t maxcnt, maxdelta;
+    uint32_t warp_tot[kWarps], warp_nz[kWarps];
 };
 
-// Verification of one candidate code (the decompressor's reconstruction).
+// Order-preserving map of finite floats to u32 (-0 < +0).
+__device__ __forceinline__ uint32_t order_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_key(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Verification of one candidate code: the decompressor's reconstruction.
 __device__ __forceinline__ bool code_ok(float x, uint32_t q, const FieldParams& p, float mn) {
     const float xh = __fmaf_rn(__uint2float_rn(q), p.s, mn);
     return fabsf(__fsub_rn(x, xh)) <= p.ebchk;
 }
 
-__device__ __noinline__ bool adjust_code(float x, uint32_t* q, FieldParams p, float mn) {
-    if (*q > 0u && code_ok(x, *q - 1u, p, mn)) {
-        *q -= 1u;
-        return true;
-    }
-    if (code_ok(x, *q + 1u, p, mn)) {
-        *q += 1u;
-        return true;
-    }
-    return false;
+// General quantiser (codes >= 2^23, or a first candidate that fails):
+// candidates q0, q0 - 1, q0 + 1; returns 0xffffffff when none is within the
+// bound (valid codes are below 2^31).
+__device__ __noinline__ uint32_t quantise_general(float x, FieldParams p, float mn) {
+    const float t = __fmaf_rn(__fsub_rn(x, mn), p.inv, 0.5f);
+    if (!(t < 2147483648.0f)) return 0xffffffffu;
+    const uint32_t q = __float2uint_rd(t);
+    if (code_ok(x, q, p, mn)) return q;
+    if (q > 0u && code_ok(x, q - 1u, p, mn)) return q - 1u;
+    if (code_ok(x, q + 1u, p, mn)) return q + 1u;
+    return 0xffffffffu;
 }
 
-// Write the packed words staged in `stage` (rows of kRow) to out: row L's
-// words [c0, c0 + len) belong at out[L * row_words + c0 + ...]; words at or
-// beyond `total` are not written.
-__device__ __forceinline__ void flush_rows(const uint32_t* stage, uint32_t* out, int nrows, uint32_t row_words,
-                                           uint32_t c0, uint32_t len, uint32_t total, int lane) {
-    __syncwarp();
-    if ((uint32_t)lane < len) {
-        for (int L = 0; L < nrows; ++L) {
-            const uint32_t idx = (uint32_t)L * row_words + c0 + lane;
-            if (idx < total) out[idx] = stage[L * kRow + lane];
-        }
-    }
-    __syncwarp();
-}
 
-// Fixed-length code of `len` u32 values held in padded rows of `src`, width
-// w (0..31); lane L packs values [32L, 32L+32).  Returns the word count.
-__device__ uint32_t pack_u32(const uint32_t* src, int len, uint32_t w, uint32_t* stage, uint32_t* out, int lane) {
-    const uint32_t total = ceil_words((uint32_t)len * w);
-    if (total == 0) return 0;
-    const int nrows = (len + 31) >> 5;
-    unsigned long long acc = 0;
-    uint32_t nb = 0, k = 0;
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-        const int j = 32 * lane + t;
-        const uint32_t v = j < len ? src[lane * kRow + t] : 0u;
+// Thread-serial fixed-length appender into zeroed shared words: appends the
+// low w (<= 32) bits of v at the current bit position.  Every completed word
+// is merged with atomicOr (a word at the edge of a thread's range is shared
+// with its neighbour); the updates are predicated, so the warp never diverges.
+struct BitAppender {
+    unsigned long long acc;
+    uint32_t nb;   // bits pending in acc (< 32)
+    uint32_t wi;   // shared word index of acc's low word
+    __device__ __forceinline__ BitAppender(uint32_t bitpos) : acc(0ull), nb(bitpos & 31u), wi(bitpos >> 5) {}
+    __device__ __forceinline__ void put(uint32_t* sw, uint32_t v, uint32_t w) {
         acc |= (unsigned long long)v << nb;
         nb += w;
-        if (nb >= 32u) {
-            stage[lane * kRow + k] = (uint32_t)acc;
-            acc >>= 32;
-            nb -= 32u;
-            ++k;
-        }
+        const bool full = nb >= 32u;
+        if (full) atomicOr(sw + wi, (uint32_t)acc);
+        acc = full ? (acc >> 32) : acc;
+        nb = full ? nb - 32u : nb;
+        wi += full ? 1u : 0u;
     }
-    flush_rows(stage, out, nrows, w, 0, w, total, lane);
-    return total;
+    __device__ __forceinline__ void finish(uint32_t* sw) {
+        if (nb) atomicOr(sw + wi, (uint32_t)acc);
+    }
+};
+
+template <int F>
+__device__ __forceinline__ void write_raw(const QseArgs& a, uint64_t first, int n_b, uint32_t* out, int t) {
+    if (t == 0) out[0] = 1u;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float* src = a.fields[f] + first;
+        for (int i = t; i < n_b; i += kThreads) out[1 + f * n_b + i] = __float_as_uint(__ldg(src + i));
+    }
+    if (a.perm)
+        for (int i = t; i < n_b; i += kThreads) a.perm[first + i] = (uint32_t)(first + i);
+    if (t == 0) a.sizes[first / kBlock] = 1u + (uint32_t)F * (uint32_t)n_b;
 }
 
-// Fixed-length code of n_b records of width W <= 64, records held as u64 in
-// padded rows of `rec`.  A lane's 32 records make W words; every 32 emitted
-// words are flushed.
-__device__ uint32_t pack_records64(const unsigned long long* rec, int n_b, uint32_t W, uint32_t* stage,
-                                   uint32_t* out, int lane) {
-    const uint32_t total = ceil_words((uint32_t)n_b * W);
-    if (total == 0) return 0;
-    const int nrows = (n_b + 31) >> 5;
-    const uint32_t wlo = W < 32u ? W : 32u;
-    const uint32_t whi = W - wlo;
-    const uint32_t mlo = wlo == 32u ? 0xffffffffu : ((1u << wlo) - 1u);
-    unsigned long long acc = 0;
-    uint32_t nb = 0, k = 0;
-    for (int t = 0; t < 32; ++t) {
-        const int j = 32 * lane + t;
-        const unsigned long long r = j < n_b ? rec[lane * kRow + t] : 0ull;
-        acc |= (unsigned long long)((uint32_t)r & mlo) << nb;
-        nb += wlo;
-        if (nb >= 32u) {
-            stage[lane * kRow + (k & 31u)] = (uint32_t)acc;
-            acc >>= 32;
-            nb -= 32u;
-            ++k;
-            if ((k & 31u) == 0u) flush_rows(stage, out, nrows, W, k - 32u, 32u, total, lane);
-        }
-        if (whi) {
-            acc |= (unsigned long long)(uint32_t)(r >> 32) << nb;
-            nb += whi;
-            if (nb >= 32u) {
-                stage[lane * kRow + (k & 31u)] = (uint32_t)acc;
-                acc >>= 32;
-                nb -= 32u;
-                ++k;
-                if ((k & 31u) == 0u) flush_rows(stage, out, nrows, W, k - 32u, 32u, total, lane);
-            }
-        }
-    }
-    if (k & 31u) flush_rows(stage, out, nrows, W, k & ~31u, k & 31u, total, lane);
-    return total;
-}
-
-// General record packer (W > 64): codes are read field by field from the
-// quantised tile through the block permutation.
-__device__ uint32_t pack_records_wide(const uint32_t* tile, const uint32_t* perm_rows, const WarpMeta* m, int F,
-                                     int P, int n_b, uint32_t W, uint32_t* stage, uint32_t* out, int lane) {
-    const uint32_t total = ceil_words((uint32_t)n_b * W);
-    const int nrows = (n_b + 31) >> 5;
-    unsigned long long acc = 0;
-    uint32_t nb = 0, k = 0;
-    for (int t = 0; t < 32; ++t) {
-        const int j = 32 * lane + t;
-        const bool valid = j < n_b;
-        const uint32_t i = valid ? perm_rows[lane * kRow + t] : 0u;
-        for (int f = F - 1; f >= 0; --f) {
-            const uint32_t wf = m->w[f];
-            uint32_t code = valid ? tile[f * kBlock + i] : 0u;
-            if (f < P) code &= (wf == 0u ? 0u : (0xffffffffu >> (32u - wf)));
-            acc |= (unsigned long long)code << nb;
-            nb += wf;
-            if (nb >= 32u) {
-                stage[lane * kRow + (k & 31u)] = (uint32_t)acc;
-                acc >>= 32;
-                nb -= 32u;
-                ++k;
-                if ((k & 31u) == 0u) flush_rows(stage, out, nrows, W, k - 32u, 32u, total, lane);
-            }
-        }
-    }
-    if (k & 31u) flush_rows(stage, out, nrows, W, k & ~31u, k & 31u, total, lane);
-    return total;
-}
-
-__device__ void write_raw_block(const QseArgs& a, const WarpMeta* m, uint64_t first, int n_b, uint32_t* out,
-                                int lane) {
-    if (lane == 0) out[0] = 1u;
-    for (int f = 0; f < a.F; ++f) {
-        const float* src = m->ptr[f] + first;
-        for (int i = lane; i < n_b; i += 32) out[1 + f * n_b + i] = __float_as_uint(__ldg(src + i));
-    }
-    if (a.perm) {
-        for (int i = lane; i < n_b; i += 32) a.perm[first + i] = (uint32_t)(first + i);
-    }
-    if (lane == 0) a.sizes[(uint32_t)(first / kBlock)] = 1u + (uint32_t)a.F * (uint32_t)n_b;
-}
-
-uint32_t qse_warp_bytes(int F, uint32_t* tile_bytes) {
-    uint32_t tb = (uint32_t)F * kBlock * 4u;
-    const uint32_t rec_bytes = kPadWords * 8u;  // 1056 u64 records
-    if (tb < rec_bytes) tb = rec_bytes;
-    tb = (tb + 127u) & ~127u;
-    if (tile_bytes) *tile_bytes = tb;
-    uint32_t bytes = tb + 2u * kPadWords * 4u + kMaxBins * 4u + (uint32_t)sizeof(WarpMeta) + 16u;
-    return (bytes + 127u) & ~127u;
-}
-
-__global__ void __launch_bounds__(32 * kQseWarps) gpz_qse_kernel(QseArgs a) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t b = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (b >= a.nblocks) return;
-
-    uint8_t* base = smem + (size_t)warp * a.warp_bytes;
-    uint32_t* tile = reinterpret_cast<uint32_t*>(base);
-    unsigned long long* rec_rows = reinterpret_cast<unsigned long long*>(base);
-    uint32_t* scr = reinterpret_cast<uint32_t*>(base + a.tile_bytes);
-    uint32_t* stage = scr + kPadWords;
-    uint32_t* hist = stage + kPadWords;
-    WarpMeta* m = reinterpret_cast<WarpMeta*>(hist + kMaxBins);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(m) + sizeof(WarpMeta));
-
-    const int F = a.F;
-    const int P = F < 3 ? F : 3;
+template <int F, bool FULL>
+__device__ __forceinline__ void qse_block(const QseArgs& a, uint8_t* dsm, QseShared& S) {
+    constexpr int P = F < 3 ? F : 3;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint32_t b = blockIdx.x;
     const uint64_t first = (uint64_t)b * kBlock;
-    const int n_b = (int)((a.n - first) < (uint64_t)kBlock ? (a.n - first) : (uint64_t)kBlock);
-
-    // Per-field constants and pointers into the warp's meta block.
-#pragma unroll
-    for (int k = 0; k < kMaxFields; ++k) {
-        if (lane == k && k < F) {
-            m->p[k] = a.d_params ? a.d_params[k] : a.params[k];
-            m->ptr[k] = a.fields[k];
-        }
-    }
-    __syncwarp();
-
-    // ---- 1. stage the field tiles
-    const bool bulk = a.bulk_ok && n_b == kBlock;
-    if (bulk) {
-        if (lane == 0) {
-            mbar_init(mbar, 1);
-            mbar_expect_tx(mbar, (uint32_t)F * kBlock * 4u);
-            for (int f = 0; f < F; ++f) bulk_g2s(tile + f * kBlock, m->ptr[f] + first, kBlock * 4u, mbar);
-        }
-    } else {
-        for (int f = 0; f < F; ++f) {
-            const float* src = m->ptr[f] + first;
-            for (int i = lane; i < n_b; i += 32) tile[f * kBlock + i] = __float_as_uint(__ldg(src + i));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxBins / 32; ++k) hist[lane + 32 * k] = 0u;
-    __syncwarp();
-    if (bulk) {
-        if (!mbar_wait_bounded(mbar, 0, a.status)) {
-            // The copy never completed (status holds GPZ_ERR_TIMEOUT): wait
-            // once more, bounded, for the copies in flight; leave an empty
-            // block so that the later stages stay inside their buffers.
-            mbar_wait_bounded(mbar, 0, a.status);
-            if (lane == 0) a.sizes[b] = 0u;
-            return;
-        }
-    }
-    __syncwarp();
-
+    const int n_b = FULL ? kBlock : (int)(a.n - first);
+    constexpr uint32_t region = qse_region_bytes(F);
+    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
+    uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
+    uint32_t* codes = reinterpret_cast<uint32_t*>(dsm);                      // [F][1024], wide records
+    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + region);             // [512]
+    uint16_t* cnt = uniq + kMaxBins;                                         // [512]
+    uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
     uint32_t* out = a.temp + (size_t)b * a.slot_words;
 
-    // ---- 2. block minimum per field; non-finite values force raw storage
-    bool nonfinite = false;
+    if (t < F) {
+        S.minkey[t] = 0xffffffffu;
+        S.maxq[t] = 0u;
+    }
+    if (t == 0) {
+        S.flags = 0u;
+        S.maxcnt = 0u;
+        S.maxdelta = 0u;
+    }
+    {
+        uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
+#pragma unroll
+        for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
+        for (uint32_t k = t; k < kStageWords; k += kThreads) stage[k] = 0u;
+    }
+
+    // ---- 1. load (coalesced, streaming) and block minimum
+    bool valid[4];
+    float x[F][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
+#pragma unroll
     for (int f = 0; f < F; ++f) {
-        const uint32_t* tf = tile + f * kBlock;
-        float mn = INFINITY;
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) {
-            const int i = 32 * r + lane;
-            if (i < n_b) {
-                const float x = __uint_as_float(tf[i]);
-                nonfinite |= !(fabsf(x) <= 3.402823466e38f);
-                mn = fminf(mn, x);
+        const float* src = a.fields[f] + first + 128 * w + lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
+    }
+    FieldParams prm[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) prm[f] = a.d_params ? a.d_params[f] : a.params[f];
+    __syncthreads();  // shared reduction slots initialised (the loads are in flight)
+    float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float m = valid[0] ? x[f][0] : INFINITY;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (valid[r]) {
+                probe = __fmaf_rn(x[f][r], 0.0f, probe);
+                m = fminf(m, x[f][r]);
             }
         }
-        mn = warp_min_f32(mn);
-        if (mn == 0.0f) mn = 0.0f;  // a zero minimum is stored as +0
-        if (lane == 0) m->mn[f] = mn;
+        const uint32_t mk = __reduce_min_sync(0xffffffffu, m == INFINITY ? 0xffffffffu : order_key(m));
+        if (lane == 0) atomicMin(&S.minkey[f], mk);
     }
-    if (__any_sync(0xffffffffu, nonfinite)) {
-        write_raw_block(a, m, first, n_b, out, lane);
+    if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
+    __syncthreads();  // A
+    if (S.flags & 1u) {
+        write_raw<F>(a, first, n_b, out, t);
         return;
     }
-    __syncwarp();
 
-    // ---- 2b. quantisation with verification; widths
+    // ---- 2. quantisation with verification (fast path for codes < 2^23)
+    float mn[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float m = from_order_key(S.minkey[f]);
+        mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
+    }
+    uint32_t q[F][4];
+    uint32_t pending = 0;  // bit 4f + r: value needs the general quantiser
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float xv = x[f][r];
+            const float tt = __fmaf_rn(__fsub_rn(xv, mn[f]), prm[f].inv, 0.5f);
+            // 2^23 + floor(t), exactly, while t < 2^23 (the sum lies in [2^23, 2^24))
+            const float u = __fadd_rd(tt, 8388608.0f);
+            q[f][r] = __float_as_uint(u) - kMagic23;
+            const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), prm[f].s, mn[f]);
+            const bool ok = (tt < 8388608.0f) && (fabsf(__fsub_rn(xv, xh)) <= prm[f].ebchk);
+            if (valid[r] && !ok) pending |= 1u << (4 * f + r);
+            if (!valid[r]) q[f][r] = 0u;
+        }
+    }
     bool fail = false;
-    for (int f = 0; f < F; ++f) {
-        uint32_t* tf = tile + f * kBlock;
-        const FieldParams p = m->p[f];
-        const float mn = m->mn[f];
-        uint32_t qmax = 0u;
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) {
-            const int i = 32 * r + lane;
-            if (i < n_b) {
-                const float x = __uint_as_float(tf[i]);
-                const float t = __fmaf_rn(__fsub_rn(x, mn), p.inv, 0.5f);
-                uint32_t q = 0u;
-                if (t < 2147483648.0f) {
-                    q = __float2uint_rd(t);
-                    if (!code_ok(x, q, p, mn)) fail |= !adjust_code(x, &q, p, mn);
-                } else {
-                    fail = true;
+    if (__any_sync(0xffffffffu, pending != 0u)) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (pending & (1u << (4 * f + r))) {
+                    const uint32_t g = quantise_general(x[f][r], prm[f], mn[f]);
+                    fail |= g == 0xffffffffu;
+                    q[f][r] = g == 0xffffffffu ? 0u : g;
                 }
-                tf[i] = q;
-                qmax = max(qmax, q);
             }
         }
-        qmax = warp_max_u32(qmax);
-        if (lane == 0) m->bits[f] = bit_width(qmax);
     }
-    if (__any_sync(0xffffffffu, fail)) {
-        write_raw_block(a, m, first, n_b, out, lane);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        uint32_t qmax = max(max(q[f][0], q[f][1]), max(q[f][2], q[f][3]));
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        if (lane == 0 && qmax) atomicMax(&S.maxq[f], qmax);
+    }
+    if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&S.flags, 2u);
+    __syncthreads();  // B
+    if (S.flags & 2u) {
+        write_raw<F>(a, first, n_b, out, t);
         return;
     }
-    __syncwarp();
 
-    // ---- 3. segment split (shift and mask), key layout, record layout
-    uint32_t keybits = 0, W = 0;
+    // ---- 3. segments, key and record layout (uniform)
+    uint32_t o[F], wf[F], kshift[F], bits[F], keybits = 0, W = 0;
     {
-        uint32_t g[kMaxFields], w[kMaxFields];
+        uint32_t g[F];
 #pragma unroll
-        for (int f = 0; f < kMaxFields; ++f) {
-            const uint32_t bf = f < F ? m->bits[f] : 0u;
-            g[f] = f < P ? min((uint32_t)a.G, bf) : 0u;
-            w[f] = f < P ? bf - g[f] : bf;
-            keybits += g[f];
-            W += w[f];
+        for (int f = 0; f < F; ++f) {
+            bits[f] = bit_width(S.maxq[f]);
+            g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
+            o[f] = f < P ? bits[f] - g[f] : 0u;
+            wf[f] = f < P ? o[f] : bits[f];
         }
-        if (lane == 0) {
-            uint32_t ks = 0, rs = 0;
+        uint32_t ks = 0;
 #pragma unroll
-            for (int f = kMaxFields - 1; f >= 0; --f) {
-                if (f < F) {
-                    m->w[f] = w[f];
-                    m->o[f] = f < P ? w[f] : 0u;
-                    m->kshift[f] = ks;
-                    m->rshift[f] = rs;
-                    ks += g[f];
-                    rs += w[f];
-                }
+        for (int f = F - 1; f >= 0; --f) {
+            kshift[f] = ks;
+            ks += g[f];
+            W += wf[f];
+        }
+        keybits = ks;
+    }
+    const bool fast = W <= kFastRecordBits;
+    // records as four words r0 (least significant) .. r3; each field's code is
+    // appended below the record so far, so field 0 ends most significant
+    uint32_t key[4], r0[4], r1[4], r2[4], r3[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        uint32_t k = 0;
+#pragma unroll
+        for (int f = 0; f < P; ++f) k |= (q[f][r] >> o[f]) << kshift[f];
+        key[r] = k;
+        r0[r] = r1[r] = r2[r] = r3[r] = 0u;
+    }
+    if (W <= 64u) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const uint32_t code = f < P ? (q[f][r] & ((1u << o[f]) - 1u)) : q[f][r];
+                hi = __funnelshift_l(lo, hi, wf[f]);
+                lo = (lo << wf[f]) | code;
             }
+            r0[r] = lo;
+            r1[r] = hi;
         }
-    }
-    __syncwarp();
-
-    const bool fast = W <= 64u;
-    uint32_t kr[32];              // key | rank << 16
-    unsigned long long rec[32];   // record (fast path)
+    } else if (fast) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        kr[r] = 0u;
-        rec[r] = 0ull;
-    }
-    for (int f = 0; f < F; ++f) {
-        const uint32_t* tf = tile + f * kBlock;
-        const uint32_t o = m->o[f], ks = m->kshift[f], rs = m->rshift[f];
-        const bool pos = f < P;
-        const bool in_rec = fast && m->w[f] != 0u;  // a zero-width field adds no bits (and rs may be 64)
-        const uint32_t omask = o == 0u ? 0u : (0xffffffffu >> (32u - o));
+        for (int r = 0; r < 4; ++r) {
+            uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int i = 32 * r + lane;
-            const uint32_t q = i < n_b ? tf[i] : 0u;
-            if (pos) kr[r] |= (q >> o) << ks;
-            if (in_rec) rec[r] |= (unsigned long long)(pos ? (q & omask) : q) << rs;
+            for (int f = 0; f < F; ++f) {
+                const uint32_t code = f < P ? (q[f][r] & ((1u << o[f]) - 1u)) : q[f][r];
+                a3 = __funnelshift_l(a2, a3, wf[f]);
+                a2 = __funnelshift_l(a1, a2, wf[f]);
+                a1 = __funnelshift_l(a0, a1, wf[f]);
+                a0 = (a0 << wf[f]) | code;
+            }
+            r0[r] = a0;
+            r1[r] = a1;
+            r2[r] = a2;
+            r3[r] = a3;
         }
     }
 
-    // ---- 4. stable counting sort: ranks in storage order
+    // ---- 4. stable counting sort: warp-local ranks in storage order
+    uint16_t* myhist = hist + w * kMaxBins;
+    uint32_t rank[4];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const int i = 32 * r + lane;
-        const bool valid = i < n_b;
-        const uint32_t key = kr[r];
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? key : 0xffffffffu);
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? key[r] : 0xffffffffu);
         uint32_t before = 0u;
-        if (valid) before = hist[key];
+        if (valid[r]) before = myhist[key[r]];
         __syncwarp();
-        if (valid && lane == 31 - __clz(peers)) hist[key] = before + __popc(peers);
+        if (valid[r] && lane == 31 - __clz(peers)) myhist[key[r]] = (uint16_t)(before + __popc(peers));
         __syncwarp();
-        kr[r] = key | ((before + __popc(peers & lanemask_lt())) << 16);
+        rank[r] = before + __popc(peers & lanemask_lt());
     }
+    __syncthreads();  // C
 
-    // ---- 4b. scan of the histogram = run-length code (unique ids, counts)
+    // ---- 4b. scan over (bin, warp): sorted positions and the run-length code
     const int nbins = 1 << keybits;
-    uint32_t* dlt = scr;            // deltas, padded rows 0..15
-    uint32_t* cnt = scr + 16 * kRow; // counts, padded rows 16..31
-    uint32_t U, wd, wc;
-    {
-        const int b0 = 16 * lane;
-        uint32_t c[16];
-        uint32_t sum = 0, nz = 0, cmax = 0;
-        int last_nz = -1;
+    const int b0 = 2 * t;
+    uint32_t c0 = 0, c1 = 0;
+    uint32_t pre[kWarps];  // (prefix of bin b0) | (prefix of bin b0+1) << 16
+    if (b0 < nbins) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            c[k] = (b0 + k < nbins) ? hist[b0 + k] : 0u;
-            sum += c[k];
-            nz += c[k] ? 1u : 0u;
-            cmax = max(cmax, c[k]);
-            if (c[k]) last_nz = b0 + k;
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t pair = *reinterpret_cast<const uint32_t*>(hist + ww * kMaxBins + b0);
+            pre[ww] = c0 | (c1 << 16);
+            c0 += pair & 0xffffu;
+            c1 += pair >> 16;
         }
-        const uint32_t sum_incl = warp_incl_sum(sum);
-        const uint32_t nz_incl = warp_incl_sum(nz);
-        int prev_nz = __shfl_up_sync(0xffffffffu, warp_incl_max(last_nz), 1);
-        if (lane == 0) prev_nz = -1;
-        uint32_t start = sum_incl - sum, idx = nz_incl - nz, dmax = 0;
+    }
+    const uint32_t tot = c0 + c1;
+    const uint32_t nz = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+    const uint32_t incl_tot = warp_incl_sum(tot);
+    const uint32_t incl_nz = warp_incl_sum(nz);
+    const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
+    if (lane == 31) {
+        S.warp_tot[w] = incl_tot;
+        S.warp_nz[w] = incl_nz;
+    }
+    if (lane == 0) atomicMax(&S.maxcnt, cmax);
+    __syncthreads();  // D
+    uint32_t base_tot = 0, base_nz = 0, U = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (b0 + k < nbins) hist[b0 + k] = start;  // exclusive start of the bin
-            start += c[k];
-            if (c[k]) {
-                const uint32_t d = (uint32_t)(b0 + k) - (prev_nz < 0 ? 0u : (uint32_t)prev_nz);
-                dlt[pad_idx((int)idx)] = d;
-                cnt[pad_idx((int)idx)] = c[k];
-                dmax = max(dmax, d);
-                prev_nz = b0 + k;
-                ++idx;
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww];
+        if (ww < w) {
+            base_tot += vt;
+            base_nz += vn;
+        }
+        U += vn;
+    }
+    if (b0 < nbins) {
+        const uint32_t start0 = base_tot + incl_tot - tot, start1 = start0 + c0;
+        const uint32_t idx0 = base_nz + incl_nz - nz, idx1 = idx0 + (c0 ? 1u : 0u);
+        const uint32_t base2 = start0 | (start1 << 16);  // neither half overflows: both < 1024
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww)
+            *reinterpret_cast<uint32_t*>(hist + ww * kMaxBins + b0) = base2 + pre[ww];
+        if (c0) {
+            uniq[idx0] = (uint16_t)b0;
+            cnt[idx0] = (uint16_t)c0;
+        }
+        if (c1) {
+            uniq[idx1] = (uint16_t)(b0 + 1);
+            cnt[idx1] = (uint16_t)c1;
+        }
+    }
+    __syncthreads();  // E
+
+    // ---- 4c. scatter to sorted order; deltas of the unique ids
+    uint32_t dest[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dest[r] = valid[r] ? myhist[key[r]] + rank[r] : 0u;
+    {
+        uint32_t dmax = 0;
+        for (uint32_t k = t; k < U; k += kThreads) {
+            const uint32_t d = (uint32_t)uniq[k] - (k ? (uint32_t)uniq[k - 1] : 0u);
+            dmax = max(dmax, d);
+        }
+        dmax = __reduce_max_sync(0xffffffffu, dmax);
+        if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
+    }
+    if (fast) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (valid[r]) recs[dest[r]] = make_uint4(r0[r], r1[r], r2[r], r3[r]);
+    }
+    if (a.perm) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (valid[r]) sperm[dest[r]] = (uint16_t)(128 * w + 32 * r + lane);
+    }
+    if (!fast) {
+        __syncthreads();  // the histograms are read; the codes may overwrite them
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (!valid[r]) continue;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const uint32_t qq = q[f][r];
+                codes[f * kBlock + dest[r]] = f < P ? (qq & ((1u << o[f]) - 1u)) : qq;
             }
         }
-        U = __shfl_sync(0xffffffffu, nz_incl, 31);
-        wd = bit_width(warp_max_u32(dmax));
-        wc = bit_width(warp_max_u32(cmax));
     }
-    __syncwarp();
+    __syncthreads();  // F
 
     // ---- encoded size; raw when not smaller (keeps the bound size a bound)
+    const uint32_t wd = bit_width(S.maxdelta), wc = bit_width(S.maxcnt);
     const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
     const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc);
     const uint32_t rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t enc = hdr + dwords + cwords + rwords;
     if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
-        write_raw_block(a, m, first, n_b, out, lane);
+        write_raw<F>(a, first, n_b, out, t);
         return;
     }
 
-    // ---- 5. block header and the three arrays
-    if (lane == 0) out[0] = (U << 1) | (wd << 12) | (wc << 17);
-    if (lane >= 1 && lane <= F) out[lane] = __float_as_uint(m->mn[lane - 1]);
-    if (lane < ((F + 3) >> 2)) {
-        uint32_t word = 0;
-        for (int k = 0; k < 4; ++k) {
-            const int f = 4 * lane + k;
-            if (f < F) word |= m->bits[f] << (8 * k);
-        }
-        out[1 + F + lane] = word;
-    }
-    pack_u32(dlt, (int)U, wd, stage, out + hdr, lane);
-    pack_u32(cnt, (int)U, wc, stage, out + hdr + dwords, lane);
-
-    // ---- 4c. scatter to sorted order: records (fast path) and the permutation
-    const bool need_perm = a.perm != nullptr || !fast;
+    // ---- 5. block header and the three arrays (Section 4.3), assembled in the
+    // zeroed staging words by thread-serial appenders, then copied out
+    if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
+    if (t >= 1 && t <= F) {
+        float m = 0.0f;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        const int i = 32 * r + lane;
-        if (i < n_b) {
-            const uint32_t key = kr[r] & 0xffffu;
-            const int dest = (int)(hist[key] + (kr[r] >> 16));
-            if (fast) rec_rows[pad_idx(dest)] = rec[r];
-            if (need_perm) scr[pad_idx(dest)] = (uint32_t)i;
+        for (int f = 0; f < F; ++f)
+            if (f == t - 1) m = mn[f];
+        stage[t] = __float_as_uint(m);
+    }
+    if (t < ((F + 3) >> 2)) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if ((f >> 2) == t) word |= bits[f] << (8 * (f & 3));
+        stage[1 + F + t] = word;
+    }
+    {
+        // deltas and counts: entries 2t, 2t+1
+        const uint32_t k0 = 2u * (uint32_t)t;
+        if (k0 < U && wd) {
+            BitAppender ap(32u * hdr + k0 * wd);
+            ap.put(stage, (uint32_t)uniq[k0] - (k0 ? (uint32_t)uniq[k0 - 1] : 0u), wd);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)uniq[k0 + 1] - (uint32_t)uniq[k0], wd);
+            ap.finish(stage);
+        }
+        if (k0 < U && wc) {
+            BitAppender ap(32u * (hdr + dwords) + k0 * wc);
+            ap.put(stage, (uint32_t)cnt[k0], wc);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)cnt[k0 + 1], wc);
+            ap.finish(stage);
         }
     }
-    __syncwarp();
-
-    if (fast)
-        pack_records64(rec_rows, n_b, W, stage, out + hdr + dwords + cwords, lane);
-    else
-        pack_records_wide(tile, scr, m, F, P, n_b, W, stage, out + hdr + dwords + cwords, lane);
-
-    if (a.perm) {
-        for (int r = 0; r < 32; ++r) {
-            const int j = 32 * r + lane;
-            if (j < n_b) a.perm[first + j] = (uint32_t)first + scr[r * kRow + lane];
+    const uint32_t len = (uint32_t)n_b;
+    const uint32_t rbase = hdr + dwords + cwords;
+    if (fast) {
+        // Thread t appends sorted records 4t..4t+3 (bits [4tW, 4tW + 4W)).
+        const uint32_t j0 = 4u * (uint32_t)t;
+        if (j0 < len && W) {
+            BitAppender ap(32u * rbase + j0 * W);
+            // widths of the record's four words
+            const uint32_t w0 = min(W, 32u), w1 = min(W - w0, 32u), w2 = min(W - w0 - w1, 32u), w3 = W - w0 - w1 - w2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint4 v = (j0 + e < len) ? recs[j0 + e] : make_uint4(0u, 0u, 0u, 0u);
+                ap.put(stage, v.x, w0);
+                if (w1) ap.put(stage, v.y, w1);
+                if (w2) ap.put(stage, v.z, w2);
+                if (w3) ap.put(stage, v.w, w3);
+            }
+            ap.finish(stage);
         }
     }
-    if (lane == 0) a.sizes[b] = enc;
+    __syncthreads();
+    {
+        // copy the staged words (all of them, or up to the records when the
+        // records are wider than 64 bits); the slot is 16-byte aligned
+        const uint32_t nstage = fast ? enc : rbase;
+        const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+        uint4* o4 = reinterpret_cast<uint4*>(out);
+        for (uint32_t k = t; k < (nstage >> 2); k += kThreads) o4[k] = s4[k];
+        for (uint32_t k = (nstage & ~3u) + t; k < nstage; k += kThreads) out[k] = stage[k];
+    }
+    if (!fast) {
+        // records wider than 128 bits: gather field by field from the codes
+        uint32_t* rout = out + rbase;
+        uint32_t rshift[F];
+        {
+            uint32_t rs = 0;
+#pragma unroll
+            for (int f = F - 1; f >= 0; --f) {
+                rshift[f] = rs;
+                rs += wf[f];
+            }
+        }
+        for (uint32_t k = t; k < rwords; k += kThreads) {
+            const uint32_t lo = 32u * k;
+            uint32_t j = div_small(lo, W);
+            uint32_t acc = 0;
+            for (; j < len && j * W < lo + 32u; ++j) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    if (wf[f] == 0u) continue;
+                    const int s0 = (int)(j * W + rshift[f]) - (int)lo;
+                    if (s0 >= 32 || s0 + (int)wf[f] <= 0) continue;
+                    const uint32_t v = codes[f * kBlock + j];
+                    acc |= s0 >= 0 ? (v << s0) : (v >> -s0);
+                }
+            }
+            rout[k] = acc;
+        }
+    }
+    if (a.perm)
+        for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
+    if (t == 0) a.sizes[b] = enc;
 }
 
-// Warps per CTA: shared memory per warp limits residency, so pick the CTA
-// width that keeps the most warps resident per SM (228 KB, 1 KB reserved per
-// CTA).
-int qse_warps_per_cta(uint32_t warp_bytes) {
-    const uint32_t sm_bytes = 228u * 1024u;
-    int best = 1, best_warps = 0;
-    for (int w = 1; w <= kQseWarps; ++w) {
-        const uint32_t cta = (uint32_t)w * warp_bytes + 1024u;
-        if ((uint32_t)w * warp_bytes > 227u * 1024u) break;
-        const int ctas = (int)(sm_bytes / cta);
-        const int warps = (ctas > 32 ? 32 : ctas) * w;
-        if (warps > best_warps) {
-            best_warps = warps;
-            best = w;
-        }
-    }
-    return best;
+template <int F>
+__global__ void __launch_bounds__(kThreads, 3) gpz_qse_kernel(QseArgs a) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ QseShared S;
+    if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
+        qse_block<F, true>(a, dsm, S);
+    else
+        qse_block<F, false>(a, dsm, S);
+}
+
+template <int F>
+cudaError_t launch_qse_f(const QseArgs& a, cudaStream_t s) {
+    const size_t smem = qse_smem_bytes(F);
+    cudaError_t e = cudaFuncSetAttribute(gpz_qse_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gpz_qse_kernel<F><<<a.nblocks, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_qse(const QseArgs& a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
-    const int wpc = qse_warps_per_cta(a.warp_bytes);
-    const size_t smem = (size_t)a.warp_bytes * wpc;
-    cudaError_t e = cudaFuncSetAttribute(gpz_qse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (a.nblocks + wpc - 1) / wpc;
-    gpz_qse_kernel<<<grid, 32 * wpc, smem, s>>>(a);
-    return cudaGetLastError();
+    switch (a.F) {
+        case 1: return launch_qse_f<1>(a, s);
+        case 2: return launch_qse_f<2>(a, s);
+        case 3: return launch_qse_f<3>(a, s);
+        case 4: return launch_qse_f<4>(a, s);
+        case 5: return launch_qse_f<5>(a, s);
+        case 6: return launch_qse_f<6>(a, s);
+        case 7: return launch_qse_f<7>(a, s);
+        case 8: return launch_qse_f<8>(a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gpz

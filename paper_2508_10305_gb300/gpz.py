@@ -55,7 +55,7 @@ def _load():
     L.gpz_status_str.restype = C.c_char_p
     L.gpz_set_stage_timing.argtypes = [C.c_int]
     L.gpz_set_stage_timing.restype = None
-    L.gpz_stage_times.argtypes = [P(C.c_char_p), P(C.c_float), C.c_int]
+    L.gpz_stage_times.argtypes = [P(C.c_char_p), P(C.c_float), P(C.c_int), C.c_int]
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
     L.gpz_launch_count.restype = u64
@@ -88,10 +88,12 @@ def gpz_set_stage_timing(enable):
 
 
 def gpz_stage_times(max_stages=8):
+    """{stage: (total_ms, launches)} since the previous read (clears the log)."""
     names = (C.c_char_p * max_stages)()
     ms = (C.c_float * max_stages)()
-    k = lib.gpz_stage_times(names, ms, max_stages)
-    return [(names[i].decode(), float(ms[i])) for i in range(k)]
+    cnt = (C.c_int * max_stages)()
+    k = lib.gpz_stage_times(names, ms, cnt, max_stages)
+    return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
 
 
 def gpz_launch_count(reset=False):
