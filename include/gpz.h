@@ -109,6 +109,31 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
                         uint64_t* h_out_size, uint32_t* d_perm, void* d_ws, uint64_t ws_size,
                         void* stream);
 
+/* Compress without allocating anything (the paper has no counterpart: this is
+ * a convenience of this library).  Same arguments, stream and behaviour as
+ * gpz_compress with d_ws = NULL, except that no device memory is allocated:
+ * the scratch space comes from a fixed 32 MiB array built into the library
+ * (reserved on every GPU that loads the library, until the process exits).
+ * It is meant for callers that cannot allocate device memory when they
+ * compress -- for example an in-situ hook inside a simulation whose device
+ * memory is fully reserved by the simulation's own pool allocator, or a
+ * latency-critical loop in which an allocation may stall the device.
+ *   - Limit: gpz_compress_workspace_size(n, n_fields) must not exceed 32 MiB
+ *     (about 8 million values n * n_fields); larger inputs return
+ *     GPZ_ERR_CAPACITY and enqueue nothing.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture on that device.
+ *   - All calls on a device share the one array, and it keeps the last
+ *     call's contents; every call clears what must start at zero.  Calls whose
+ *     work overlaps on the GPU (different streams, or host threads issuing
+ *     concurrently) race on the array: serialise them.
+ *   - Device-side errors are returned only when h_out_size is given (the call
+ *     then synchronises `stream`). */
+gpz_status gpz_compress_noalloc(const float* const* d_fields, uint64_t n, const gpz_params* p,
+                                void* d_out, uint64_t out_capacity, uint64_t* d_out_size,
+                                uint64_t* h_out_size, uint32_t* d_perm, void* stream);
+
 /* Decompress (Section 3.2, last paragraph: the inverse without sorting).
  *   d_in/in_size: the stream (device, 4-byte aligned) and its size in bytes.
  *   d_fields:     host array of n_fields device pointers, each receiving n

@@ -45,6 +45,8 @@ def _load():
     L.gpz_decompress_workspace_size.restype = u64
     L.gpz_compress.argtypes = [P(vp), u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp, u64, vp]
     L.gpz_compress.restype = C.c_int
+    L.gpz_compress_noalloc.argtypes = [P(vp), u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp]
+    L.gpz_compress_noalloc.restype = C.c_int
     L.gpz_decompress.argtypes = [vp, u64, P(vp), C.c_int, u64, vp, u64, vp]
     L.gpz_decompress.restype = C.c_int
     L.gpz_sync_status.argtypes = [vp, vp]
@@ -147,6 +149,18 @@ def gpz_compress(fields, n, params, out, out_capacity, d_out_size=None, h_out_si
                             C.byref(h_out_size) if h_out_size is not None else None,
                             perm.data_ptr() if perm is not None else None,
                             ws.data_ptr() if ws is not None else None, ws_size, _stream_handle(stream))
+
+
+def gpz_compress_noalloc(fields, n, params, out, out_capacity, d_out_size=None, h_out_size=None, perm=None,
+                         stream=None):
+    """Mirror of the C entry point that allocates nothing (its scratch space is
+    a fixed array inside the library; see include/gpz.h for the limit)."""
+    if isinstance(fields, torch.Tensor):
+        fields = [fields[f] for f in range(fields.shape[0])]
+    return lib.gpz_compress_noalloc(_ptr_array(fields), n, C.byref(params), out.data_ptr(), out_capacity,
+                                    d_out_size.data_ptr() if d_out_size is not None else None,
+                                    C.byref(h_out_size) if h_out_size is not None else None,
+                                    perm.data_ptr() if perm is not None else None, _stream_handle(stream))
 
 
 def gpz_decompress(stream_buf, in_size, fields, n_fields, n, ws=None, ws_size=0, stream=None):
