@@ -31,7 +31,7 @@ uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * k
 uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kScanTile; }
 
 struct WsLayout {
-    uint64_t ctrl, params, states, partials, sizes, temp, total, zero_bytes;
+    uint64_t ctrl, params, states, partials, sizes, list, temp, total, zero_bytes;
 };
 
 WsLayout layout_of(uint64_t n, int F) {
@@ -48,6 +48,8 @@ WsLayout layout_of(uint64_t n, int F) {
     L.partials = o;
     o += align_up((uint64_t)kRangeGridMax * F * sizeof(float2), kAlign);
     L.sizes = o;
+    o += align_up(nb * 4, kAlign);
+    L.list = o;
     o += align_up(nb * 4, kAlign);
     L.temp = o;
     o += align_up(nb * slot_words_of(F) * 4ull, kAlign);
@@ -306,9 +308,12 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
         qa.perm = d_perm;
         qa.status = status;
+        qa.general_list = reinterpret_cast<uint32_t*>(ws + L.list);
+        qa.general_count = status + 3;
         if (nb > 0) {
             if ((rc = cuda_status(launch_qse(qa, s))) != GPZ_OK) break;
             rec.mark("qse");
+            ++g_launches;  // launch_qse enqueues two kernels: the fast path and the general list
         }
 
         uint32_t* stream_words = static_cast<uint32_t*>(d_out);

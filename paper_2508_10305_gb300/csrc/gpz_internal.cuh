@@ -63,6 +63,8 @@ struct QseArgs {
     uint32_t* sizes;            // [nblocks] words per block
     uint32_t* perm;             // [n] or nullptr
     uint32_t* status;
+    uint32_t* general_list;     // [nblocks] blocks left to the general kernel
+    uint32_t* general_count;    // zeroed
 };
 
 struct ScanArgs {

@@ -212,11 +212,12 @@ __device__ __forceinline__ void write_raw(const QseArgs& a, uint64_t first, int 
     if (t == 0) a.sizes[first / kBlock] = 1u + (uint32_t)F * (uint32_t)n_b;
 }
 
+// The general per-block path: any block, including codes >= 2^23, values
+// that need a fallback candidate, and records wider than 128 bits.
 template <int F, bool FULL>
-__device__ __forceinline__ void qse_block(const QseArgs& a, uint8_t* dsm, QseShared& S) {
+__device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm, QseShared& S, uint32_t b) {
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const uint32_t b = blockIdx.x;
     const uint64_t first = (uint64_t)b * kBlock;
     const int n_b = FULL ? kBlock : (int)(a.n - first);
     constexpr uint32_t region = qse_region_bytes(F);
@@ -609,22 +610,384 @@ __device__ __forceinline__ void qse_block(const QseArgs& a, uint8_t* dsm, QseSha
     if (t == 0) a.sizes[b] = enc;
 }
 
+// Blocks the fast kernel leaves to the general path (rare): processed by a
+// persistent grid walking the list.
 template <int F>
-__global__ void __launch_bounds__(kThreads, 3) gpz_qse_kernel(QseArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) gpz_qse_general_kernel(QseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseShared S;
+    const uint32_t count = *(volatile const uint32_t*)a.general_count;
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint32_t b = a.general_list[i];
+        if ((uint64_t)(b + 1) * kBlock <= a.n)
+            qse_block_general<F, true>(a, dsm, S, b);
+        else
+            qse_block_general<F, false>(a, dsm, S, b);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ fast path
+
+constexpr uint32_t kFastRegion = kHistBytes + kBlock * 16u;  // histograms + 128-bit sorted records
+
+__host__ __device__ constexpr uint32_t qse_fast_smem_bytes() {
+    return kFastRegion + kMaxBins * 2u + kMaxBins * 2u + kBlock * 2u + kStageWords * 4u;
+}
+
+struct QseFastShared {
+    uint32_t minkey[kMaxFields];
+    uint32_t maxkey[kMaxFields];
+    uint32_t flags;                 // bit 0: non-finite value, bit 1: a value needs a fallback candidate
+    uint32_t maxcnt, maxdelta;
+    uint32_t warp_tot[kWarps], warp_nz[kWarps];
+};
+
+// Quantise the thread's 4 values of field f (fast candidate only), add the
+// field's segId to the key and append its code to the record words.
+template <int NW>
+__device__ __forceinline__ void quantise_append(const float (&x)[4], const bool (&valid)[4], float mn,
+                                                const FieldParams& p, bool pos, uint32_t o, uint32_t ks,
+                                                uint32_t wf, uint32_t (&key)[4], uint32_t (&rw)[4][4],
+                                                bool& pend) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float tt = __fmaf_rn(__fsub_rn(x[r], mn), p.inv, 0.5f);
+        const float u = __fadd_rd(tt, 8388608.0f);  // 2^23 + floor(t), t < 2^23 here
+        uint32_t q = __float_as_uint(u) - kMagic23;
+        const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), p.s, mn);
+        pend |= valid[r] && !(fabsf(__fsub_rn(x[r], xh)) <= p.ebchk);
+        q = valid[r] ? q : 0u;
+        uint32_t code = q;
+        if (pos) {
+            key[r] |= (q >> o) << ks;
+            code = q & ((1u << o) - 1u);
+        }
+        // append below the record so far (field 0 ends most significant)
+        if (NW == 4) {
+            rw[r][3] = __funnelshift_l(rw[r][2], rw[r][3], wf);
+            rw[r][2] = __funnelshift_l(rw[r][1], rw[r][2], wf);
+        }
+        rw[r][1] = __funnelshift_l(rw[r][0], rw[r][1], wf);
+        rw[r][0] = (rw[r][0] << wf) | code;
+    }
+}
+
+template <int F, bool FULL>
+__device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S) {
+    constexpr int P = F < 3 ? F : 3;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint32_t b = blockIdx.x;
+    const uint64_t first = (uint64_t)b * kBlock;
+    const int n_b = FULL ? kBlock : (int)(a.n - first);
+    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
+    uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
+    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastRegion);        // [512]
+    uint16_t* cnt = uniq + kMaxBins;                                         // [512]
+    uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
+    uint32_t* out = a.temp + (size_t)b * a.slot_words;
+
+    if (t < F) {
+        S.minkey[t] = 0xffffffffu;
+        S.maxkey[t] = 0u;
+    }
+    if (t == 0) {
+        S.flags = 0u;
+        S.maxcnt = 0u;
+        S.maxdelta = 0u;
+    }
+    {
+        uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
+#pragma unroll
+        for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
+        for (uint32_t k = t; k < kStageWords; k += kThreads) stage[k] = 0u;
+    }
+
+    // ---- 1. load (coalesced, streaming); block minimum and maximum
+    bool valid[4];
+    float x[F][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float* src = a.fields[f] + first + 128 * w + lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
+    }
+    __syncthreads();  // shared reduction slots initialised (the loads are in flight)
+    float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (valid[r]) {
+                probe = __fmaf_rn(x[f][r], 0.0f, probe);
+                lo = fminf(lo, x[f][r]);
+                hi = fmaxf(hi, x[f][r]);
+            }
+        }
+        const uint32_t lk = __reduce_min_sync(0xffffffffu, lo == INFINITY ? 0xffffffffu : order_key(lo));
+        const uint32_t hk = __reduce_max_sync(0xffffffffu, hi == -INFINITY ? 0u : order_key(hi));
+        if (lane == 0) {
+            atomicMin(&S.minkey[f], lk);
+            atomicMax(&S.maxkey[f], hk);
+        }
+    }
+    if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
+    __syncthreads();  // A
+    if (S.flags & 1u) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 2. widths from the block maxima: q0 = floor(fma(x - min, 1/s, 1/2))
+    // is monotone in x, so when every value keeps its first candidate the
+    // largest code is q0 of the block maximum
+    float mn[F];
+    uint32_t bits[F], o[F], wf[F], kshift[F], W = 0, keybits = 0;
+    bool big = false;
+    {
+        uint32_t g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            const float m = from_order_key(S.minkey[f]);
+            mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
+            const float tq = __fmaf_rn(__fsub_rn(from_order_key(S.maxkey[f]), mn[f]), p.inv, 0.5f);
+            big |= !(tq < 8388608.0f);
+            bits[f] = bit_width(__float_as_uint(__fadd_rd(tq, 8388608.0f)) - kMagic23);
+            g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
+            o[f] = f < P ? bits[f] - g[f] : 0u;
+            wf[f] = f < P ? o[f] : bits[f];
+        }
+        uint32_t ks = 0;
+#pragma unroll
+        for (int f = F - 1; f >= 0; --f) {
+            kshift[f] = ks;
+            ks += g[f];
+            W += wf[f];
+        }
+        keybits = ks;
+    }
+    if (big || W > kFastRecordBits) {
+        // left to the general kernel (uniform decision)
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = b;
+        return;
+    }
+
+    // ---- 3. quantise, key and record in one pass
+    uint32_t key[4] = {0u, 0u, 0u, 0u};
+    uint32_t rw[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rw[r][0] = rw[r][1] = rw[r][2] = rw[r][3] = 0u;
+    bool pend = false;
+    if (W <= 64u) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            quantise_append<2>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            quantise_append<4>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+        }
+    }
+    if (__any_sync(0xffffffffu, pend) && lane == 0) atomicOr(&S.flags, 2u);
+
+    // ---- 4. stable counting sort: warp-local ranks in storage order
+    uint16_t* myhist = hist + w * kMaxBins;
+    uint32_t rank[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? key[r] : 0xffffffffu);
+        uint32_t before = 0u;
+        if (valid[r]) before = myhist[key[r]];
+        __syncwarp();
+        if (valid[r] && lane == 31 - __clz(peers)) myhist[key[r]] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        rank[r] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();  // C
+    if (S.flags & 2u) {
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = b;
+        return;
+    }
+
+    // ---- 4b. scan over (bin, warp): sorted positions and the run-length code
+    const int nbins = 1 << keybits;
+    const int b0 = 2 * t;
+    uint32_t c0 = 0, c1 = 0;
+    uint32_t pre[kWarps];  // (prefix of bin b0) | (prefix of bin b0+1) << 16
+    if (b0 < nbins) {
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t pair = *reinterpret_cast<const uint32_t*>(hist + ww * kMaxBins + b0);
+            pre[ww] = c0 | (c1 << 16);
+            c0 += pair & 0xffffu;
+            c1 += pair >> 16;
+        }
+    }
+    const uint32_t tot = c0 + c1;
+    const uint32_t nz = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+    const uint32_t incl_tot = warp_incl_sum(tot);
+    const uint32_t incl_nz = warp_incl_sum(nz);
+    const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
+    if (lane == 31) {
+        S.warp_tot[w] = incl_tot;
+        S.warp_nz[w] = incl_nz;
+    }
+    if (lane == 0) atomicMax(&S.maxcnt, cmax);
+    __syncthreads();  // D
+    uint32_t base_tot = 0, base_nz = 0, U = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww];
+        if (ww < w) {
+            base_tot += vt;
+            base_nz += vn;
+        }
+        U += vn;
+    }
+    if (b0 < nbins) {
+        const uint32_t start0 = base_tot + incl_tot - tot, start1 = start0 + c0;
+        const uint32_t idx0 = base_nz + incl_nz - nz, idx1 = idx0 + (c0 ? 1u : 0u);
+        const uint32_t base2 = start0 | (start1 << 16);  // neither half overflows: both < 1024
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww)
+            *reinterpret_cast<uint32_t*>(hist + ww * kMaxBins + b0) = base2 + pre[ww];
+        if (c0) {
+            uniq[idx0] = (uint16_t)b0;
+            cnt[idx0] = (uint16_t)c0;
+        }
+        if (c1) {
+            uniq[idx1] = (uint16_t)(b0 + 1);
+            cnt[idx1] = (uint16_t)c1;
+        }
+    }
+    __syncthreads();  // E
+
+    // ---- 4c. scatter to sorted order; deltas of the unique ids
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (valid[r]) {
+            const uint32_t dest = myhist[key[r]] + rank[r];
+            recs[dest] = make_uint4(rw[r][0], rw[r][1], rw[r][2], rw[r][3]);
+            if (a.perm) sperm[dest] = (uint16_t)(128 * w + 32 * r + lane);
+        }
+    }
+    {
+        uint32_t dmax = 0;
+        for (uint32_t k = t; k < U; k += kThreads) {
+            const uint32_t d = (uint32_t)uniq[k] - (k ? (uint32_t)uniq[k - 1] : 0u);
+            dmax = max(dmax, d);
+        }
+        dmax = __reduce_max_sync(0xffffffffu, dmax);
+        if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
+    }
+    __syncthreads();  // F
+
+    // ---- encoded size; raw when not smaller (keeps the bound size a bound)
+    const uint32_t wd = bit_width(S.maxdelta), wc = bit_width(S.maxcnt);
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc);
+    const uint32_t rwords = ceil_words((uint32_t)n_b * W);
+    const uint32_t enc = hdr + dwords + cwords + rwords;
+    if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 5. block header and the three arrays (Section 4.3), assembled in the
+    // zeroed staging words by thread-serial appenders, then copied out
+    if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
+    if (t >= 1 && t <= F) {
+        float m = 0.0f;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if (f == t - 1) m = mn[f];
+        stage[t] = __float_as_uint(m);
+    }
+    if (t < ((F + 3) >> 2)) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if ((f >> 2) == t) word |= bits[f] << (8 * (f & 3));
+        stage[1 + F + t] = word;
+    }
+    {
+        const uint32_t k0 = 2u * (uint32_t)t;
+        if (k0 < U && wd) {
+            BitAppender ap(32u * hdr + k0 * wd);
+            ap.put(stage, (uint32_t)uniq[k0] - (k0 ? (uint32_t)uniq[k0 - 1] : 0u), wd);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)uniq[k0 + 1] - (uint32_t)uniq[k0], wd);
+            ap.finish(stage);
+        }
+        if (k0 < U && wc) {
+            BitAppender ap(32u * (hdr + dwords) + k0 * wc);
+            ap.put(stage, (uint32_t)cnt[k0], wc);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)cnt[k0 + 1], wc);
+            ap.finish(stage);
+        }
+    }
+    const uint32_t len = (uint32_t)n_b;
+    {
+        const uint32_t j0 = 4u * (uint32_t)t;
+        if (j0 < len && W) {
+            BitAppender ap(32u * (hdr + dwords + cwords) + j0 * W);
+            const uint32_t w0 = min(W, 32u), w1 = min(W - w0, 32u), w2 = min(W - w0 - w1, 32u), w3 = W - w0 - w1 - w2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint4 v = (j0 + e < len) ? recs[j0 + e] : make_uint4(0u, 0u, 0u, 0u);
+                ap.put(stage, v.x, w0);
+                if (w1) ap.put(stage, v.y, w1);
+                if (w2) ap.put(stage, v.z, w2);
+                if (w3) ap.put(stage, v.w, w3);
+            }
+            ap.finish(stage);
+        }
+    }
+    __syncthreads();
+    {
+        const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+        uint4* o4 = reinterpret_cast<uint4*>(out);
+        for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
+        for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+    }
+    if (a.perm)
+        for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
+    if (t == 0) a.sizes[b] = enc;
+}
+
+template <int F>
+__global__ void __launch_bounds__(kThreads, 4) gpz_qse_kernel(QseArgs a) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ QseFastShared S;
     if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
-        qse_block<F, true>(a, dsm, S);
+        qse_block_fast<F, true>(a, dsm, S);
     else
-        qse_block<F, false>(a, dsm, S);
+        qse_block_fast<F, false>(a, dsm, S);
 }
 
 template <int F>
 cudaError_t launch_qse_f(const QseArgs& a, cudaStream_t s) {
-    const size_t smem = qse_smem_bytes(F);
+    const size_t smem = qse_fast_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(gpz_qse_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gpz_qse_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     gpz_qse_kernel<F><<<a.nblocks, kThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the blocks left to the general path (usually none); the grid walks the list
+    const size_t gsmem = qse_smem_bytes(F);
+    e = cudaFuncSetAttribute(gpz_qse_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+    if (e != cudaSuccess) return e;
+    const unsigned ggrid = a.nblocks < 2u * 152u ? a.nblocks : 2u * 152u;
+    gpz_qse_general_kernel<F><<<ggrid, kThreads, gsmem, s>>>(a);
     return cudaGetLastError();
 }
 
