@@ -130,7 +130,7 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
 }
 
 template <int F>
-__global__ void __launch_bounds__(kThreads, 4) gpz_decompress_kernel(DecArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) gpz_decompress_kernel(DecArgs a) {
     __shared__ uint16_t uniq[kMaxBins];
     __shared__ uint32_t mask[32], mpre[32];
     __shared__ uint32_t warp_u[kWarps], warp_c[kWarps];
