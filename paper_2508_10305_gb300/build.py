@@ -1,4 +1,4 @@
-"""Build libgpz.so (the C ABI of include/gpz.h) in-tree with nvcc for sm_103a.
+"""Build libgpz.so (the C ABI of include/gpz.h and include/gpz_batch.h) in-tree with nvcc for sm_103a.
 
 Each .cu file under csrc/ is compiled to an object in parallel, then linked
 into paper_2508_10305_gb300/libgpz.so with the static CUDA runtime.
@@ -42,8 +42,9 @@ def _stale(target, deps):
 def build(force=False, verbose=False, ptxas_info=False):
     """Compile libgpz.so if missing or older than any source; return its path."""
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    headers.append(os.path.join(ROOT, "include", "gpz.h"))
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".hpp"))]
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     deps = srcs + headers + [os.path.abspath(__file__)]
     if not force and not _stale(LIB, deps):
         return LIB

@@ -9,9 +9,18 @@
 #include <mutex>
 
 #include "gpz.h"
+#include "gpz_host.hpp"
 #include "gpz_internal.cuh"
 
 using namespace gpz;
+using namespace gpz::host;
+
+namespace gpz {
+namespace host {
+StageTimer g_timer;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace host
+}  // namespace gpz
 
 namespace {
 
@@ -19,12 +28,6 @@ constexpr uint64_t kAlign = 256;
 constexpr int kRangeGridMax = 152 * 4;
 constexpr uint64_t kCtrlBytes = 256;    // status, tile counter, range counter, out size
 constexpr uint64_t kParamBytes = 256;   // FieldParams[8]
-
-std::atomic<uint64_t> g_launches{0};
-
-uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
-
-uint64_t nblocks_of(uint64_t n) { return (n + kBlock - 1) / kBlock; }
 
 uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * kBlock, 4); }
 
@@ -56,76 +59,6 @@ WsLayout layout_of(uint64_t n, int F) {
     L.total = o;
     return L;
 }
-
-// The constants of one field from its bound eb: step eb * 63/32 (2 eb less
-// 1/64), reciprocal, and the verification threshold RD32(eb * (1 - 2^-22)).
-FieldParams finalise(double eb) {
-    FieldParams p;
-    p.eb = (float)eb;
-    p.s = (float)(eb * 1.96875);
-    p.inv = (float)(1.0 / (double)p.s);
-    const double t = eb * (1.0 - std::ldexp(1.0, -22));
-    float c = (float)t;
-    if ((double)c > t) c = std::nextafterf(c, -INFINITY);
-    p.ebchk = c;
-    return p;
-}
-
-// ---------------------------------------------------------------- stage timing
-//
-// When enabled, each call records one event on its stream before its first
-// kernel and one after each kernel, from a pool; gpz_stage_times resolves
-// the logged pairs into per-stage totals and recycles the pool.
-
-constexpr int kEventPool = 8192;
-
-struct StageTimer {
-    std::mutex mu;
-    bool enabled = false;
-    bool created = false;
-    cudaEvent_t ev[kEventPool] = {};
-    int used = 0;
-    struct Span {
-        const char* name;
-        int a, b;
-    };
-    Span spans[kEventPool];
-    int nspans = 0;
-} g_timer;
-
-struct Recorder {
-    bool on = false;
-    cudaStream_t s;
-    int last = -1;
-    explicit Recorder(cudaStream_t stream) : s(stream) {}
-    // Start of the call's first kernel (after its memsets).
-    void begin() {
-        std::lock_guard<std::mutex> g(g_timer.mu);
-        if (!g_timer.enabled) return;
-        if (!g_timer.created) {
-            for (auto& e : g_timer.ev) cudaEventCreate(&e);
-            g_timer.created = true;
-        }
-        if (g_timer.used + 8 >= kEventPool) return;  // pool full until the next read
-        on = true;
-        last = g_timer.used++;
-        cudaEventRecord(g_timer.ev[last], s);
-    }
-    void mark(const char* name) {
-        ++g_launches;
-        if (!on) return;
-        std::lock_guard<std::mutex> g(g_timer.mu);
-        if (g_timer.used >= kEventPool) return;
-        const int e = g_timer.used++;
-        cudaEventRecord(g_timer.ev[e], s);
-        g_timer.spans[g_timer.nspans++] = {name, last, e};
-        last = e;
-    }
-};
-
-gpz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GPZ_OK : GPZ_ERR_CUDA; }
-
-bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 gpz_status read_status(void* d_ws, cudaStream_t s, bool clear) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return GPZ_ERR_CUDA;

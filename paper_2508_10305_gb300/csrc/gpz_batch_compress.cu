@@ -1,0 +1,455 @@
+// gpz_batch_compress.cu -- batched compression: every chunk of a batch in one
+// persistent launch (range pass of the relative-bound chunks + the fused
+// quantise/sort/encode of every block, Sections 4.1-4.3), then the rare
+// general-path blocks, one 64-bit look-back scan over all blocks and one
+// compaction pass that also writes every chunk's header and block table
+// (Section 4.4, steps 2 and 3).  Each chunk's stream is the one a call of its
+// own produces: the per-block code is the single-array code.
+#include "gpz_batch.cuh"
+#include "gpz_qse_block.cuh"
+
+namespace gpz {
+
+namespace {
+
+// Per-chunk argument block of the per-block code, built in shared memory.
+// The constants are copied in (d_params stays null), read from L2: a
+// relative bound's constants were written during this launch.
+__device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint32_t c, QseArgs& A) {
+    const int t = threadIdx.x;
+    const BatchChunk* ch = g.chunks + c;
+    if (t < kMaxFields) A.fields[t] = ch->in[t];
+    if (t >= 32 && t < 32 + 4 * kMaxFields) {
+        const int f = (t - 32) >> 2, k = (t - 32) & 3;
+        const uint32_t* src = ch->mode ? reinterpret_cast<const uint32_t*>(g.rparams + (size_t)c * kMaxFields + f)
+                                       : reinterpret_cast<const uint32_t*>(ch->params + f);
+        reinterpret_cast<uint32_t*>(A.params + f)[k] = __ldcg(src + k);
+    }
+    if (t == 64) {
+        A.n = ch->n;
+        A.nblocks = ch->nblocks;
+        A.F = ch->F;
+        A.G = ch->G;
+        A.bulk_ok = ch->bulk_ok;
+        A.d_params = nullptr;
+        A.temp = g.temp + ch->temp_base;
+        A.slot_words = batch_slot_words(ch->F);
+        A.sizes = g.sizes + ch->block_base;
+        A.perm = ch->perm;
+        A.status = g.chunk_status + c;
+        A.general_list = g.general_list;
+        A.general_count = g.general_count;
+    }
+}
+
+// One range item: minimum and maximum of one slice of one field of a
+// relative-bound chunk, merged into the chunk's order keys; the CTA that
+// finishes the chunk's last item writes its constants and raises its flag.
+__device__ __forceinline__ void range_item(const BatchCompressArgs& g, uint32_t c, uint32_t local, float2* red) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const BatchChunk* ch = g.chunks + c;
+    const uint32_t slices = ch->range_slices;
+    const uint32_t f = local / slices, sl = local - f * slices;
+    const uint64_t n = ch->n;
+    const uint64_t start = (uint64_t)sl * g.slice;
+    const uint64_t end = start + g.slice < n ? start + g.slice : n;
+    const float* x = ch->in[f];
+    float lo = INFINITY, hi = -INFINITY;
+    uint64_t tail = start + t;
+    if (ch->bulk_ok && start < end) {
+        // start is a multiple of the slice (itself a multiple of 1024): aligned
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const uint64_t e4 = end >> 2;
+        uint64_t i = (start >> 2) + t;
+        for (; i + 3 * kThreads < e4; i += 4 * kThreads) {
+            const float4 v0 = __ldcs(x4 + i), v1 = __ldcs(x4 + i + kThreads), v2 = __ldcs(x4 + i + 2 * kThreads),
+                         v3 = __ldcs(x4 + i + 3 * kThreads);
+            lo = fminf(lo, fminf(fminf(fminf(v0.x, v0.y), fminf(v0.z, v0.w)), fminf(fminf(v1.x, v1.y), fminf(v1.z, v1.w))));
+            lo = fminf(lo, fminf(fminf(fminf(v2.x, v2.y), fminf(v2.z, v2.w)), fminf(fminf(v3.x, v3.y), fminf(v3.z, v3.w))));
+            hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v0.x, v0.y), fmaxf(v0.z, v0.w)), fmaxf(fmaxf(v1.x, v1.y), fmaxf(v1.z, v1.w))));
+            hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v2.x, v2.y), fmaxf(v2.z, v2.w)), fmaxf(fmaxf(v3.x, v3.y), fmaxf(v3.z, v3.w))));
+        }
+        for (; i < e4; i += kThreads) {
+            const float4 v = __ldcs(x4 + i);
+            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+        tail = (e4 << 2) + t;
+    }
+    for (uint64_t i = tail; i < end; i += kThreads) {
+        const float v = x[i];
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    lo = warp_min_f32(lo);
+    hi = warp_max_f32(hi);
+    if (lane == 0) red[warp] = make_float2(lo, hi);
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < kWarps; ++w) {
+            lo = fminf(lo, red[w].x);
+            hi = fmaxf(hi, red[w].y);
+        }
+        uint32_t* keys = g.rkeys + ((size_t)c * kMaxFields + f) * 2;
+        if (lo <= hi) {  // NaNs are ignored, as fminf / fmaxf do
+            atomicMax(keys, ~order_key(lo));
+            atomicMax(keys + 1, order_key(hi));
+        }
+        __threadfence();
+        const uint32_t items = (uint32_t)ch->F * slices;
+        if (atomicAdd(g.rdone + c, 1u) == items - 1) {
+            __threadfence();
+            for (int ff = 0; ff < ch->F; ++ff) {
+                const volatile uint32_t* k = g.rkeys + ((size_t)c * kMaxFields + ff) * 2;
+                const uint32_t kmin = k[0], kmax = k[1];
+                const float flo = kmax ? from_order_key(~kmin) : INFINITY;
+                const float fhi = kmax ? from_order_key(kmax) : -INFINITY;
+                g.rparams[(size_t)c * kMaxFields + ff] = range_params(flo, fhi, ch->rel[ff]);
+            }
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(g.ready + c), "r"(1u) : "memory");
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+}  // namespace
+
+template <int F>
+__global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCompressArgs g) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ QseFastShared S;
+    __shared__ QseArgs A;
+    __shared__ float2 red[kWarps];
+    __shared__ uint32_t s_ticket, s_ok;
+    const int t = threadIdx.x;
+    const uint32_t total = g.range_items + g.total_blocks;
+    const uint32_t* range_end = g.range_end + g.first;
+    const uint32_t* block_end = g.block_end + g.first;
+    uint32_t rcur = 0, bcur = 0;  // group-relative chunk cursors
+    uint32_t loaded = 0xffffffffu;
+    bool loaded_ok = false;
+    if (t == 0) s_ticket = atomicAdd(g.ticket, g.claim);
+    __syncthreads();
+    uint32_t base = s_ticket;
+    while (base < total) {
+        uint32_t next = 0;
+        if (t == 0) next = atomicAdd(g.ticket, g.claim);  // in flight while the items run
+        const uint32_t stop = total - base < g.claim ? total : base + g.claim;
+        for (uint32_t q = base; q < stop; ++q) {
+            if (q < g.range_items) {
+                const uint32_t r = g.range_first + q;
+                rcur = find_chunk(range_end, g.nchunks, r, rcur);
+                const uint32_t c = g.first + rcur;
+                range_item(g, c, r - g.chunks[c].range_base, red);
+            } else {
+                const uint32_t gb = g.block_first + (q - g.range_items);
+                bcur = find_chunk(block_end, g.nchunks, gb, bcur);
+                const uint32_t c = g.first + bcur;
+                if (c != loaded) {
+                    if (t == 0) {
+                        uint32_t ok = 1u;
+                        if (g.chunks[c].mode) {  // wait for the chunk's relative constants
+                            const long long t0 = clock64();
+                            while (ld_acquire_u32(g.ready + c) == 0u) {
+                                if (clock64() - t0 > (1ll << 31)) {
+                                    set_status(g.chunk_status + c, kStTimeout);
+                                    ok = 0u;
+                                    break;
+                                }
+                                __nanosleep(64);
+                            }
+                        }
+                        s_ok = ok;
+                    }
+                    __syncthreads();
+                    load_chunk_args(g, c, A);
+                    __syncthreads();
+                    loaded = c;
+                    loaded_ok = s_ok != 0u;
+                }
+                const uint32_t b = gb - g.chunks[c].block_base;
+                if (!loaded_ok) {
+                    if (t == 0) A.sizes[b] = 0u;  // the chunk is reported as timed out
+                } else if ((uint64_t)(b + 1) * kBlock <= A.n) {
+                    qse_block_fast<F, true>(A, dsm, S, b, gb);
+                } else {
+                    qse_block_fast<F, false>(A, dsm, S, b, gb);
+                }
+            }
+            __syncthreads();
+        }
+        if (t == 0) s_ticket = next;
+        __syncthreads();
+        base = s_ticket;
+    }
+}
+
+// Blocks the fast path left to the general one (rare); the grid walks the
+// group's list.
+template <int F>
+__global__ void __launch_bounds__(kThreads, 2) gpz_batch_general_kernel(BatchCompressArgs g) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    __shared__ QseShared S;
+    __shared__ QseArgs A;
+    const uint32_t count = *(volatile const uint32_t*)g.general_count;
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint32_t gb = __ldcg(g.general_list + i);
+        const uint32_t c = g.first + find_chunk(g.block_end + g.first, g.nchunks, gb, 0);
+        load_chunk_args(g, c, A);
+        __syncthreads();
+        const uint32_t b = gb - g.chunks[c].block_base;
+        if ((uint64_t)(b + 1) * kBlock <= A.n)
+            qse_block_general<F, true>(A, dsm, S, b);
+        else
+            qse_block_general<F, false>(A, dsm, S, b);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ 64-bit look-back scan over all blocks
+
+namespace {
+
+constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
+constexpr unsigned long long kAggregate = 1ull << 62;
+constexpr unsigned long long kPrefix = 2ull << 62;
+constexpr uint32_t kMaxBlockWords = 1u + (uint32_t)kMaxFields * (uint32_t)kBlock;
+
+__device__ unsigned long long lookback64(const BatchScanArgs& a, uint32_t tile) {
+    unsigned long long excl = 0;
+    int p = (int)tile - 1;
+    while (p >= 0) {
+        const long long t0 = clock64();
+        unsigned long long st;
+        for (;;) {
+            st = ld_acquire_u64(a.tile_state + p);
+            if ((st >> 62) != 0ull) break;
+            if (clock64() - t0 > (1ll << 31)) {
+                set_status(a.status, kStTimeout);
+                st = kPrefix;  // give up: treat the predecessor's prefix as 0
+                break;
+            }
+            __nanosleep(32);
+        }
+        excl += st & kValMask;
+        if ((st >> 62) == 2ull) break;
+        --p;
+    }
+    return excl;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kScanThreads) gpz_batch_scan_kernel(BatchScanArgs a) {
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t start = (uint64_t)tile * kScanTile + (uint64_t)tid * kScanItems;
+    uint32_t v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        v[k] = (start + k < a.total_blocks) ? min(__ldcg(a.sizes + start + k), kMaxBlockWords) : 0u;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
+    const uint32_t incl = warp_incl_sum(sum);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t warp_base = 0, aggregate = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const uint32_t x = s_warp[w];
+        if (w < warp) warp_base += x;
+        aggregate += x;
+    }
+    if (tid == 0) {
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            st_release_u64(a.tile_state, kPrefix | aggregate);
+        } else {
+            st_release_u64(a.tile_state + tile, kAggregate | aggregate);
+            excl = lookback64(a, tile);
+            st_release_u64(a.tile_state + tile, kPrefix | (excl + aggregate));
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + warp_base + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (start + k <= a.total_blocks) a.offsets[start + k] = run;
+        run += v[k];
+    }
+}
+
+// ------------------------------------------------------------------ compaction, tables and headers
+
+__global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(BatchCompactArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * kCompactWarps;
+    const uint32_t items = a.total_blocks + a.nchunks;
+    uint32_t cur = 0;
+    for (uint32_t q = blockIdx.x * kCompactWarps + warp; q < items; q += nwarps) {
+        if (q < a.total_blocks) {
+            cur = find_chunk(a.block_end, a.nchunks, q, cur);
+            const BatchChunk* ch = a.chunks + cur;
+            const uint32_t F = (uint32_t)ch->F, nb = ch->nblocks, b = q - ch->block_base;
+            const uint64_t n = ch->n;
+            const unsigned long long base = __ldcg(a.offsets + ch->block_base);
+            const unsigned long long o0 = __ldcg(a.offsets + q), o1 = __ldcg(a.offsets + q + 1);
+            const uint64_t first = (uint64_t)b * kBlock;
+            const uint32_t n_b = (uint32_t)(n - first < (uint64_t)kBlock ? n - first : (uint64_t)kBlock);
+            const uint64_t table_start = kHeaderWords + 2ull * F;
+            const uint64_t payload_start = table_start + nb + 1;
+            const unsigned long long rel = o0 - base, len = o1 - o0;
+            uint32_t* dst = ch->dst;
+            if (len > 1ull + F * n_b || payload_start + rel + len > ch->words) {
+                if (lane == 0) set_status(a.chunk_status + cur, kStCapacity);
+                continue;
+            }
+            if (lane == 0) dst[table_start + b] = (uint32_t)rel;
+            const uint32_t* src = a.temp + ch->temp_base + (uint64_t)b * batch_slot_words((int)F);
+            uint32_t* out = dst + payload_start + rel;
+            const uint32_t L = (uint32_t)len;
+            uint32_t k = lane;
+            for (; k + 96 < L; k += 128) {
+                const uint32_t x0 = __ldcs(src + k), x1 = __ldcs(src + k + 32), x2 = __ldcs(src + k + 64),
+                               x3 = __ldcs(src + k + 96);
+                out[k] = x0;
+                out[k + 32] = x1;
+                out[k + 64] = x2;
+                out[k + 96] = x3;
+            }
+            for (; k < L; k += 32) out[k] = __ldcs(src + k);
+        } else {
+            // the chunk's stream header, constants, closing table entry and size
+            const uint32_t c = q - a.total_blocks;
+            const BatchChunk* ch = a.chunks + c;
+            const uint32_t F = (uint32_t)ch->F, nb = ch->nblocks;
+            const unsigned long long payload = __ldcg(a.offsets + ch->block_base + nb) - __ldcg(a.offsets + ch->block_base);
+            const uint64_t table_start = kHeaderWords + 2ull * F;
+            const uint64_t payload_start = table_start + nb + 1;
+            uint32_t* dst = ch->dst;
+            if (payload_start + payload > ch->words) {
+                if (lane == 0) {
+                    set_status(a.chunk_status + c, kStCapacity);
+                    a.out_sizes[ch->index] = 0ull;
+                }
+                continue;
+            }
+            if (lane < kHeaderWords) {
+                uint32_t v = 0;
+                switch (lane) {
+                    case 0: v = kMagic; break;
+                    case 1: v = kVersion; break;
+                    case 2: v = F; break;
+                    case 3: v = (uint32_t)ch->G; break;
+                    case 4: v = (uint32_t)kBlock; break;
+                    case 5: v = (uint32_t)ch->mode; break;
+                    case 6: v = (uint32_t)(ch->n & 0xffffffffull); break;
+                    case 7: v = (uint32_t)(ch->n >> 32); break;
+                    case 8: v = nb; break;
+                    case 9: v = (uint32_t)payload; break;
+                    default: v = 0; break;
+                }
+                dst[lane] = v;
+            }
+            if ((uint32_t)lane < 2 * F) {
+                const int f = lane >> 1;
+                const FieldParams* p = ch->mode ? a.rparams + (size_t)c * kMaxFields + f : ch->params + f;
+                const uint32_t* pw = reinterpret_cast<const uint32_t*>(p);
+                dst[kHeaderWords + lane] = __ldcg((lane & 1) ? pw + 1 : pw);  // eb, then the step
+            }
+            if (lane == 0) {
+                dst[table_start + nb] = (uint32_t)payload;
+                a.out_sizes[ch->index] = 4ull * (payload_start + payload);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launches
+
+template <int F>
+int max_ctas_f() {
+    int n = 0;
+    if (cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)qse_fast_smem_bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(gpz_batch_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)qse_smem_bytes(F)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gpz_batch_compress_kernel<F>, kThreads,
+                                                      qse_fast_smem_bytes()) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Also sets the kernels' shared-memory attributes: call once before launching.
+int batch_compress_max_ctas_per_sm(int F) {
+    switch (F) {
+        case 1: return max_ctas_f<1>();
+        case 2: return max_ctas_f<2>();
+        case 3: return max_ctas_f<3>();
+        case 4: return max_ctas_f<4>();
+        case 5: return max_ctas_f<5>();
+        case 6: return max_ctas_f<6>();
+        case 7: return max_ctas_f<7>();
+        case 8: return max_ctas_f<8>();
+    }
+    return 0;
+}
+
+template <int F>
+void launch_f(const BatchCompressArgs& a, int grid, cudaStream_t s, bool general) {
+    if (general)
+        gpz_batch_general_kernel<F><<<grid, kThreads, qse_smem_bytes(F), s>>>(a);
+    else
+        gpz_batch_compress_kernel<F><<<grid, kThreads, qse_fast_smem_bytes(), s>>>(a);
+}
+
+cudaError_t launch_group(const BatchCompressArgs& a, int F, int grid, cudaStream_t s, bool general) {
+    switch (F) {
+        case 1: launch_f<1>(a, grid, s, general); break;
+        case 2: launch_f<2>(a, grid, s, general); break;
+        case 3: launch_f<3>(a, grid, s, general); break;
+        case 4: launch_f<4>(a, grid, s, general); break;
+        case 5: launch_f<5>(a, grid, s, general); break;
+        case 6: launch_f<6>(a, grid, s, general); break;
+        case 7: launch_f<7>(a, grid, s, general); break;
+        case 8: launch_f<8>(a, grid, s, general); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, int grid, cudaStream_t s) {
+    return launch_group(a, F, grid, s, false);
+}
+
+cudaError_t launch_batch_general(const BatchCompressArgs& a, int F, int grid, cudaStream_t s) {
+    return launch_group(a, F, grid, s, true);
+}
+
+cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s) {
+    const unsigned tiles = (unsigned)(((uint64_t)a.total_blocks + 1 + kScanTile - 1) / kScanTile);
+    gpz_batch_scan_kernel<<<tiles, kScanThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_compact(const BatchCompactArgs& a, int grid, cudaStream_t s) {
+    gpz_batch_compact_kernel<<<grid, 32 * kCompactWarps, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gpz

@@ -1,0 +1,381 @@
+// gpz_decode_block.cuh -- the per-block body of GPZ decompression (Section
+// 3.2: the reverse of compression, without sorting), shared by the
+// single-stream kernel (gpz_decode.cu) and the batched persistent kernel
+// (gpz_batch_decode.cu).  See gpz_decode.cu for the design.
+#pragma once
+
+#include "gpz_internal.cuh"
+
+namespace gpz {
+
+
+constexpr int kDecWarps = kDecThreads / 32;
+// deltas (<= 512 x 9 bits) + counts (<= 512 x 11 bits) + records (<= 1024 x 128 bits)
+constexpr uint32_t kDecStageWords = 144u + 176u + 4096u;
+
+
+__device__ __forceinline__ uint32_t mask_bits(uint32_t w) { return w >= 32u ? 0xffffffffu : ((1u << w) - 1u); }
+
+// Value k of a fixed-length array of width w (<= 31) starting at A.
+__device__ __forceinline__ uint32_t extract(const uint32_t* A, uint32_t k, uint32_t w) {
+    if (w == 0u) return 0u;
+    const uint32_t p = k * w;
+    const uint32_t wi = p >> 5, sh = p & 31u;
+    const uint32_t lo = __ldg(A + wi);
+    const uint32_t hi = (sh + w > 32u) ? __ldg(A + wi + 1) : 0u;
+    return __funnelshift_r(lo, hi, sh) & mask_bits(w);
+}
+
+// Value k of a fixed-length array of width w (<= 31) held in shared memory.
+__device__ __forceinline__ uint32_t extract_s(const uint32_t* A, uint32_t k, uint32_t w) {
+    if (w == 0u) return 0u;
+    const uint32_t p = k * w;
+    const uint32_t wi = p >> 5, sh = p & 31u;
+    const uint32_t hi = (sh + w > 32u) ? A[wi + 1] : 0u;
+    return __funnelshift_r(A[wi], hi, sh) & mask_bits(w);
+}
+
+struct DecLayout {
+    uint32_t rs[kMaxFields];  // bit offset of the field in the record
+    uint32_t ks[kMaxFields];  // bit offset of the axis' segId in the key
+    uint32_t of[kMaxFields];  // segOffset bits of a position axis
+    uint32_t gm[kMaxFields];  // segId mask
+    uint32_t cm[kMaxFields];  // code mask
+};
+
+// (float)q for q < 2^23 with two full-rate operations.
+__device__ __forceinline__ float small_u2f(uint32_t q) {
+    return __fsub_rn(__uint_as_float(q + 0x4B000000u), 8388608.0f);
+}
+
+// Rebuild four consecutive values x = fma((float)q, step, min) and store them.
+__device__ __forceinline__ void store4(float* dst, const uint32_t* qv, uint32_t bits, float s, float mn, int left) {
+    float v[4];
+    if (bits <= 23u) {  // uniform: codes below 2^23 convert with one add
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = __fmaf_rn(small_u2f(qv[e]), s, mn);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = __fmaf_rn(__uint2float_rn(qv[e]), s, mn);
+    }
+    if (left >= 4 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < left) dst[e] = v[e];
+    }
+}
+
+// Records wider than 128 bits (rare): every code is read field by field from
+// the stream itself; the block header is re-read here so that the common path
+// passes nothing through memory.
+template <int F>
+__device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* blk, uint32_t rwords_off,
+                                         uint32_t rwords, uint32_t W, uint32_t G, int j0, int n_b, uint64_t first,
+                                         uint32_t key0, uint32_t key1, uint32_t key2, uint32_t key3) {
+    constexpr int P = F < 3 ? F : 3;
+    const uint32_t* R = blk + rwords_off;
+    const uint32_t key[4] = {key0, key1, key2, key3};
+    uint32_t rs = W;
+    uint32_t ks = 0;
+    // walk the fields from the top of the record down: field 0 is most significant
+    uint32_t kacc[F], racc[F], wfv[F], gv[F];
+    {
+        uint32_t r = 0, k = 0;
+        for (int f = F - 1; f >= 0; --f) {
+            const uint32_t bf = (__ldg(blk + 1 + F + (f >> 2)) >> (8 * (f & 3))) & 0xffu;
+            const uint32_t g = f < P ? min(G, bf) : 0u;
+            gv[f] = g;
+            wfv[f] = f < P ? bf - g : bf;
+            racc[f] = r;
+            kacc[f] = k;
+            r += wfv[f];
+            k += g;
+        }
+    }
+    (void)rs;
+    (void)ks;
+    for (int f = 0; f < F; ++f) {
+        const uint32_t bf = (__ldg(blk + 1 + F + (f >> 2)) >> (8 * (f & 3))) & 0xffu;
+        const float mnf = __uint_as_float(__ldg(blk + 1 + f));
+        const float sf = __uint_as_float(__ldg(a.stream + kHeaderWords + 2 * f + 1));
+        const uint32_t cm = mask_bits(wfv[f]), gm = mask_bits(gv[f]);
+        uint32_t qv[4];
+        for (int e = 0; e < 4; ++e) {
+            uint32_t code = 0u;
+            if (cm && j0 + e < n_b) {
+                const uint32_t p = (uint32_t)(j0 + e) * W + racc[f];
+                const uint32_t wi = p >> 5, sh = p & 31u;
+                const uint32_t lo = __ldg(R + wi);
+                const uint32_t hi = (sh + wfv[f] > 32u) && (wi + 1 < rwords) ? __ldg(R + wi + 1) : 0u;
+                code = __funnelshift_r(lo, hi, sh) & cm;
+            }
+            qv[e] = f < P ? (code | (((key[e] >> kacc[f]) & gm) << wfv[f])) : code;
+        }
+        store4(a.out[f] + first + j0, qv, bf, sf, mnf, n_b - j0);
+    }
+}
+
+struct DecShared {
+    uint16_t uniq[kMaxBins];
+    uint32_t mask[32], mpre[32];
+    uint32_t warp_u[kDecWarps], warp_c[kDecWarps];
+    uint32_t bad;
+    alignas(16) uint32_t stage[kDecStageWords];
+};
+
+// Decode block b of the stream described by a (every thread of the CTA).
+template <int F>
+__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uint32_t b) {
+    uint16_t* uniq = S.uniq;
+    uint32_t* mask = S.mask;
+    uint32_t* mpre = S.mpre;
+    uint32_t* warp_u = S.warp_u;
+    uint32_t* warp_c = S.warp_c;
+    uint32_t& s_bad = S.bad;
+    uint32_t* stage = S.stage;
+    constexpr int P = F < 3 ? F : 3;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint32_t* Sw = a.stream;
+    const uint64_t first = (uint64_t)b * kBlock;
+    const int n_b = (int)((a.n - first) < (uint64_t)kBlock ? (a.n - first) : (uint64_t)kBlock);
+    const uint64_t table_start = kHeaderWords + 2ull * F;
+    const uint64_t payload_start = table_start + a.nblocks + 1;
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    if (t < 32) mask[t] = 0u;
+    if (t == 0) s_bad = 0u;
+
+    // ---- 1. checks, in every warp (broadcast loads; no serial phase)
+    // round trip 1: header words and, when the header fits, the block's table entries
+    const bool header_fits = payload_start <= a.total_words;
+    uint32_t hw = 0;
+    if (lane < kHeaderWords) hw = __ldg(Sw + lane);
+    else if (lane < kHeaderWords + 2 && header_fits) hw = __ldg(Sw + table_start + b + (lane - kHeaderWords));
+    bool ok = true;
+    switch (lane) {
+        case 0: ok = hw == kMagic; break;
+        case 1: ok = hw == kVersion; break;
+        case 2: ok = hw == (uint32_t)F; break;
+        case 3: ok = hw <= (uint32_t)kMaxSegBits; break;
+        case 4: ok = hw == (uint32_t)kBlock; break;
+        case 5: ok = hw <= 1u; break;
+        case 6: ok = hw == (uint32_t)(a.n & 0xffffffffull); break;
+        case 7: ok = hw == (uint32_t)(a.n >> 32); break;
+        case 8: ok = hw == a.nblocks; break;
+        case 9: break;
+        default: ok = lane >= 10 + 6 || hw == 0u; break;
+    }
+    const uint32_t G = __shfl_sync(0xffffffffu, hw, 3);
+    const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 9);
+    const uint32_t off = __shfl_sync(0xffffffffu, hw, kHeaderWords);
+    const uint32_t end = __shfl_sync(0xffffffffu, hw, kHeaderWords + 1);
+    ok = __all_sync(0xffffffffu, ok) && header_fits && payload_start + payload_words <= a.total_words &&
+         off <= end && end <= payload_words && !(b == 0 && off != 0) &&
+         !(b + 1 == a.nblocks && end != payload_words) && end != off;
+    const uint32_t* blk = Sw + payload_start + off;
+    const uint32_t nw = end - off;
+    // round trip 2: the block header (mode word, minima, width bytes), the steps,
+    // and the block's words after its header staged in shared memory (all of
+    // them when they fit; the deltas and counts always fit)
+    if (ok && nw > hdr) {
+        const uint32_t nst = min(nw - hdr, kDecStageWords);
+        for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
+    }
+    uint32_t bw = 0;
+    if (ok && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
+    float step = 0.0f;
+    if (ok && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
+    const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
+    const bool raw = ok && (mode & 1u);
+    if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
+    uint32_t U = 0, wd = 0, wc = 0, W = 0, keybits = 0;
+    uint32_t bits[F];
+    float mn[F], s[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const uint32_t word = __shfl_sync(0xffffffffu, bw, 1 + F + (f >> 2));
+        bits[f] = (word >> (8 * (f & 3))) & 0xffu;
+        mn[f] = __uint_as_float(__shfl_sync(0xffffffffu, bw, 1 + f));
+        s[f] = __shfl_sync(0xffffffffu, step, f);
+    }
+    if (ok && !raw) {
+        U = (mode >> 1) & 0x7ffu;
+        wd = (mode >> 12) & 31u;
+        wc = (mode >> 17) & 31u;
+        ok = (mode >> 22) == 0u && nw >= hdr;
+        // padding bytes of the last width word are zero
+        const uint32_t lastw = __shfl_sync(0xffffffffu, bw, hdr - 1);
+        if ((F & 3) != 0) ok = ok && (lastw >> (8 * (F & 3))) == 0u;
+#pragma unroll
+        for (int f = F - 1; f >= 0; --f) {
+            ok = ok && bits[f] <= 31u;
+            const uint32_t g = f < P ? min(G, bits[f]) : 0u;
+            keybits += g;
+            W += f < P ? bits[f] - g : bits[f];
+        }
+        ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) &&
+             nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
+    }
+    if (!ok) {
+        if (t == 0) set_status(a.status, kStCorrupt);
+        return;  // uniform across the CTA: every warp reached the same verdict
+    }
+
+    // ---- 2. raw block
+    if (raw) {
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            for (int i = t; i < n_b; i += kDecThreads) a.out[f][first + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
+        return;
+    }
+
+    const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc), rwords = ceil_words((uint32_t)n_b * W);
+    const uint32_t idlimit = 1u << keybits;
+
+    // round trip 3: stage the deltas, counts and (when at most 128 bits wide)
+    // the records in shared memory, coalesced; they are contiguous in the stream
+    const bool fast = W <= 128u;  // then dwords + cwords + rwords <= the staged words
+    const uint32_t ndc = dwords + cwords;
+    __syncthreads();
+    const uint32_t* sD = stage;
+    const uint32_t* sC = stage + dwords;
+    const uint32_t* sR = stage + ndc;
+    const uint32_t k0 = 2u * t, k1 = k0 + 1u;
+    const bool v0 = k0 < U, v1 = k1 < U;
+    uint32_t d0 = v0 ? extract_s(sD, k0, wd) : 0u, d1 = v1 ? extract_s(sD, k1, wd) : 0u;
+    uint32_t c0 = v0 ? extract_s(sC, k0, wc) : 0u, c1 = v1 ? extract_s(sC, k1, wc) : 0u;
+
+    // ---- 3. unique ids and run starts
+    {
+        bool bad = (v0 && (d0 >= idlimit || c0 == 0u || c0 > (uint32_t)n_b || (k0 > 0 && d0 == 0u))) ||
+                   (v1 && (d1 >= idlimit || c1 == 0u || c1 > (uint32_t)n_b || d1 == 0u));
+        if (bad) d0 = d1 = c0 = c1 = 0u;  // keep the sums small; the block is rejected below
+        const uint32_t su = d0 + d1, sc = c0 + c1;
+        const uint32_t iu = warp_incl_sum(su), ic = warp_incl_sum(sc);
+        if (lane == 31) {
+            warp_u[w] = iu;
+            warp_c[w] = ic;
+        }
+        __syncthreads();
+        uint32_t bu = 0, bc = 0, total = 0;
+#pragma unroll
+        for (int ww = 0; ww < kDecWarps; ++ww) {
+            const uint32_t cu = warp_u[ww], cc = warp_c[ww];
+            if (ww < w) {
+                bu += cu;
+                bc += cc;
+            }
+            total += cc;
+        }
+        const uint32_t u0 = bu + iu - su + d0, u1 = u0 + d1;
+        const uint32_t s0 = bc + ic - sc, s1 = s0 + c0;
+        if (v0) {
+            if (u0 >= idlimit || s0 >= (uint32_t)n_b) {
+                bad = true;
+            } else {
+                uniq[k0] = (uint16_t)u0;
+                atomicOr(&mask[s0 >> 5], 1u << (s0 & 31u));
+            }
+        }
+        if (v1) {
+            if (u1 >= idlimit || s1 >= (uint32_t)n_b) {
+                bad = true;
+            } else {
+                uniq[k1] = (uint16_t)u1;
+                atomicOr(&mask[s1 >> 5], 1u << (s1 & 31u));
+            }
+        }
+        if (t == 0 && total != (uint32_t)n_b) bad = true;
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_bad, 1u);
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (t == 0) set_status(a.status, kStCorrupt);
+        return;
+    }
+    if (w == 0) {
+        const uint32_t pc = __popc(mask[lane]);
+        mpre[lane] = warp_incl_sum(pc) - pc;
+    }
+    __syncthreads();
+
+    // ---- 4. positions 4t..4t+3
+    const int j0 = 4 * t;
+    if (j0 >= n_b) return;
+    const uint32_t mrow = mask[t >> 3], prow = mpre[t >> 3];
+    uint32_t key[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t bit = (uint32_t)(j0 + e) & 31u;
+        int run = (int)(prow + __popc(mrow & ((2u << bit) - 1u))) - 1;
+        run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
+        key[e] = uniq[run];
+    }
+    // per-field layout (uniform): record shift, key shift, offset bits, masks
+    DecLayout L;
+    {
+        uint32_t r = 0, k = 0;
+#pragma unroll
+        for (int f = F - 1; f >= 0; --f) {
+            const uint32_t g = f < P ? min(G, bits[f]) : 0u;
+            const uint32_t wf = f < P ? bits[f] - g : bits[f];
+            L.rs[f] = r;
+            L.ks[f] = k;
+            L.of[f] = f < P ? wf : 0u;
+            L.gm[f] = mask_bits(g);
+            L.cm[f] = mask_bits(wf);
+            r += wf;
+            k += g;
+        }
+    }
+    if (!fast) {
+        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, G, j0, n_b, first, key[0], key[1], key[2], key[3]);
+        return;
+    }
+    uint32_t rr[4][4];
+    {
+        // masks of the record's four words
+        const uint32_t m0 = mask_bits(min(W, 32u));
+        const uint32_t m1 = W > 32u ? mask_bits(min(W - 32u, 32u)) : 0u;
+        const uint32_t m2 = W > 64u ? mask_bits(min(W - 64u, 32u)) : 0u;
+        const uint32_t m3 = W > 96u ? mask_bits(W - 96u) : 0u;
+        const bool wide = W > 64u;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t p = (uint32_t)(j0 + e) * W;
+            const uint32_t wi = p >> 5, sh = p & 31u;
+            // words past the record array read as 0 (the array is staged whole)
+            const uint32_t x0 = sR[wi];
+            const uint32_t x1 = wi + 1 < rwords ? sR[wi + 1] : 0u;
+            const uint32_t x2 = wi + 2 < rwords ? sR[wi + 2] : 0u;
+            rr[e][0] = __funnelshift_r(x0, x1, sh) & m0;
+            rr[e][1] = __funnelshift_r(x1, x2, sh) & m1;
+            if (wide) {
+                const uint32_t x3 = wi + 3 < rwords ? sR[wi + 3] : 0u;
+                const uint32_t x4 = wi + 4 < rwords ? sR[wi + 4] : 0u;
+                rr[e][2] = __funnelshift_r(x2, x3, sh) & m2;
+                rr[e][3] = __funnelshift_r(x3, x4, sh) & m3;
+            } else {
+                rr[e][2] = rr[e][3] = 0u;
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        // the field starts in record word kw at bit kb (uniform); a zero-width
+        // field at the very top may sit at bit 128 and reads nothing
+        const uint32_t kw = min(L.rs[f] >> 5, 3u), kb = L.rs[f] & 31u;
+        uint32_t qv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t lo = kw == 0u ? rr[e][0] : kw == 1u ? rr[e][1] : kw == 2u ? rr[e][2] : rr[e][3];
+            const uint32_t hi = kw == 0u ? rr[e][1] : kw == 1u ? rr[e][2] : kw == 2u ? rr[e][3] : 0u;
+            const uint32_t code = __funnelshift_r(lo, hi, kb) & L.cm[f];
+            qv[e] = f < P ? (code | (((key[e] >> L.ks[f]) & L.gm[f]) << L.of[f])) : code;
+        }
+        store4(a.out[f] + first + j0, qv, bits[f], s[f], mn[f], n_b - j0);
+    }
+}
+
+}  // namespace gpz

@@ -27,6 +27,7 @@ constexpr int kRangeThreads = 256;
 constexpr int kCompactWarps = 8;
 
 // Status codes written to the workspace status word (values of gpz_status).
+constexpr uint32_t kStCapacity = 2;
 constexpr uint32_t kStCorrupt = 3;
 constexpr uint32_t kStTimeout = 6;
 
@@ -104,6 +105,28 @@ struct DecArgs {
     uint32_t nblocks;
     uint32_t* status;
 };
+
+// The constants of one field under a relative bound rel, from the field's
+// range [lo, hi] (lo > hi when the field holds no value): eb = rel * (hi - lo)
+// when that is a finite positive number, else eb = rel; then the step
+// eb * 63/32, its reciprocal and the verification threshold, all from the
+// double eb (one rounding each).
+__device__ __forceinline__ FieldParams range_params(float lo, float hi, double rel) {
+    double eb = rel;
+    if (lo <= hi) {
+        const double range = (double)hi - (double)lo;
+        if (range > 0.0 && range < HUGE_VAL) {
+            const double e = rel * range;
+            if (e > 0.0 && e < HUGE_VAL) eb = e;
+        }
+    }
+    FieldParams p;
+    p.eb = __double2float_rn(eb);
+    p.s = __double2float_rn(eb * 1.96875);
+    p.inv = __double2float_rn(1.0 / (double)p.s);
+    p.ebchk = __double2float_rd(eb * (1.0 - 0x1p-22));
+    return p;
+}
 
 // ---------------------------------------------------------------- helpers
 

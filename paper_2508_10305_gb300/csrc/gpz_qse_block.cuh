@@ -1,0 +1,843 @@
+// gpz_qse_block.cuh -- the per-block body of the fused compression kernel
+// (quantisation, sorting, encoding; Sections 4.1-4.3), shared by the
+// single-array kernels (gpz_qse.cu) and the batched persistent kernels
+// (gpz_batch.cu).  See gpz_qse.cu for the design.
+#pragma once
+
+#include "gpz_internal.cuh"
+
+namespace gpz {
+
+// ------------------------------------------------------------------ fused Q.S.E. kernel
+
+constexpr int kThreads = kQseThreads;        // 256
+constexpr int kWarps = kThreads / 32;        // 8
+constexpr uint32_t kHistBytes = kWarps * kMaxBins * 2u;  // u16 per-warp histograms
+constexpr uint32_t kMagic23 = 0x4B000000u;   // bit pattern of 2^23
+
+__host__ __device__ constexpr uint32_t qse_region_bytes(int F) {
+    const uint32_t rec = kHistBytes + kBlock * 16u;         // histograms + 128-bit sorted records
+    const uint32_t codes = (uint32_t)F * kBlock * 4u;        // u32 sorted codes per field (W > 128)
+    return rec > codes ? rec : codes;
+}
+
+// The whole encoded block of the packed path: header (<= 11 words), deltas
+// (<= 512 x 9 bits), counts (<= 512 x 11 bits), records (<= 1024 x 128 bits).
+constexpr uint32_t kStageWords = 4432u;
+constexpr uint32_t kFastRecordBits = 128u;
+
+__host__ __device__ constexpr uint32_t qse_smem_bytes(int F) {
+    return qse_region_bytes(F) + kMaxBins * 2u /*uniq*/ + kMaxBins * 2u /*counts*/ + kBlock * 2u /*perm*/ +
+           kStageWords * 4u /*packed records*/;
+}
+
+struct QseShared {
+    uint32_t minkey[kMaxFields];
+    uint32_t maxq[kMaxFields];
+    uint32_t flags;                 // bit 0: non-finite value, bit 1: no code within the bound
+    uint32_t maxcnt, maxdelta;
+    uint32_t warp_tot[kWarps], warp_nz[kWarps];
+};
+
+// Order-preserving map of finite floats to u32 (-0 < +0).
+__device__ __forceinline__ uint32_t order_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_key(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Verification of one candidate code: the decompressor's reconstruction.
+__device__ __forceinline__ bool code_ok(float x, uint32_t q, const FieldParams& p, float mn) {
+    const float xh = __fmaf_rn(__uint2float_rn(q), p.s, mn);
+    return fabsf(__fsub_rn(x, xh)) <= p.ebchk;
+}
+
+// General quantiser (codes >= 2^23, or a first candidate that fails):
+// candidates q0, q0 - 1, q0 + 1; returns 0xffffffff when none is within the
+// bound (valid codes are below 2^31).
+static __device__ __noinline__ uint32_t quantise_general(float x, FieldParams p, float mn) {
+    const float t = __fmaf_rn(__fsub_rn(x, mn), p.inv, 0.5f);
+    if (!(t < 2147483648.0f)) return 0xffffffffu;
+    const uint32_t q = __float2uint_rd(t);
+    if (code_ok(x, q, p, mn)) return q;
+    if (q > 0u && code_ok(x, q - 1u, p, mn)) return q - 1u;
+    if (code_ok(x, q + 1u, p, mn)) return q + 1u;
+    return 0xffffffffu;
+}
+
+
+// Thread-serial fixed-length appender into zeroed shared words: appends the
+// low w (<= 32) bits of v at the current bit position.  Every completed word
+// is merged with atomicOr (a word at the edge of a thread's range is shared
+// with its neighbour); the updates are predicated, so the warp never diverges.
+struct BitAppender {
+    unsigned long long acc;
+    uint32_t nb;   // bits pending in acc (< 32)
+    uint32_t wi;   // shared word index of acc's low word
+    __device__ __forceinline__ BitAppender(uint32_t bitpos) : acc(0ull), nb(bitpos & 31u), wi(bitpos >> 5) {}
+    __device__ __forceinline__ void put(uint32_t* sw, uint32_t v, uint32_t w) {
+        acc |= (unsigned long long)v << nb;
+        nb += w;
+        const bool full = nb >= 32u;
+        if (full) atomicOr(sw + wi, (uint32_t)acc);
+        acc = full ? (acc >> 32) : acc;
+        nb = full ? nb - 32u : nb;
+        wi += full ? 1u : 0u;
+    }
+    __device__ __forceinline__ void finish(uint32_t* sw) {
+        if (nb) atomicOr(sw + wi, (uint32_t)acc);
+    }
+};
+
+template <int F>
+__device__ __forceinline__ void write_raw(const QseArgs& a, uint64_t first, int n_b, uint32_t* out, int t) {
+    if (t == 0) out[0] = 1u;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float* src = a.fields[f] + first;
+        for (int i = t; i < n_b; i += kThreads) out[1 + f * n_b + i] = __float_as_uint(__ldg(src + i));
+    }
+    if (a.perm)
+        for (int i = t; i < n_b; i += kThreads) a.perm[first + i] = (uint32_t)(first + i);
+    if (t == 0) a.sizes[first / kBlock] = 1u + (uint32_t)F * (uint32_t)n_b;
+}
+
+// The general per-block path: any block, including codes >= 2^23, values
+// that need a fallback candidate, and records wider than 128 bits.
+template <int F, bool FULL>
+__device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm, QseShared& S, uint32_t b) {
+    constexpr int P = F < 3 ? F : 3;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint64_t first = (uint64_t)b * kBlock;
+    const int n_b = FULL ? kBlock : (int)(a.n - first);
+    constexpr uint32_t region = qse_region_bytes(F);
+    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
+    uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
+    uint32_t* codes = reinterpret_cast<uint32_t*>(dsm);                      // [F][1024], wide records
+    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + region);             // [512]
+    uint16_t* cnt = uniq + kMaxBins;                                         // [512]
+    uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
+    uint32_t* out = a.temp + (size_t)b * a.slot_words;
+
+    if (t < F) {
+        S.minkey[t] = 0xffffffffu;
+        S.maxq[t] = 0u;
+    }
+    if (t == 0) {
+        S.flags = 0u;
+        S.maxcnt = 0u;
+        S.maxdelta = 0u;
+    }
+    {
+        uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
+#pragma unroll
+        for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
+        for (uint32_t k = t; k < kStageWords; k += kThreads) stage[k] = 0u;
+    }
+
+    // ---- 1. load (coalesced, streaming) and block minimum
+    bool valid[4];
+    float x[F][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float* src = a.fields[f] + first + 128 * w + lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
+    }
+    FieldParams prm[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) prm[f] = a.d_params ? a.d_params[f] : a.params[f];
+    __syncthreads();  // shared reduction slots initialised (the loads are in flight)
+    float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float m = valid[0] ? x[f][0] : INFINITY;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (valid[r]) {
+                probe = __fmaf_rn(x[f][r], 0.0f, probe);
+                m = fminf(m, x[f][r]);
+            }
+        }
+        const uint32_t mk = __reduce_min_sync(0xffffffffu, m == INFINITY ? 0xffffffffu : order_key(m));
+        if (lane == 0) atomicMin(&S.minkey[f], mk);
+    }
+    if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
+    __syncthreads();  // A
+    if (S.flags & 1u) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 2. quantisation with verification (fast path for codes < 2^23)
+    float mn[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float m = from_order_key(S.minkey[f]);
+        mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
+    }
+    uint32_t q[F][4];
+    uint32_t pending = 0;  // bit 4f + r: value needs the general quantiser
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float xv = x[f][r];
+            const float tt = __fmaf_rn(__fsub_rn(xv, mn[f]), prm[f].inv, 0.5f);
+            // 2^23 + floor(t), exactly, while t < 2^23 (the sum lies in [2^23, 2^24))
+            const float u = __fadd_rd(tt, 8388608.0f);
+            q[f][r] = __float_as_uint(u) - kMagic23;
+            const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), prm[f].s, mn[f]);
+            const bool ok = (tt < 8388608.0f) && (fabsf(__fsub_rn(xv, xh)) <= prm[f].ebchk);
+            if (valid[r] && !ok) pending |= 1u << (4 * f + r);
+            if (!valid[r]) q[f][r] = 0u;
+        }
+    }
+    bool fail = false;
+    if (__any_sync(0xffffffffu, pending != 0u)) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (pending & (1u << (4 * f + r))) {
+                    const uint32_t g = quantise_general(x[f][r], prm[f], mn[f]);
+                    fail |= g == 0xffffffffu;
+                    q[f][r] = g == 0xffffffffu ? 0u : g;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        uint32_t qmax = max(max(q[f][0], q[f][1]), max(q[f][2], q[f][3]));
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        if (lane == 0 && qmax) atomicMax(&S.maxq[f], qmax);
+    }
+    if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&S.flags, 2u);
+    __syncthreads();  // B
+    if (S.flags & 2u) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 3. segments, key and record layout (uniform)
+    uint32_t o[F], wf[F], kshift[F], bits[F], keybits = 0, W = 0;
+    {
+        uint32_t g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            bits[f] = bit_width(S.maxq[f]);
+            g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
+            o[f] = f < P ? bits[f] - g[f] : 0u;
+            wf[f] = f < P ? o[f] : bits[f];
+        }
+        uint32_t ks = 0;
+#pragma unroll
+        for (int f = F - 1; f >= 0; --f) {
+            kshift[f] = ks;
+            ks += g[f];
+            W += wf[f];
+        }
+        keybits = ks;
+    }
+    const bool fast = W <= kFastRecordBits;
+    // records as four words r0 (least significant) .. r3; each field's code is
+    // appended below the record so far, so field 0 ends most significant
+    uint32_t key[4], r0[4], r1[4], r2[4], r3[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        uint32_t k = 0;
+#pragma unroll
+        for (int f = 0; f < P; ++f) k |= (q[f][r] >> o[f]) << kshift[f];
+        key[r] = k;
+        r0[r] = r1[r] = r2[r] = r3[r] = 0u;
+    }
+    if (W <= 64u) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const uint32_t code = f < P ? (q[f][r] & ((1u << o[f]) - 1u)) : q[f][r];
+                hi = __funnelshift_l(lo, hi, wf[f]);
+                lo = (lo << wf[f]) | code;
+            }
+            r0[r] = lo;
+            r1[r] = hi;
+        }
+    } else if (fast) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const uint32_t code = f < P ? (q[f][r] & ((1u << o[f]) - 1u)) : q[f][r];
+                a3 = __funnelshift_l(a2, a3, wf[f]);
+                a2 = __funnelshift_l(a1, a2, wf[f]);
+                a1 = __funnelshift_l(a0, a1, wf[f]);
+                a0 = (a0 << wf[f]) | code;
+            }
+            r0[r] = a0;
+            r1[r] = a1;
+            r2[r] = a2;
+            r3[r] = a3;
+        }
+    }
+
+    // ---- 4. stable counting sort: warp-local ranks in storage order
+    uint16_t* myhist = hist + w * kMaxBins;
+    uint32_t rank[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? key[r] : 0xffffffffu);
+        uint32_t before = 0u;
+        if (valid[r]) before = myhist[key[r]];
+        __syncwarp();
+        if (valid[r] && lane == 31 - __clz(peers)) myhist[key[r]] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        rank[r] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();  // C
+
+    // ---- 4b. scan over (bin, warp): sorted positions and the run-length code
+    const int nbins = 1 << keybits;
+    const int b0 = 2 * t;
+    uint32_t c0 = 0, c1 = 0;
+    uint32_t pre[kWarps];  // (prefix of bin b0) | (prefix of bin b0+1) << 16
+    if (b0 < nbins) {
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t pair = *reinterpret_cast<const uint32_t*>(hist + ww * kMaxBins + b0);
+            pre[ww] = c0 | (c1 << 16);
+            c0 += pair & 0xffffu;
+            c1 += pair >> 16;
+        }
+    }
+    const uint32_t tot = c0 + c1;
+    const uint32_t nz = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+    const uint32_t incl_tot = warp_incl_sum(tot);
+    const uint32_t incl_nz = warp_incl_sum(nz);
+    const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
+    if (lane == 31) {
+        S.warp_tot[w] = incl_tot;
+        S.warp_nz[w] = incl_nz;
+    }
+    if (lane == 0) atomicMax(&S.maxcnt, cmax);
+    __syncthreads();  // D
+    uint32_t base_tot = 0, base_nz = 0, U = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww];
+        if (ww < w) {
+            base_tot += vt;
+            base_nz += vn;
+        }
+        U += vn;
+    }
+    if (b0 < nbins) {
+        const uint32_t start0 = base_tot + incl_tot - tot, start1 = start0 + c0;
+        const uint32_t idx0 = base_nz + incl_nz - nz, idx1 = idx0 + (c0 ? 1u : 0u);
+        const uint32_t base2 = start0 | (start1 << 16);  // neither half overflows: both < 1024
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww)
+            *reinterpret_cast<uint32_t*>(hist + ww * kMaxBins + b0) = base2 + pre[ww];
+        if (c0) {
+            uniq[idx0] = (uint16_t)b0;
+            cnt[idx0] = (uint16_t)c0;
+        }
+        if (c1) {
+            uniq[idx1] = (uint16_t)(b0 + 1);
+            cnt[idx1] = (uint16_t)c1;
+        }
+    }
+    __syncthreads();  // E
+
+    // ---- 4c. scatter to sorted order; deltas of the unique ids
+    uint32_t dest[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dest[r] = valid[r] ? myhist[key[r]] + rank[r] : 0u;
+    {
+        uint32_t dmax = 0;
+        for (uint32_t k = t; k < U; k += kThreads) {
+            const uint32_t d = (uint32_t)uniq[k] - (k ? (uint32_t)uniq[k - 1] : 0u);
+            dmax = max(dmax, d);
+        }
+        dmax = __reduce_max_sync(0xffffffffu, dmax);
+        if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
+    }
+    if (fast) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (valid[r]) recs[dest[r]] = make_uint4(r0[r], r1[r], r2[r], r3[r]);
+    }
+    if (a.perm) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (valid[r]) sperm[dest[r]] = (uint16_t)(128 * w + 32 * r + lane);
+    }
+    if (!fast) {
+        __syncthreads();  // the histograms are read; the codes may overwrite them
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (!valid[r]) continue;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const uint32_t qq = q[f][r];
+                codes[f * kBlock + dest[r]] = f < P ? (qq & ((1u << o[f]) - 1u)) : qq;
+            }
+        }
+    }
+    __syncthreads();  // F
+
+    // ---- encoded size; raw when not smaller (keeps the bound size a bound)
+    const uint32_t wd = bit_width(S.maxdelta), wc = bit_width(S.maxcnt);
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc);
+    const uint32_t rwords = ceil_words((uint32_t)n_b * W);
+    const uint32_t enc = hdr + dwords + cwords + rwords;
+    if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 5. block header and the three arrays (Section 4.3), assembled in the
+    // zeroed staging words by thread-serial appenders, then copied out
+    if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
+    if (t >= 1 && t <= F) {
+        float m = 0.0f;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if (f == t - 1) m = mn[f];
+        stage[t] = __float_as_uint(m);
+    }
+    if (t < ((F + 3) >> 2)) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if ((f >> 2) == t) word |= bits[f] << (8 * (f & 3));
+        stage[1 + F + t] = word;
+    }
+    {
+        // deltas and counts: entries 2t, 2t+1
+        const uint32_t k0 = 2u * (uint32_t)t;
+        if (k0 < U && wd) {
+            BitAppender ap(32u * hdr + k0 * wd);
+            ap.put(stage, (uint32_t)uniq[k0] - (k0 ? (uint32_t)uniq[k0 - 1] : 0u), wd);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)uniq[k0 + 1] - (uint32_t)uniq[k0], wd);
+            ap.finish(stage);
+        }
+        if (k0 < U && wc) {
+            BitAppender ap(32u * (hdr + dwords) + k0 * wc);
+            ap.put(stage, (uint32_t)cnt[k0], wc);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)cnt[k0 + 1], wc);
+            ap.finish(stage);
+        }
+    }
+    const uint32_t len = (uint32_t)n_b;
+    const uint32_t rbase = hdr + dwords + cwords;
+    if (fast) {
+        // Thread t appends sorted records 4t..4t+3 (bits [4tW, 4tW + 4W)).
+        const uint32_t j0 = 4u * (uint32_t)t;
+        if (j0 < len && W) {
+            BitAppender ap(32u * rbase + j0 * W);
+            // widths of the record's four words
+            const uint32_t w0 = min(W, 32u), w1 = min(W - w0, 32u), w2 = min(W - w0 - w1, 32u), w3 = W - w0 - w1 - w2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint4 v = (j0 + e < len) ? recs[j0 + e] : make_uint4(0u, 0u, 0u, 0u);
+                ap.put(stage, v.x, w0);
+                if (w1) ap.put(stage, v.y, w1);
+                if (w2) ap.put(stage, v.z, w2);
+                if (w3) ap.put(stage, v.w, w3);
+            }
+            ap.finish(stage);
+        }
+    }
+    __syncthreads();
+    {
+        // copy the staged words (all of them, or up to the records when the
+        // records are wider than 64 bits); the slot is 16-byte aligned
+        const uint32_t nstage = fast ? enc : rbase;
+        const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+        uint4* o4 = reinterpret_cast<uint4*>(out);
+        for (uint32_t k = t; k < (nstage >> 2); k += kThreads) o4[k] = s4[k];
+        for (uint32_t k = (nstage & ~3u) + t; k < nstage; k += kThreads) out[k] = stage[k];
+    }
+    if (!fast) {
+        // records wider than 128 bits: gather field by field from the codes
+        uint32_t* rout = out + rbase;
+        uint32_t rshift[F];
+        {
+            uint32_t rs = 0;
+#pragma unroll
+            for (int f = F - 1; f >= 0; --f) {
+                rshift[f] = rs;
+                rs += wf[f];
+            }
+        }
+        for (uint32_t k = t; k < rwords; k += kThreads) {
+            const uint32_t lo = 32u * k;
+            uint32_t j = div_small(lo, W);
+            uint32_t acc = 0;
+            for (; j < len && j * W < lo + 32u; ++j) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    if (wf[f] == 0u) continue;
+                    const int s0 = (int)(j * W + rshift[f]) - (int)lo;
+                    if (s0 >= 32 || s0 + (int)wf[f] <= 0) continue;
+                    const uint32_t v = codes[f * kBlock + j];
+                    acc |= s0 >= 0 ? (v << s0) : (v >> -s0);
+                }
+            }
+            rout[k] = acc;
+        }
+    }
+    if (a.perm)
+        for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
+    if (t == 0) a.sizes[b] = enc;
+}
+
+// ------------------------------------------------------------------ fast path
+
+constexpr uint32_t kFastRegion = kHistBytes + kBlock * 16u;  // histograms + 128-bit sorted records
+
+__host__ __device__ constexpr uint32_t qse_fast_smem_bytes() {
+    return kFastRegion + kMaxBins * 2u + kMaxBins * 2u + kBlock * 2u + kStageWords * 4u;
+}
+
+struct QseFastShared {
+    uint32_t minkey[kMaxFields];
+    uint32_t maxkey[kMaxFields];
+    uint32_t flags;                 // bit 0: non-finite value, bit 1: a value needs a fallback candidate
+    uint32_t maxcnt, maxdelta;
+    uint32_t warp_tot[kWarps], warp_nz[kWarps];
+};
+
+// Quantise the thread's 4 values of field f (fast candidate only), add the
+// field's segId to the key and append its code to the record words.
+template <int NW>
+__device__ __forceinline__ void quantise_append(const float (&x)[4], const bool (&valid)[4], float mn,
+                                                const FieldParams& p, bool pos, uint32_t o, uint32_t ks,
+                                                uint32_t wf, uint32_t (&key)[4], uint32_t (&rw)[4][4],
+                                                bool& pend) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float tt = __fmaf_rn(__fsub_rn(x[r], mn), p.inv, 0.5f);
+        const float u = __fadd_rd(tt, 8388608.0f);  // 2^23 + floor(t), t < 2^23 here
+        uint32_t q = __float_as_uint(u) - kMagic23;
+        const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), p.s, mn);
+        pend |= valid[r] && !(fabsf(__fsub_rn(x[r], xh)) <= p.ebchk);
+        q = valid[r] ? q : 0u;
+        uint32_t code = q;
+        if (pos) {
+            key[r] |= (q >> o) << ks;
+            code = q & ((1u << o) - 1u);
+        }
+        // append below the record so far (field 0 ends most significant)
+        if (NW == 4) {
+            rw[r][3] = __funnelshift_l(rw[r][2], rw[r][3], wf);
+            rw[r][2] = __funnelshift_l(rw[r][1], rw[r][2], wf);
+        }
+        rw[r][1] = __funnelshift_l(rw[r][0], rw[r][1], wf);
+        rw[r][0] = (rw[r][0] << wf) | code;
+    }
+}
+
+// Block b of the array described by a; a block the fast path cannot take is
+// appended to a.general_list as list_id.
+template <int F, bool FULL>
+__device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, uint32_t b,
+                                               uint32_t list_id) {
+    constexpr int P = F < 3 ? F : 3;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint64_t first = (uint64_t)b * kBlock;
+    const int n_b = FULL ? kBlock : (int)(a.n - first);
+    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
+    uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
+    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastRegion);        // [512]
+    uint16_t* cnt = uniq + kMaxBins;                                         // [512]
+    uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
+    uint32_t* out = a.temp + (size_t)b * a.slot_words;
+
+    if (t < F) {
+        S.minkey[t] = 0xffffffffu;
+        S.maxkey[t] = 0u;
+    }
+    if (t == 0) {
+        S.flags = 0u;
+        S.maxcnt = 0u;
+        S.maxdelta = 0u;
+    }
+    {
+        uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
+#pragma unroll
+        for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
+        for (uint32_t k = t; k < kStageWords; k += kThreads) stage[k] = 0u;
+    }
+
+    // ---- 1. load (coalesced, streaming); block minimum and maximum
+    bool valid[4];
+    float x[F][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float* src = a.fields[f] + first + 128 * w + lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
+    }
+    __syncthreads();  // shared reduction slots initialised (the loads are in flight)
+    float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (valid[r]) {
+                probe = __fmaf_rn(x[f][r], 0.0f, probe);
+                lo = fminf(lo, x[f][r]);
+                hi = fmaxf(hi, x[f][r]);
+            }
+        }
+        const uint32_t lk = __reduce_min_sync(0xffffffffu, lo == INFINITY ? 0xffffffffu : order_key(lo));
+        const uint32_t hk = __reduce_max_sync(0xffffffffu, hi == -INFINITY ? 0u : order_key(hi));
+        if (lane == 0) {
+            atomicMin(&S.minkey[f], lk);
+            atomicMax(&S.maxkey[f], hk);
+        }
+    }
+    if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
+    __syncthreads();  // A
+    if (S.flags & 1u) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 2. widths from the block maxima: q0 = floor(fma(x - min, 1/s, 1/2))
+    // is monotone in x, so when every value keeps its first candidate the
+    // largest code is q0 of the block maximum
+    float mn[F];
+    uint32_t bits[F], o[F], wf[F], kshift[F], W = 0, keybits = 0;
+    bool big = false;
+    {
+        uint32_t g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            const float m = from_order_key(S.minkey[f]);
+            mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
+            const float tq = __fmaf_rn(__fsub_rn(from_order_key(S.maxkey[f]), mn[f]), p.inv, 0.5f);
+            big |= !(tq < 8388608.0f);
+            bits[f] = bit_width(__float_as_uint(__fadd_rd(tq, 8388608.0f)) - kMagic23);
+            g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
+            o[f] = f < P ? bits[f] - g[f] : 0u;
+            wf[f] = f < P ? o[f] : bits[f];
+        }
+        uint32_t ks = 0;
+#pragma unroll
+        for (int f = F - 1; f >= 0; --f) {
+            kshift[f] = ks;
+            ks += g[f];
+            W += wf[f];
+        }
+        keybits = ks;
+    }
+    if (big || W > kFastRecordBits) {
+        // left to the general kernel (uniform decision)
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = list_id;
+        return;
+    }
+
+    // ---- 3. quantise, key and record in one pass
+    uint32_t key[4] = {0u, 0u, 0u, 0u};
+    uint32_t rw[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rw[r][0] = rw[r][1] = rw[r][2] = rw[r][3] = 0u;
+    bool pend = false;
+    if (W <= 64u) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            quantise_append<2>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+            quantise_append<4>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+        }
+    }
+    if (__any_sync(0xffffffffu, pend) && lane == 0) atomicOr(&S.flags, 2u);
+
+    // ---- 4. stable counting sort: warp-local ranks in storage order
+    uint16_t* myhist = hist + w * kMaxBins;
+    uint32_t rank[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid[r] ? key[r] : 0xffffffffu);
+        uint32_t before = 0u;
+        if (valid[r]) before = myhist[key[r]];
+        __syncwarp();
+        if (valid[r] && lane == 31 - __clz(peers)) myhist[key[r]] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        rank[r] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();  // C
+    if (S.flags & 2u) {
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = list_id;
+        return;
+    }
+
+    // ---- 4b. scan over (bin, warp): sorted positions and the run-length code
+    const int nbins = 1 << keybits;
+    const int b0 = 2 * t;
+    uint32_t c0 = 0, c1 = 0;
+    uint32_t pre[kWarps];  // (prefix of bin b0) | (prefix of bin b0+1) << 16
+    if (b0 < nbins) {
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t pair = *reinterpret_cast<const uint32_t*>(hist + ww * kMaxBins + b0);
+            pre[ww] = c0 | (c1 << 16);
+            c0 += pair & 0xffffu;
+            c1 += pair >> 16;
+        }
+    }
+    const uint32_t tot = c0 + c1;
+    const uint32_t nz = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+    const uint32_t incl_tot = warp_incl_sum(tot);
+    const uint32_t incl_nz = warp_incl_sum(nz);
+    const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
+    if (lane == 31) {
+        S.warp_tot[w] = incl_tot;
+        S.warp_nz[w] = incl_nz;
+    }
+    if (lane == 0) atomicMax(&S.maxcnt, cmax);
+    __syncthreads();  // D
+    uint32_t base_tot = 0, base_nz = 0, U = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww];
+        if (ww < w) {
+            base_tot += vt;
+            base_nz += vn;
+        }
+        U += vn;
+    }
+    if (b0 < nbins) {
+        const uint32_t start0 = base_tot + incl_tot - tot, start1 = start0 + c0;
+        const uint32_t idx0 = base_nz + incl_nz - nz, idx1 = idx0 + (c0 ? 1u : 0u);
+        const uint32_t base2 = start0 | (start1 << 16);  // neither half overflows: both < 1024
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww)
+            *reinterpret_cast<uint32_t*>(hist + ww * kMaxBins + b0) = base2 + pre[ww];
+        if (c0) {
+            uniq[idx0] = (uint16_t)b0;
+            cnt[idx0] = (uint16_t)c0;
+        }
+        if (c1) {
+            uniq[idx1] = (uint16_t)(b0 + 1);
+            cnt[idx1] = (uint16_t)c1;
+        }
+    }
+    __syncthreads();  // E
+
+    // ---- 4c. scatter to sorted order; deltas of the unique ids
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (valid[r]) {
+            const uint32_t dest = myhist[key[r]] + rank[r];
+            recs[dest] = make_uint4(rw[r][0], rw[r][1], rw[r][2], rw[r][3]);
+            if (a.perm) sperm[dest] = (uint16_t)(128 * w + 32 * r + lane);
+        }
+    }
+    {
+        uint32_t dmax = 0;
+        for (uint32_t k = t; k < U; k += kThreads) {
+            const uint32_t d = (uint32_t)uniq[k] - (k ? (uint32_t)uniq[k - 1] : 0u);
+            dmax = max(dmax, d);
+        }
+        dmax = __reduce_max_sync(0xffffffffu, dmax);
+        if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
+    }
+    __syncthreads();  // F
+
+    // ---- encoded size; raw when not smaller (keeps the bound size a bound)
+    const uint32_t wd = bit_width(S.maxdelta), wc = bit_width(S.maxcnt);
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc);
+    const uint32_t rwords = ceil_words((uint32_t)n_b * W);
+    const uint32_t enc = hdr + dwords + cwords + rwords;
+    if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
+        write_raw<F>(a, first, n_b, out, t);
+        return;
+    }
+
+    // ---- 5. block header and the three arrays (Section 4.3), assembled in the
+    // zeroed staging words by thread-serial appenders, then copied out
+    if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
+    if (t >= 1 && t <= F) {
+        float m = 0.0f;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if (f == t - 1) m = mn[f];
+        stage[t] = __float_as_uint(m);
+    }
+    if (t < ((F + 3) >> 2)) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if ((f >> 2) == t) word |= bits[f] << (8 * (f & 3));
+        stage[1 + F + t] = word;
+    }
+    {
+        const uint32_t k0 = 2u * (uint32_t)t;
+        if (k0 < U && wd) {
+            BitAppender ap(32u * hdr + k0 * wd);
+            ap.put(stage, (uint32_t)uniq[k0] - (k0 ? (uint32_t)uniq[k0 - 1] : 0u), wd);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)uniq[k0 + 1] - (uint32_t)uniq[k0], wd);
+            ap.finish(stage);
+        }
+        if (k0 < U && wc) {
+            BitAppender ap(32u * (hdr + dwords) + k0 * wc);
+            ap.put(stage, (uint32_t)cnt[k0], wc);
+            if (k0 + 1 < U) ap.put(stage, (uint32_t)cnt[k0 + 1], wc);
+            ap.finish(stage);
+        }
+    }
+    const uint32_t len = (uint32_t)n_b;
+    {
+        const uint32_t j0 = 4u * (uint32_t)t;
+        if (j0 < len && W) {
+            BitAppender ap(32u * (hdr + dwords + cwords) + j0 * W);
+            const uint32_t w0 = min(W, 32u), w1 = min(W - w0, 32u), w2 = min(W - w0 - w1, 32u), w3 = W - w0 - w1 - w2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint4 v = (j0 + e < len) ? recs[j0 + e] : make_uint4(0u, 0u, 0u, 0u);
+                ap.put(stage, v.x, w0);
+                if (w1) ap.put(stage, v.y, w1);
+                if (w2) ap.put(stage, v.z, w2);
+                if (w3) ap.put(stage, v.w, w3);
+            }
+            ap.finish(stage);
+        }
+    }
+    __syncthreads();
+    {
+        const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+        uint4* o4 = reinterpret_cast<uint4*>(out);
+        for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
+        for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+    }
+    if (a.perm)
+        for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
+    if (t == 0) a.sizes[b] = enc;
+}
+
+
+}  // namespace gpz

@@ -26,6 +26,24 @@ class gpz_params(C.Structure):
                 ("eb", C.c_double * MAX_FIELDS)]
 
 
+class gpz_compress_chunk(C.Structure):
+    _fields_ = [("fields", C.c_void_p * MAX_FIELDS), ("n", C.c_uint64), ("params", gpz_params),
+                ("out", C.c_void_p), ("out_capacity", C.c_uint64), ("perm", C.c_void_p)]
+
+
+class gpz_decompress_chunk(C.Structure):
+    _fields_ = [("in_", C.c_void_p), ("in_size", C.c_uint64), ("fields", C.c_void_p * MAX_FIELDS),
+                ("n_fields", C.c_int), ("n", C.c_uint64)]
+
+
+class gpz_batch_config(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_uint32), ("claim", C.c_uint32), ("range_slice", C.c_uint32),
+                ("compact_ctas", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class GpzError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -61,6 +79,27 @@ def _load():
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
     L.gpz_launch_count.restype = u64
+    # batched entry points (include/gpz_batch.h)
+    L.gpz_batch_create_compress.argtypes = [P(gpz_compress_chunk), C.c_uint32, P(vp)]
+    L.gpz_batch_create_compress.restype = C.c_int
+    L.gpz_batch_create_decompress.argtypes = [P(gpz_decompress_chunk), C.c_uint32, P(vp)]
+    L.gpz_batch_create_decompress.restype = C.c_int
+    L.gpz_batch_destroy.argtypes = [vp]
+    L.gpz_batch_destroy.restype = None
+    L.gpz_batch_workspace_size.argtypes = [vp]
+    L.gpz_batch_workspace_size.restype = u64
+    L.gpz_batch_set_config.argtypes = [vp, P(gpz_batch_config)]
+    L.gpz_batch_set_config.restype = C.c_int
+    L.gpz_batch_get_config.argtypes = [vp, P(gpz_batch_config)]
+    L.gpz_batch_get_config.restype = C.c_int
+    L.gpz_batch_run.argtypes = [vp, vp, u64, vp, C.c_int, vp]
+    L.gpz_batch_run.restype = C.c_int
+    L.gpz_batch_sync_status.argtypes = [vp, vp, P(C.c_uint32), vp]
+    L.gpz_batch_sync_status.restype = C.c_int
+    L.gpz_batch_tune.argtypes = [vp, vp, u64, vp, C.c_int, vp, P(gpz_batch_config), P(C.c_float)]
+    L.gpz_batch_tune.restype = C.c_int
+    L.gpz_batch_launches.argtypes = [vp]
+    L.gpz_batch_launches.restype = C.c_uint32
     return L
 
 
@@ -175,6 +214,68 @@ def gpz_sync_status(ws, stream=None):
     return lib.gpz_sync_status(ws.data_ptr(), _stream_handle(stream))
 
 
+def gpz_batch_create_compress(chunks):
+    """chunks: sequence of gpz_compress_chunk.  Returns (status, plan handle)."""
+    arr = (gpz_compress_chunk * len(chunks))(*chunks)
+    h = C.c_void_p()
+    st = lib.gpz_batch_create_compress(arr, len(chunks), C.byref(h))
+    return st, h
+
+
+def gpz_batch_create_decompress(chunks):
+    arr = (gpz_decompress_chunk * len(chunks))(*chunks)
+    h = C.c_void_p()
+    st = lib.gpz_batch_create_decompress(arr, len(chunks), C.byref(h))
+    return st, h
+
+
+def gpz_batch_destroy(plan):
+    lib.gpz_batch_destroy(plan)
+
+
+def gpz_batch_workspace_size(plan):
+    return int(lib.gpz_batch_workspace_size(plan))
+
+
+def gpz_batch_set_config(plan, cfg):
+    return lib.gpz_batch_set_config(plan, C.byref(cfg))
+
+
+def gpz_batch_get_config(plan):
+    cfg = gpz_batch_config()
+    st = lib.gpz_batch_get_config(plan, C.byref(cfg))
+    if st != OK:
+        raise GpzError(st, "gpz_batch_get_config")
+    return cfg
+
+
+def gpz_batch_run(plan, ws, ws_size, d_out_sizes=None, use_graph=False, stream=None):
+    return lib.gpz_batch_run(plan, ws.data_ptr(), ws_size,
+                             d_out_sizes.data_ptr() if d_out_sizes is not None else None,
+                             1 if use_graph else 0, _stream_handle(stream))
+
+
+def gpz_batch_sync_status(plan, ws, count, stream=None):
+    """Returns (first status, per-chunk status list)."""
+    arr = (C.c_uint32 * count)()
+    st = lib.gpz_batch_sync_status(plan, ws.data_ptr(), arr, _stream_handle(stream))
+    return st, [int(v) for v in arr]
+
+
+def gpz_batch_tune(plan, ws, ws_size, d_out_sizes=None, reps=2, stream=None):
+    """Returns (status, chosen gpz_batch_config, ms per run)."""
+    cfg = gpz_batch_config()
+    ms = C.c_float(0.0)
+    st = lib.gpz_batch_tune(plan, ws.data_ptr(), ws_size,
+                            d_out_sizes.data_ptr() if d_out_sizes is not None else None, reps,
+                            _stream_handle(stream), C.byref(cfg), C.byref(ms))
+    return st, cfg, float(ms.value)
+
+
+def gpz_batch_launches(plan):
+    return int(lib.gpz_batch_launches(plan))
+
+
 # ----------------------------------------------------------------------------- convenience wrappers
 
 class Compressor:
@@ -236,3 +337,124 @@ def compress(x, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
 def decompress(stream_buf, n_fields, n, stream=None):
     d = Decompressor(n, n_fields, stream_buf.device)
     return d(stream_buf, stream_buf.numel(), stream).clone()
+
+
+def _fields_list(x):
+    if isinstance(x, torch.Tensor):
+        return [x[f] for f in range(x.shape[0])] if x.dim() == 2 else [x]
+    return list(x)
+
+
+class BatchCompressor:
+    """A compression plan over many arrays (include/gpz_batch.h), with its
+    output buffers (one of gpz_bound_size bytes per chunk), the per-chunk size
+    array and the workspace.  chunks: list of (fields, params[, perm]) with
+    fields a [F, n] CUDA float32 tensor or a list of F 1-D tensors."""
+
+    def __init__(self, chunks, device=None, use_graph=True):
+        device = device or torch.device("cuda")
+        self.use_graph = use_graph
+        self.count = len(chunks)
+        self._keep = []
+        descs, self.outs, self.n = [], [], []
+        for ch in chunks:
+            fields, params = _fields_list(ch[0]), ch[1]
+            perm = ch[2] if len(ch) > 2 else None
+            n = fields[0].numel() if fields else 0
+            cap = gpz_bound_size(n, params.n_fields)
+            out = torch.empty(max(cap, 64), dtype=torch.uint8, device=device)
+            d = gpz_compress_chunk()
+            for f in range(params.n_fields):
+                d.fields[f] = fields[f].data_ptr() if n else None
+            d.n, d.params, d.out, d.out_capacity = n, params, out.data_ptr(), cap
+            d.perm = perm.data_ptr() if perm is not None else None
+            descs.append(d)
+            self.outs.append(out)
+            self.n.append(n)
+            self._keep.append((fields, perm))
+        st, self.plan = gpz_batch_create_compress(descs)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_create_compress")
+        self.ws_size = gpz_batch_workspace_size(self.plan)
+        self.ws = torch.empty(max(self.ws_size, 256), dtype=torch.uint8, device=device)
+        self.sizes = torch.zeros(self.count, dtype=torch.int64, device=device)
+
+    def __call__(self, stream=None):
+        st = gpz_batch_run(self.plan, self.ws, self.ws_size, self.sizes, self.use_graph, stream)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_run")
+
+    def status(self, stream=None):
+        return gpz_batch_sync_status(self.plan, self.ws, self.count, stream)
+
+    def streams(self):
+        """The chunks' streams (CUDA uint8 views of the exact sizes)."""
+        sizes = self.sizes.tolist()
+        return [self.outs[c][:sizes[c]] for c in range(self.count)]
+
+    def tune(self, reps=2, stream=None):
+        st, cfg, ms = gpz_batch_tune(self.plan, self.ws, self.ws_size, self.sizes, reps, stream)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_tune")
+        return cfg, ms
+
+    def close(self):
+        if self.plan:
+            gpz_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchDecompressor:
+    """A decompression plan: chunks is a list of (stream tensor, size in bytes,
+    n_fields, n); the outputs are allocated here, one [F, n] tensor per chunk."""
+
+    def __init__(self, chunks, device=None, use_graph=True, outs=None):
+        device = device or torch.device("cuda")
+        self.use_graph = use_graph
+        self.count = len(chunks)
+        descs = []
+        self.outs = outs if outs is not None else [
+            torch.empty((F, max(n, 1)), dtype=torch.float32, device=device) for (_, _, F, n) in chunks]
+        self._keep = [c[0] for c in chunks]
+        for (buf, size, F, n), out in zip(chunks, self.outs):
+            d = gpz_decompress_chunk()
+            d.in_, d.in_size, d.n_fields, d.n = buf.data_ptr(), size, F, n
+            for f in range(F):
+                d.fields[f] = out[f].data_ptr() if n else None
+            descs.append(d)
+        st, self.plan = gpz_batch_create_decompress(descs)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_create_decompress")
+        self.ws_size = gpz_batch_workspace_size(self.plan)
+        self.ws = torch.empty(max(self.ws_size, 256), dtype=torch.uint8, device=device)
+
+    def __call__(self, stream=None):
+        st = gpz_batch_run(self.plan, self.ws, self.ws_size, None, self.use_graph, stream)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_run")
+
+    def status(self, stream=None):
+        return gpz_batch_sync_status(self.plan, self.ws, self.count, stream)
+
+    def tune(self, reps=2, stream=None):
+        st, cfg, ms = gpz_batch_tune(self.plan, self.ws, self.ws_size, None, reps, stream)
+        if st != OK:
+            raise GpzError(st, "gpz_batch_tune")
+        return cfg, ms
+
+    def close(self):
+        if self.plan:
+            gpz_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,7 +9,9 @@ CPU oracle then both receive unchanged.
   cosmology         -- halo mixture + uniform background, positions and
                        velocities (OuterRim / NewWorlds / LAMMPS-sized)
   lidar             -- airborne-LiDAR-like scan-order point cloud (USGS 3DEP-like)
+  uniform_box_torch -- the same distribution drawn with torch (GPU or CPU)
   chunk_sizes       -- particle counts of the batched workload
+  batched_workload  -- the batched workload: many chunks of 3 or 6 fields
   request_trace     -- the served workload's Poisson arrivals
 
 The large generators use torch so that they can run on the GPU (fast) or
@@ -121,10 +123,65 @@ def lidar(n, seed=3, device="cpu", pts_per_line=20000, tile=10000.0):
     return out
 
 
+def uniform_box_torch(n, seed=0, device="cpu", box=BOX):
+    """[3, n] float32 uniform in [0, box)^3, drawn with torch (fast on a GPU)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    x = torch.rand((3, n), generator=g, device=torch.device(device), dtype=torch.float64) * box
+    return _below(x.to(torch.float32), box)
+
+
 def chunk_sizes(n_chunks=4096, lo=10_000, hi=4_000_000, seed=4):
     """Particle counts log-uniform in [lo, hi] (the batched workload)."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), n_chunks)).astype(np.int64)
+
+
+class BatchedWorkload:
+    """Chunks held in two pools (one per field count), each chunk's fields
+    starting on a 128-byte boundary."""
+
+    def __init__(self, n, F, rel, pools, offsets):
+        self.n, self.F, self.rel = [int(v) for v in n], [int(v) for v in F], [float(v) for v in rel]
+        self.pools, self.offsets = pools, [int(v) for v in offsets]
+        self.count = len(self.n)
+
+    def fields(self, c):
+        pool, o, n = self.pools[self.F[c]], self.offsets[c], self.n[c]
+        return [pool[f, o:o + n] for f in range(self.F[c])]
+
+    def input_bytes(self):
+        return sum(4 * n * F for n, F in zip(self.n, self.F))
+
+
+def batched_workload(n_chunks=4096, lo=10_000, hi=4_000_000, seed=4, device="cpu"):
+    """The batched workload: n_chunks chunks with log-uniform particle counts
+    in [lo, hi]; each has 3 fields drawn like the small configuration (uniform
+    box) or 6 drawn like the cosmology snapshot (its halo count scaled to keep
+    the snapshot's particles per halo), with equal odds, and a relative error
+    bound 1e-3 or 1e-4, with equal odds.  Chunk c is seeded 1000 + c."""
+    n = chunk_sizes(n_chunks, lo, hi, seed)
+    rng = np.random.default_rng(seed + 1)
+    F = rng.choice([3, 6], n_chunks)
+    rel = rng.choice([1e-3, 1e-4], n_chunks)
+    pad = [int(-(-int(v) // 32) * 32) for v in n]
+    offsets = np.zeros(n_chunks, dtype=np.int64)
+    pools = {}
+    for ff in (3, 6):
+        idx = [c for c in range(n_chunks) if F[c] == ff]
+        total = sum(pad[c] for c in idx)
+        pool = torch.empty((ff, max(total, 32)), dtype=torch.float32, device=torch.device(device))
+        o = 0
+        for c in idx:
+            offsets[c] = o
+            if ff == 3:
+                pool[:, o:o + n[c]] = uniform_box_torch(int(n[c]), seed=1000 + c, device=device)
+            else:
+                halos = max(4, int(round(20000 * int(n[c]) / 2 ** 26)))
+                pool[:, o:o + n[c]] = cosmology(int(n[c]), seed=1000 + c, n_halos=halos, device=device)
+            o += pad[c]
+        pools[ff] = pool
+    return BatchedWorkload(n, F, rel, pools, offsets)
 
 
 def request_trace(n_requests=20000, rate=2000.0, lo=100_000, hi=64_000_000, seed=5):

@@ -1,14 +1,17 @@
-"""The C ABI library loads and exports every entry point include/gpz.h
-declares; host-side entry points behave without touching a GPU."""
+"""The C ABI library loads and exports every entry point include/gpz.h and
+include/gpz_batch.h declare; host-side entry points behave without touching a
+GPU."""
 import ctypes as C
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "gpz.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("gpz.h", "gpz_batch.h")]
 
 
 @pytest.fixture(scope="module")
@@ -20,15 +23,24 @@ def gpz():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(gpz_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(gpz_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gpz_bound_size", "gpz_compress", "gpz_decompress", "gpz_compress_workspace_size",
                      "gpz_decompress_workspace_size", "gpz_sync_status", "gpz_inspect", "gpz_status_str"):
+        assert required in names
+
+
+def test_header_declares_the_batch_boundary():
+    names = declared_functions()
+    for required in ("gpz_batch_create_compress", "gpz_batch_create_decompress", "gpz_batch_run",
+                     "gpz_batch_tune", "gpz_batch_sync_status", "gpz_batch_destroy", "gpz_batch_workspace_size"):
         assert required in names
 
 
@@ -92,3 +104,83 @@ def test_argument_errors_need_no_device(gpz):
     assert L.gpz_decompress(dummy, 8, outs, 3, 10, None, 0, None) == gpz.ERR_CORRUPT
     assert L.gpz_decompress(dummy, 1024, outs, 0, 10, None, 0, None) == gpz.ERR_INVALID_ARG
     assert L.gpz_decompress(None, 1024, outs, 3, 10, None, 0, None) == gpz.ERR_INVALID_ARG
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_batch_struct_layout_matches_the_header(gpz, tmp_path):
+    """The binding's ctypes descriptors have the header's sizes and offsets."""
+    src = tmp_path / "sz.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "gpz_batch.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gpz_compress_chunk), offsetof(gpz_compress_chunk, n),
+           offsetof(gpz_compress_chunk, params), offsetof(gpz_compress_chunk, out),
+           offsetof(gpz_compress_chunk, perm), sizeof(gpz_decompress_chunk),
+           offsetof(gpz_decompress_chunk, n_fields), offsetof(gpz_decompress_chunk, n), sizeof(gpz_batch_config));
+    return 0;
+}
+""")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    cc, dc = gpz.gpz_compress_chunk, gpz.gpz_decompress_chunk
+    want = [C.sizeof(cc), cc.n.offset, cc.params.offset, cc.out.offset, cc.perm.offset, C.sizeof(dc),
+            dc.n_fields.offset, dc.n.offset, C.sizeof(gpz.gpz_batch_config)]
+    assert got == want
+
+
+def test_batch_argument_errors_need_no_device(gpz):
+    """Descriptor errors are found before any CUDA call; NULL plans are refused."""
+    L = gpz.lib
+
+    def chunk(n=1000, F=3, eb=1e-3, cap=None, out=4096, mode=0, G=3):
+        d = gpz.gpz_compress_chunk()
+        for f in range(F):
+            d.fields[f] = 16 * (f + 1)
+        d.n, d.params = n, gpz.make_params(F, eb, mode, G)
+        d.out = out
+        d.out_capacity = gpz.gpz_bound_size(n, F) if cap is None else cap
+        return d
+
+    def create(chunks):
+        arr = (gpz.gpz_compress_chunk * len(chunks))(*chunks)
+        h = C.c_void_p()
+        st = L.gpz_batch_create_compress(arr, len(chunks), C.byref(h))
+        assert not h.value
+        return st
+
+    assert create([chunk(), chunk(eb=0.0)]) == gpz.ERR_INVALID_ARG
+    assert create([chunk(), chunk(cap=100)]) == gpz.ERR_CAPACITY
+    assert create([chunk(out=4098)]) == gpz.ERR_INVALID_ARG
+    assert create([chunk(G=4)]) == gpz.ERR_INVALID_ARG
+    bad = chunk()
+    bad.params.n_fields = 9
+    assert create([bad]) == gpz.ERR_INVALID_ARG
+    bad = chunk()
+    bad.fields[1] = None
+    assert create([bad]) == gpz.ERR_INVALID_ARG
+    assert create([chunk(n=1 << 29, F=8, cap=1 << 62)]) == gpz.ERR_UNSUPPORTED
+    h = C.c_void_p()
+    assert L.gpz_batch_create_compress(None, 1, C.byref(h)) == gpz.ERR_INVALID_ARG
+    assert L.gpz_batch_create_compress((gpz.gpz_compress_chunk * 1)(chunk()), 0, C.byref(h)) == gpz.ERR_INVALID_ARG
+    assert L.gpz_batch_create_compress((gpz.gpz_compress_chunk * 1)(chunk()), 1, None) == gpz.ERR_INVALID_ARG
+
+    d = gpz.gpz_decompress_chunk()
+    d.in_, d.in_size, d.n_fields, d.n = 4096, 8, 3, 10
+    for f in range(3):
+        d.fields[f] = 16 * (f + 1)
+    assert L.gpz_batch_create_decompress((gpz.gpz_decompress_chunk * 1)(d), 1, C.byref(h)) == gpz.ERR_CORRUPT
+    d.in_size, d.n_fields = 1024, 0
+    assert L.gpz_batch_create_decompress((gpz.gpz_decompress_chunk * 1)(d), 1, C.byref(h)) == gpz.ERR_INVALID_ARG
+
+    assert L.gpz_batch_workspace_size(None) == 0
+    assert L.gpz_batch_launches(None) == 0
+    assert L.gpz_batch_run(None, C.c_void_p(256), 1 << 20, None, 0, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_batch_sync_status(None, C.c_void_p(256), None, None) == gpz.ERR_INVALID_ARG
+    cfg = gpz.gpz_batch_config()
+    assert L.gpz_batch_set_config(None, C.byref(cfg)) == gpz.ERR_INVALID_ARG
+    assert L.gpz_batch_get_config(None, C.byref(cfg)) == gpz.ERR_INVALID_ARG
+    assert L.gpz_batch_tune(None, C.c_void_p(256), 1 << 20, None, 1, None, None, None) == gpz.ERR_INVALID_ARG
+    L.gpz_batch_destroy(None)
