@@ -57,7 +57,7 @@ typedef struct {
 /* Launch shape of a plan.  A zero field takes the default.
  *   ctas_per_sm:   CTAs per SM of the persistent launches (compression 1..4,
  *                  decompression 1..5; clamped to what fits).  Default: the most that fit.
- *   claim:         work items (blocks or range slices) per ticket, 1..64.  Default 2.
+ *   claim:         blocks per ticket, 1..64 (range slices are claimed one at a time).  Default 4.
  *   range_slice:   values per range work item (relative bounds), a multiple
  *                  of 1024 in 1024..2^24.  Default 65536.
  *   compact_ctas:  CTAs of the compaction launch, 8 warps each, per SM, 1..32.  Default 16. */

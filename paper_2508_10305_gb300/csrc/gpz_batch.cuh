@@ -5,15 +5,16 @@
 //
 // The chunks of one field count F form a group, served by one persistent
 // launch of the kernel compiled for that F.  Its work is claimed from the
-// group's atomic ticket counter over a flattened item list, ordered by chunk:
-// in compression the range-pass slices of the group's relative-bound chunks
-// come first, then every block of every chunk; in decompression every block
-// of every chunk.  A CTA claims `claim` consecutive items per ticket and finds
-// each item's chunk by a forward search from the chunk of its previous item
-// (tickets only grow).  A block item of a
-// relative-bound chunk waits for that chunk's constants; those come from
-// range items with smaller tickets, claimed by CTAs that are already running
-// and never wait themselves, so the wait always ends (it is bounded anyway).
+// group's atomic ticket counters over a flattened item list, ordered by
+// chunk: in compression the range-pass slices of the group's relative-bound
+// chunks come first (claimed one at a time from their own counter), then
+// every block of every chunk; in decompression every block of every chunk.
+// A CTA claims `claim` consecutive blocks per ticket and finds each item's
+// chunk by a forward search from the chunk of its previous item (tickets only
+// grow).  A block of a relative-bound chunk waits for that chunk's constants;
+// those come from range items claimed before any block (by CTAs that are
+// already running and never wait themselves), so the wait always ends (it is
+// bounded anyway).
 #pragma once
 
 #include "gpz_internal.cuh"
@@ -54,7 +55,7 @@ struct BatchCompressArgs {
     uint32_t total_blocks;       // the group's blocks
     uint32_t slice;              // elements per range item
     uint32_t claim;              // items per ticket
-    uint32_t* ticket;            // the group's counter, zeroed
+    uint32_t* ticket;            // the group's block counter (ticket[24]: its range-item counter), zeroed
     uint32_t* rkeys;             // [chunks][kMaxFields][2]: ~order key of the min, order key of the max; zeroed
     uint32_t* rdone;             // [chunks] range items finished; zeroed
     uint32_t* ready;             // [chunks] 1 once the chunk's relative constants are written; zeroed
@@ -95,7 +96,7 @@ struct BatchDecompressArgs {
     uint32_t block_first;        // the group's first block
     uint32_t total_blocks;       // the group's blocks
     uint32_t claim;
-    uint32_t* ticket;            // the group's counter, zeroed
+    uint32_t* ticket;            // the group's block counter (ticket[24]: its range-item counter), zeroed
     uint32_t* chunk_status;      // [chunks] zeroed
 };
 

@@ -17,7 +17,9 @@ using namespace gpz::host;
 namespace {
 
 constexpr uint64_t kAlign = 256;
-constexpr uint64_t kCtrlBytes = 256;  // tickets[8], general counts[8], scan tile counter, scan status
+// block tickets[8], general counts[8] (at 8), scan tile counter (16), scan
+// status (17), range-item tickets[8] (24): one word each, per group
+constexpr uint64_t kCtrlBytes = 256;
 constexpr uint32_t kMaxItems = 1u << 31;
 
 struct Group {
@@ -118,7 +120,7 @@ gpz_batch_config clamp_cfg(const gpz_batch* p, gpz_batch_config c) {
     for (const auto& g : p->groups) fit = std::min(fit, g.max_ctas);
     if (fit < 1) fit = 1;
     if (c.ctas_per_sm == 0 || c.ctas_per_sm > (uint32_t)fit) c.ctas_per_sm = (uint32_t)fit;
-    if (c.claim == 0) c.claim = 2;
+    if (c.claim == 0) c.claim = 4;
     c.claim = std::min<uint32_t>(c.claim, 64);
     if (c.range_slice == 0) c.range_slice = 65536;
     c.range_slice = std::min<uint32_t>(std::max<uint32_t>(c.range_slice / 1024 * 1024, 1024), 1u << 24);

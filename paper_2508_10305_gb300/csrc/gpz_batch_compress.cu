@@ -120,73 +120,106 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 
 }  // namespace
 
+// The loop state lives in shared memory: thread 0 claims and decodes each
+// item between barriers, so that no register stays live across the inlined
+// block code (the block index is re-read from the slot where it is used).
+struct LoopState {
+    uint32_t q, stop;      // current item, end of the claimed run
+    uint32_t rcur, bcur;   // group-relative chunk cursors of range and block items
+    uint32_t loaded, ok;   // chunk whose arguments are in A, and whether its constants arrived
+    uint32_t kind, c;      // 0: range item, 1: block; its chunk
+    uint32_t local;        // range item within its chunk
+    uint32_t slot[2];      // block within its chunk, global block id
+};
+
 template <int F>
 __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCompressArgs g) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     __shared__ QseArgs A;
     __shared__ float2 red[kWarps];
-    __shared__ uint32_t s_ticket, s_ok;
+    __shared__ LoopState L;
     const int t = threadIdx.x;
-    const uint32_t total = g.range_items + g.total_blocks;
-    const uint32_t* range_end = g.range_end + g.first;
-    const uint32_t* block_end = g.block_end + g.first;
-    uint32_t rcur = 0, bcur = 0;  // group-relative chunk cursors
-    uint32_t loaded = 0xffffffffu;
-    bool loaded_ok = false;
-    if (t == 0) s_ticket = atomicAdd(g.ticket, g.claim);
-    __syncthreads();
-    uint32_t base = s_ticket;
-    while (base < total) {
-        uint32_t next = 0;
-        if (t == 0) next = atomicAdd(g.ticket, g.claim);  // in flight while the items run
-        const uint32_t stop = total - base < g.claim ? total : base + g.claim;
-        for (uint32_t q = base; q < stop; ++q) {
-            if (q < g.range_items) {
-                const uint32_t r = g.range_first + q;
-                rcur = find_chunk(range_end, g.nchunks, r, rcur);
-                const uint32_t c = g.first + rcur;
-                range_item(g, c, r - g.chunks[c].range_base, red);
-            } else {
-                const uint32_t gb = g.block_first + (q - g.range_items);
-                bcur = find_chunk(block_end, g.nchunks, gb, bcur);
-                const uint32_t c = g.first + bcur;
-                if (c != loaded) {
-                    if (t == 0) {
-                        uint32_t ok = 1u;
-                        if (g.chunks[c].mode) {  // wait for the chunk's relative constants
-                            const long long t0 = clock64();
-                            while (ld_acquire_u32(g.ready + c) == 0u) {
-                                if (clock64() - t0 > (1ll << 31)) {
-                                    set_status(g.chunk_status + c, kStTimeout);
-                                    ok = 0u;
-                                    break;
-                                }
-                                __nanosleep(64);
-                            }
-                        }
-                        s_ok = ok;
-                    }
-                    __syncthreads();
-                    load_chunk_args(g, c, A);
-                    __syncthreads();
-                    loaded = c;
-                    loaded_ok = s_ok != 0u;
-                }
-                const uint32_t b = gb - g.chunks[c].block_base;
-                if (!loaded_ok) {
-                    if (t == 0) A.sizes[b] = 0u;  // the chunk is reported as timed out
-                } else if ((uint64_t)(b + 1) * kBlock <= A.n) {
-                    qse_block_fast<F, true>(A, dsm, S, b, gb);
+    if (t == 0) {
+        L.q = L.stop = 0u;
+        L.rcur = L.bcur = 0u;
+        L.loaded = 0xffffffffu;
+        L.ok = 0u;
+        L.kind = 0u;
+    }
+    for (;;) {
+        if (t == 0) {
+            const uint32_t total = g.range_items + g.total_blocks;
+            if (L.q >= L.stop) {  // claim: range items one at a time, then runs of blocks
+                uint32_t b0 = g.range_items;
+                if (L.kind != 1u) b0 = atomicAdd(g.ticket + 24, 1u);
+                if (b0 < g.range_items) {
+                    L.q = b0;
+                    L.stop = b0 + 1u;
                 } else {
-                    qse_block_fast<F, false>(A, dsm, S, b, gb);
+                    L.kind = 1u;
+                    b0 = g.range_items + atomicAdd(g.ticket, g.claim);
+                    L.q = b0;
+                    L.stop = total - min(b0, total) < g.claim ? total : b0 + g.claim;
                 }
             }
-            __syncthreads();
+            const uint32_t q = L.q;
+            if (q < g.range_items) {
+                const uint32_t r = g.range_first + q;
+                const uint32_t rc = find_chunk(g.range_end + g.first, g.nchunks, r, L.rcur);
+                L.rcur = rc;
+                L.kind = 0u;
+                L.c = g.first + rc;
+                L.local = r - g.chunks[g.first + rc].range_base;
+            } else if (q < total) {
+                const uint32_t gb = g.block_first + (q - g.range_items);
+                const uint32_t bc = find_chunk(g.block_end + g.first, g.nchunks, gb, L.bcur);
+                L.bcur = bc;
+                L.kind = 1u;
+                L.c = g.first + bc;
+                L.slot[0] = gb - g.chunks[g.first + bc].block_base;
+                L.slot[1] = gb;
+            }
         }
-        if (t == 0) s_ticket = next;
         __syncthreads();
-        base = s_ticket;
+        if (L.q >= g.range_items + g.total_blocks) break;
+        if (L.kind == 0u) {
+            range_item(g, L.c, L.local, red);
+        } else {
+            const uint32_t c = L.c;
+            if (c != L.loaded) {
+                __syncthreads();  // every thread has read L.loaded
+                if (t == 0) {
+                    uint32_t ok = 1u;
+                    if (g.chunks[c].mode) {  // wait for the chunk's relative constants
+                        const long long t0 = clock64();
+                        while (ld_acquire_u32(g.ready + c) == 0u) {
+                            if (clock64() - t0 > (1ll << 31)) {
+                                set_status(g.chunk_status + c, kStTimeout);
+                                ok = 0u;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                    L.ok = ok;
+                    L.loaded = c;
+                }
+                __syncthreads();
+                load_chunk_args(g, c, A);
+                __syncthreads();
+            }
+            const SlotBlock idx{L.slot};
+            if (!L.ok) {
+                if (t == 0) A.sizes[idx.b()] = 0u;  // the chunk is reported as timed out
+            } else if ((uint64_t)(idx.b() + 1) * kBlock <= A.n) {
+                qse_block_fast<F, true>(A, dsm, S, idx);
+            } else {
+                qse_block_fast<F, false>(A, dsm, S, idx);
+            }
+        }
+        __syncthreads();
+        if (t == 0) L.q = L.q + 1u;
     }
 }
 

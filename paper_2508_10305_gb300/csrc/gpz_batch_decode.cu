@@ -8,44 +8,58 @@
 
 namespace gpz {
 
+// The loop state lives in shared memory: thread 0 claims and decodes each
+// item between barriers, so that no register stays live across the inlined
+// block code (the block index is re-read from the slot where it is used).
+struct DecLoopState {
+    uint32_t q, stop, cur, loaded, b;
+};
+
 template <int F>
 __global__ void __launch_bounds__(kDecThreads, 5) gpz_batch_decompress_kernel(BatchDecompressArgs g) {
     __shared__ DecShared S;
     __shared__ DecArgs A;
-    __shared__ uint32_t s_ticket;
+    __shared__ DecLoopState L;
     const int t = threadIdx.x;
-    const uint32_t* block_end = g.block_end + g.first;
-    uint32_t cur = 0, loaded = 0xffffffffu;  // group-relative
-    if (t == 0) s_ticket = atomicAdd(g.ticket, g.claim);
-    __syncthreads();
-    uint32_t base = s_ticket;
-    while (base < g.total_blocks) {
-        uint32_t next = 0;
-        if (t == 0) next = atomicAdd(g.ticket, g.claim);  // in flight while the blocks decode
-        const uint32_t stop = g.total_blocks - base < g.claim ? g.total_blocks : base + g.claim;
-        for (uint32_t q = base; q < stop; ++q) {
-            const uint32_t gb = g.block_first + q;
-            cur = find_chunk(block_end, g.nchunks, gb, cur);
-            const BatchChunk* ch = g.chunks + g.first + cur;
-            if (cur != loaded) {
-                if (t < kMaxFields) A.out[t] = ch->out[t];
-                if (t == 32) {
-                    A.stream = ch->src;
-                    A.total_words = ch->words;
-                    A.n = ch->n;
-                    A.F = F;
-                    A.nblocks = ch->nblocks;
-                    A.status = g.chunk_status + g.first + cur;
-                }
-                __syncthreads();
-                loaded = cur;
+    if (t == 0) {
+        L.q = L.stop = L.cur = 0u;
+        L.loaded = 0xffffffffu;
+    }
+    for (;;) {
+        if (t == 0) {
+            if (L.q >= L.stop) {  // claim the next run of blocks
+                const uint32_t b0 = atomicAdd(g.ticket, g.claim);
+                L.q = b0;
+                L.stop = g.total_blocks - min(b0, g.total_blocks) < g.claim ? g.total_blocks : b0 + g.claim;
             }
-            decode_block<F>(A, S, gb - ch->block_base);
+            if (L.q < g.total_blocks) {
+                const uint32_t gb = g.block_first + L.q;
+                const uint32_t cur = find_chunk(g.block_end + g.first, g.nchunks, gb, L.cur);
+                L.cur = cur;
+                L.b = gb - g.chunks[g.first + cur].block_base;
+            }
+        }
+        __syncthreads();
+        if (L.q >= g.total_blocks) break;
+        const uint32_t cur = L.cur;
+        if (cur != L.loaded) {
+            __syncthreads();  // every thread has read L.loaded
+            const BatchChunk* ch = g.chunks + g.first + cur;
+            if (t < kMaxFields) A.out[t] = ch->out[t];
+            if (t == 32) {
+                A.stream = ch->src;
+                A.total_words = ch->words;
+                A.n = ch->n;
+                A.F = F;
+                A.nblocks = ch->nblocks;
+                A.status = g.chunk_status + g.first + cur;
+            }
+            if (t == 64) L.loaded = cur;
             __syncthreads();
         }
-        if (t == 0) s_ticket = next;
+        decode_block<F>(A, S, DecSlotBlock{&L.b});
         __syncthreads();
-        base = s_ticket;
+        if (t == 0) L.q = L.q + 1u;
     }
 }
 

@@ -125,9 +125,20 @@ struct DecShared {
     alignas(16) uint32_t stage[kDecStageWords];
 };
 
-// Decode block b of the stream described by a (every thread of the CTA).
-template <int F>
-__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uint32_t b) {
+// Where a CTA gets its block's index: the grid (one CTA per block), or a
+// shared-memory slot written by a persistent loop and re-read at each use,
+// so that the index holds no register through the block code.
+struct DecGridBlock {
+    __device__ __forceinline__ uint32_t b() const { return blockIdx.x; }
+};
+struct DecSlotBlock {
+    const volatile uint32_t* slot;
+    __device__ __forceinline__ uint32_t b() const { return *slot; }
+};
+
+// Decode block idx.b() of the stream described by a (every thread of the CTA).
+template <int F, class Idx>
+__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx idx) {
     uint16_t* uniq = S.uniq;
     uint32_t* mask = S.mask;
     uint32_t* mpre = S.mpre;
@@ -138,8 +149,8 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uin
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t* Sw = a.stream;
-    const uint64_t first = (uint64_t)b * kBlock;
-    const int n_b = (int)((a.n - first) < (uint64_t)kBlock ? (a.n - first) : (uint64_t)kBlock);
+    const uint32_t b = idx.b();
+    const int n_b = (int)((a.n - (uint64_t)b * kBlock) < (uint64_t)kBlock ? (a.n - (uint64_t)b * kBlock) : (uint64_t)kBlock);
     const uint64_t table_start = kHeaderWords + 2ull * F;
     const uint64_t payload_start = table_start + a.nblocks + 1;
     const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
@@ -226,7 +237,8 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uin
     if (raw) {
 #pragma unroll
         for (int f = 0; f < F; ++f)
-            for (int i = t; i < n_b; i += kDecThreads) a.out[f][first + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
+            for (int i = t; i < n_b; i += kDecThreads)
+                a.out[f][(uint64_t)idx.b() * kBlock + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
         return;
     }
 
@@ -330,7 +342,8 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uin
         }
     }
     if (!fast) {
-        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, G, j0, n_b, first, key[0], key[1], key[2], key[3]);
+        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, G, j0, n_b, (uint64_t)idx.b() * kBlock, key[0], key[1],
+                       key[2], key[3]);
         return;
     }
     uint32_t rr[4][4];
@@ -374,7 +387,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, uin
             const uint32_t code = __funnelshift_r(lo, hi, kb) & L.cm[f];
             qv[e] = f < P ? (code | (((key[e] >> L.ks[f]) & L.gm[f]) << L.of[f])) : code;
         }
-        store4(a.out[f] + first + j0, qv, bits[f], s[f], mn[f], n_b - j0);
+        store4(a.out[f] + (uint64_t)idx.b() * kBlock + j0, qv, bits[f], s[f], mn[f], n_b - j0);
     }
 }
 

@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(kThreads, 4) gpz_qse_kernel(QseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
-        qse_block_fast<F, true>(a, dsm, S, blockIdx.x, blockIdx.x);
+        qse_block_fast<F, true>(a, dsm, S, GridBlock{});
     else
-        qse_block_fast<F, false>(a, dsm, S, blockIdx.x, blockIdx.x);
+        qse_block_fast<F, false>(a, dsm, S, GridBlock{});
 }
 
 template <int F>

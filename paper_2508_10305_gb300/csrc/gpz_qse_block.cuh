@@ -39,6 +39,19 @@ struct QseShared {
     uint32_t warp_tot[kWarps], warp_nz[kWarps];
 };
 
+// Where the fast path gets its block's index: the grid (one CTA per block),
+// or a shared-memory slot written by a persistent loop and re-read at each
+// use, so that the index holds no register through the block code.
+struct GridBlock {
+    __device__ __forceinline__ uint32_t b() const { return blockIdx.x; }   // block within its array
+    __device__ __forceinline__ uint32_t id() const { return blockIdx.x; }  // entry for the general list
+};
+struct SlotBlock {
+    const volatile uint32_t* slot;  // [0]: block within its array, [1]: entry for the general list
+    __device__ __forceinline__ uint32_t b() const { return slot[0]; }
+    __device__ __forceinline__ uint32_t id() const { return slot[1]; }
+};
+
 // Order-preserving map of finite floats to u32 (-0 < +0).
 __device__ __forceinline__ uint32_t order_key(float x) {
     const uint32_t u = __float_as_uint(x);
@@ -92,7 +105,9 @@ struct BitAppender {
 };
 
 template <int F>
-__device__ __forceinline__ void write_raw(const QseArgs& a, uint64_t first, int n_b, uint32_t* out, int t) {
+__device__ __forceinline__ void write_raw(const QseArgs& a, uint32_t b, int n_b, int t) {
+    const uint64_t first = (uint64_t)b * kBlock;
+    uint32_t* out = a.temp + (size_t)b * a.slot_words;
     if (t == 0) out[0] = 1u;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -101,7 +116,7 @@ __device__ __forceinline__ void write_raw(const QseArgs& a, uint64_t first, int 
     }
     if (a.perm)
         for (int i = t; i < n_b; i += kThreads) a.perm[first + i] = (uint32_t)(first + i);
-    if (t == 0) a.sizes[first / kBlock] = 1u + (uint32_t)F * (uint32_t)n_b;
+    if (t == 0) a.sizes[b] = 1u + (uint32_t)F * (uint32_t)n_b;
 }
 
 // The general per-block path: any block, including codes >= 2^23, values
@@ -170,7 +185,7 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
     if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
     __syncthreads();  // A
     if (S.flags & 1u) {
-        write_raw<F>(a, first, n_b, out, t);
+        write_raw<F>(a, b, n_b, t);
         return;
     }
 
@@ -221,7 +236,7 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
     if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&S.flags, 2u);
     __syncthreads();  // B
     if (S.flags & 2u) {
-        write_raw<F>(a, first, n_b, out, t);
+        write_raw<F>(a, b, n_b, t);
         return;
     }
 
@@ -401,7 +416,7 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
     const uint32_t rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t enc = hdr + dwords + cwords + rwords;
     if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
-        write_raw<F>(a, first, n_b, out, t);
+        write_raw<F>(a, b, n_b, t);
         return;
     }
 
@@ -550,20 +565,17 @@ __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool 
 
 // Block b of the array described by a; a block the fast path cannot take is
 // appended to a.general_list as list_id.
-template <int F, bool FULL>
-__device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, uint32_t b,
-                                               uint32_t list_id) {
+template <int F, bool FULL, class Idx>
+__device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, Idx idx) {
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const uint64_t first = (uint64_t)b * kBlock;
-    const int n_b = FULL ? kBlock : (int)(a.n - first);
+    const int n_b = FULL ? kBlock : (int)(a.n - (uint64_t)idx.b() * kBlock);
     uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
     uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
     uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastRegion);        // [512]
     uint16_t* cnt = uniq + kMaxBins;                                         // [512]
     uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
     uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
-    uint32_t* out = a.temp + (size_t)b * a.slot_words;
 
     if (t < F) {
         S.minkey[t] = 0xffffffffu;
@@ -588,7 +600,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-        const float* src = a.fields[f] + first + 128 * w + lane;
+        const float* src = a.fields[f] + (uint64_t)idx.b() * kBlock + 128 * w + lane;
 #pragma unroll
         for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
     }
@@ -615,7 +627,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
     __syncthreads();  // A
     if (S.flags & 1u) {
-        write_raw<F>(a, first, n_b, out, t);
+        write_raw<F>(a, idx.b(), n_b, t);
         return;
     }
 
@@ -650,7 +662,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     if (big || W > kFastRecordBits) {
         // left to the general kernel (uniform decision)
-        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = list_id;
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
         return;
     }
 
@@ -690,7 +702,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     __syncthreads();  // C
     if (S.flags & 2u) {
-        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = list_id;
+        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
         return;
     }
 
@@ -774,7 +786,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     const uint32_t rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t enc = hdr + dwords + cwords + rwords;
     if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
-        write_raw<F>(a, first, n_b, out, t);
+        write_raw<F>(a, idx.b(), n_b, t);
         return;
     }
 
@@ -829,14 +841,17 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     __syncthreads();
     {
+        const uint32_t b = idx.b();
+        uint32_t* out = a.temp + (size_t)b * a.slot_words;
         const uint4* s4 = reinterpret_cast<const uint4*>(stage);
         uint4* o4 = reinterpret_cast<uint4*>(out);
         for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
         for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+        const uint64_t first = (uint64_t)b * kBlock;
+        if (a.perm)
+            for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
+        if (t == 0) a.sizes[b] = enc;
     }
-    if (a.perm)
-        for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
-    if (t == 0) a.sizes[b] = enc;
 }
 
 
