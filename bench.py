@@ -14,6 +14,15 @@ collective touches the data path).
 One JSON line on rank 0.  The reference arm (--impl reference) times the
 plain single-threaded CPU oracle on a bounded sample of the same workload.
 
+    python bench.py --workload served [--requests 4000]
+
+replays a Poisson trace (2,000 requests/s, 100K-64M particles log-uniform,
+the uniform-box, cosmology-like and LiDAR-like generators, half compress and
+half decompress) in real time against the serving engine with a 40 GB
+admission budget: continuous batching over two lanes against the plain path
+(one request per launch sequence, one lane); p50 / p99 latency and aggregate
+GB/s of each.
+
     python bench.py --workload batched [--chunks 4096] [--steps K] [--warmup W]
 
 measures the batched form instead (one line, not the headline): 4,096 chunks
@@ -55,7 +64,13 @@ def parse():
     ap.add_argument("--n", type=int, default=N_PARTICLES, help="particles (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched"])
+    ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served"])
+    ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served workload: requests per second")
+    ap.add_argument("--serve-arms", default="batched:2:64:0:64,plain:1:1:0:0",
+                    help="served workload: name:lanes:max_batch:max_batch_MB:express_lane_MB, comma separated; "
+                         "the first is reported as the served value, the one named plain as the comparison")
     ap.add_argument("--chunks", type=int, default=4096, help="batched workload: number of chunks")
     ap.add_argument("--chunk-lo", type=int, default=10_000)
     ap.add_argument("--chunk-hi", type=int, default=4_000_000)
@@ -599,6 +614,169 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- served workload
+
+SERVED_GENS = [("uniform box", 3, 1e-2, 0), ("cosmology-like", 6, 1e-4, 1), ("LiDAR-like", 3, 1e-3, 0)]
+
+
+def run_served(args):
+    """Real-time replay of a Poisson request trace against the serving engine:
+    continuous batching (two lanes, up to 64 requests per batch) against the
+    plain path (one lane, one request per launch sequence)."""
+    import torch
+    from paper_2508_10305_gb300 import build
+    build.build()
+    from paper_2508_10305_gb300 import gpz, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pool_n = 64_000_000
+    t0 = time.perf_counter()
+    pools = [synth.uniform_box_torch(pool_n, seed=0, device=dev),
+             synth.cosmology(pool_n, seed=2, device=dev),
+             synth.lidar(pool_n, seed=3, device=dev)]
+    params = [gpz.make_params(F, eb, mode, SEG_BITS) for (_, F, eb, mode) in SERVED_GENS]
+    # decompression requests read resident streams: 16 sizes per generator, log-spaced in [1e5, 6.4e7]
+    classes = np.unique(np.round(np.exp(np.linspace(np.log(1e5), np.log(6.4e7), 16))).astype(np.int64))
+    streams = {}
+    for g, (_, F, _, _) in enumerate(SERVED_GENS):
+        for n in classes:
+            comp = gpz.Compressor(int(n), F, params[g].eb[:F], params[g].mode, SEG_BITS, device=dev)
+            size = comp([pools[g][f, :n] for f in range(F)])
+            streams[(g, int(n))] = comp.out[:size].clone()
+            del comp
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    t_arr, size, gen, op = synth.request_trace(args.requests, rate=args.rate, lo=100_000, hi=64_000_000, seed=5)
+    rng = np.random.default_rng(6)
+    reqs = []
+    for i in range(args.requests):
+        g, F = int(gen[i]), SERVED_GENS[int(gen[i])][1]
+        if op[i] == 0:
+            n = int(size[i])
+            off = int(rng.integers(0, (pool_n - n) // 32 + 1)) * 32
+            reqs.append((0, g, F, n, off))
+        else:
+            n = int(classes[np.argmin(np.abs(np.log(classes) - np.log(size[i])))])
+            reqs.append((1, g, F, n, 0))
+    raw_bytes = sum(4 * r[3] * r[2] for r in reqs)
+
+    def arm(lanes, max_batch, batch_mb, lane_mb):
+        srv = gpz.Server(int(args.budget_gb * (1 << 30)), lanes=lanes, max_batch=max_batch,
+                         max_batch_bytes=int(batch_mb * (1 << 20)), lane_bytes=int(lane_mb * (1 << 20)))
+        # warm-up: one request of each kind and generator
+        warm = []
+        for g, (_, F, _, _) in enumerate(SERVED_GENS):
+            warm.append(srv.submit_compress([pools[g][f, :200_000] for f in range(F)], params[g]))
+            s_ = streams[(g, int(classes[0]))]
+            warm.append(srv.submit_decompress(s_, s_.numel(), F, int(classes[0])))
+        left = len(warm)
+        while left:
+            for res in srv.poll(timeout_ms=5000):
+                srv.release(res["id"])
+                left -= 1
+        results, checks = [], {}
+        sample = set(range(0, len(reqs), 97))
+        id_to_req = {}
+        done = threading.Event()
+
+        def poller():
+            got = 0
+            while got < len(reqs):
+                for res in srv.poll(timeout_ms=200):
+                    k = id_to_req.get(res["id"])
+                    while k is None:  # the submitting thread has not recorded the id yet
+                        time.sleep(0.0001)
+                        k = id_to_req.get(res["id"])
+                    if k in sample and res["status"] == gpz.OK:
+                        r = reqs[k]
+                        checks[k] = (srv.stream_of(res).clone() if r[0] == 0 else
+                                     srv.fields_of(res, r[2], r[3]))
+                    results.append((k, res))
+                    srv.release(res["id"])
+                    got += 1
+            done.set()
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        lag = []
+        start = time.perf_counter() + 0.05
+        for k, r in enumerate(reqs):
+            target = start + float(t_arr[k])
+            while True:
+                dt = target - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 0.0006:
+                    time.sleep(dt - 0.0004)
+            kind, g, F, n, off = r
+            if kind == 0:
+                rid = srv.submit_compress([pools[g][f, off:off + n] for f in range(F)], params[g])
+            else:
+                s_ = streams[(g, n)]
+                rid = srv.submit_decompress(s_, s_.numel(), F, n)
+            id_to_req[rid] = k
+            lag.append(time.perf_counter() - target)
+        done.wait()
+        th.join()
+        stats = srv.stats()
+        srv.close()
+        # parity of the sampled results against one call per request
+        equal = 0
+        for k, out in checks.items():
+            kind, g, F, n, off = reqs[k]
+            if kind == 0:
+                comp = gpz.Compressor(n, F, params[g].eb[:F], params[g].mode, SEG_BITS, device=dev)
+                sz = comp([pools[g][f, off:off + n] for f in range(F)])
+                equal += int(torch.equal(comp.out[:sz], out))
+            else:
+                s_ = streams[(g, n)]
+                ref = gpz.Decompressor(n, F, device=dev)(s_, s_.numel())
+                equal += int(torch.equal(ref[:, :n].view(torch.int32), out.view(torch.int32)))
+        lat = np.array([(res["t_done_ns"] - res["t_submit_ns"]) / 1e6 for _, res in results])
+        kinds = np.array([reqs[k][0] for k, _ in results])
+        ok = all(res["status"] == gpz.OK for _, res in results)
+        span = (max(res["t_done_ns"] for _, res in results) - min(res["t_submit_ns"] for _, res in results)) / 1e9
+        bsz = np.array([res["batch_size"] for _, res in results])
+
+        def pct(a, q):
+            return float(np.percentile(a, q)) if a.size else None
+        return {
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(lat.mean()),
+            "compress_p50_ms": pct(lat[kinds == 0], 50), "compress_p99_ms": pct(lat[kinds == 0], 99),
+            "decompress_p50_ms": pct(lat[kinds == 1], 50), "decompress_p99_ms": pct(lat[kinds == 1], 99),
+            "aggregate_gbs": raw_bytes / span / 1e9, "span_s": span, "all_ok": ok,
+            "batches": stats["batches"], "mean_batch": float(bsz.mean()), "max_batch": int(bsz.max()),
+            "arena_peak_gb": stats["arena_peak"] / 1e9, "submit_lag_p99_ms": 1e3 * float(np.percentile(lag, 99)),
+            "sampled_equal_single_call": equal, "sampled": len(checks), "lanes": lanes, "max_batch_cfg": max_batch,
+            "max_batch_mb": batch_mb, "express_lane_mb": lane_mb,
+        }
+
+    arms = {}
+    with ClockSampler(0) as clk:
+        for spec in args.serve_arms.split(","):
+            name, lanes, mb, bmb, lmb = spec.split(":")
+            arms[name] = arm(int(lanes), int(mb), float(bmb), float(lmb))
+    names = list(arms)
+    batched, plain = arms[names[0]], arms.get("plain", arms[names[-1]])
+    offered = raw_bytes / float(t_arr[-1]) / 1e9
+    line = {
+        "metric": "served p50/p99 latency (ms) and aggregate GB/s: continuous batching vs plain path",
+        "value": batched["p99_ms"], "unit": "ms (p99 latency)", "n_gpus": 1, "steps": args.requests, "warmup": 6,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "served: Poisson %d requests/s, %d requests, 100K-64M particles log-uniform, "
+                               "generators uniform box (3 fields, abs 1e-2) / cosmology-like (6, rel 1e-4) / "
+                               "LiDAR-like (3, abs 1e-3), half compress, half decompress (resident streams of 16 "
+                               "size classes)" % (args.rate, args.requests),
+                   "budget_gb": args.budget_gb, "offered_gbs": offered, "raw_gb": raw_bytes / 1e9},
+        "served_arm": names[0], "arms": arms,
+        "p99_speedup_vs_plain": plain["p99_ms"] / batched["p99_ms"],
+        "p50_speedup_vs_plain": plain["p50_ms"] / batched["p50_ms"],
+        "clocks": clk.summary(), "prepare_s": prep_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -607,6 +785,9 @@ def main():
     elif args.workload == "batched":
         if rank == 0:
             run_batched(args)
+    elif args.workload == "served":
+        if rank == 0:
+            run_served(args)
     else:
         run_gpz(args, rank, world, local)
 

@@ -1,0 +1,349 @@
+// gpz_batch_core.cu -- host side of one batched run (see gpz_batch_core.hpp):
+// descriptor checks, grouping by field count, the flattened work lists, the
+// workspace layout and the enqueue of the kernels.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "gpz_batch_core.hpp"
+#include "gpz_host.hpp"
+
+namespace gpz {
+namespace host {
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+// block tickets[8], general counts[8] (at 8), scan tile counter (16), scan
+// status (17), range-item tickets[8] (24): one word each, per group
+constexpr uint64_t kCtrlBytes = 256;
+constexpr uint32_t kMaxItems = 1u << 31;
+
+uint64_t ntiles_of(uint64_t blocks) { return (blocks + 1 + kScanTile - 1) / kScanTile; }
+
+// Occupancy of the persistent kernels per field count (also sets their
+// shared-memory attributes), looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_occ_mu;
+int g_occ[kMaxDevices][2][kMaxFields + 1] = {};
+int g_sms[kMaxDevices] = {};
+
+gpz_status device_info(int kind, int F, int* sms, int* ctas) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GPZ_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_occ_mu);
+    if (!g_sms[dev] && (cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                        g_sms[dev] < 1)) {
+        g_sms[dev] = 0;
+        return GPZ_ERR_CUDA;
+    }
+    int& o = g_occ[dev][kind][F];
+    if (!o) o = kind == 0 ? batch_compress_max_ctas_per_sm(F) : batch_decompress_max_ctas_per_sm(F);
+    if (o < 1) {
+        o = 0;
+        return GPZ_ERR_CUDA;
+    }
+    *sms = g_sms[dev];
+    *ctas = o;
+    return GPZ_OK;
+}
+
+gpz_batch_config clamp_cfg(const BatchCore& c, gpz_batch_config cfg) {
+    int fit = 5;
+    for (const auto& g : c.groups) fit = std::min(fit, g.max_ctas);
+    if (fit < 1) fit = 1;
+    if (cfg.ctas_per_sm == 0 || cfg.ctas_per_sm > (uint32_t)fit) cfg.ctas_per_sm = (uint32_t)fit;
+    if (cfg.claim == 0) cfg.claim = 4;
+    cfg.claim = std::min<uint32_t>(cfg.claim, 64);
+    if (cfg.range_slice == 0) cfg.range_slice = 65536;
+    cfg.range_slice = std::min<uint32_t>(std::max<uint32_t>(cfg.range_slice / 1024 * 1024, 1024), 1u << 24);
+    if (cfg.compact_ctas == 0) cfg.compact_ctas = 16;
+    cfg.compact_ctas = std::min<uint32_t>(cfg.compact_ctas, 32);
+    return cfg;
+}
+
+// Range items of every relative-bound chunk for the current slice.  False
+// when the items do not fit the 31-bit ticket space.
+bool lay_out_range(BatchCore& c) {
+    uint64_t r = 0;
+    c.range_end.assign(c.count(), 0);
+    for (auto& g : c.groups) {
+        g.range_first = (uint32_t)r;
+        for (uint32_t k = 0; k < g.count; ++k) {
+            BatchChunk& ch = c.chunks[g.first + k];
+            ch.range_base = (uint32_t)r;
+            ch.range_slices = 0;
+            if (c.kind == 0 && ch.mode == GPZ_EB_REL) {
+                const uint64_t s = std::max<uint64_t>(1, (ch.n + c.cfg.range_slice - 1) / c.cfg.range_slice);
+                ch.range_slices = (uint32_t)std::min<uint64_t>(s, kMaxItems);
+                r += (uint64_t)ch.F * s;
+            }
+            c.range_end[g.first + k] = (uint32_t)std::min<uint64_t>(r, kMaxItems);
+        }
+        g.range_items = (uint32_t)std::min<uint64_t>(r - g.range_first, kMaxItems);
+        if ((uint64_t)g.range_items + g.blocks >= kMaxItems) return false;
+    }
+    return r < kMaxItems;
+}
+
+uint64_t desc_offset(const BatchCore& c, int part) {  // 0 chunks, 1 range_end, 2 block_end
+    const uint64_t a = align_up(sizeof(BatchChunk) * c.count(), kAlign), b = align_up(4ull * c.count(), kAlign);
+    return part == 0 ? 0 : part == 1 ? a : a + b;
+}
+
+}  // namespace
+
+gpz_status core_add_compress(BatchCore& c, const gpz_compress_chunk& d) {
+    const gpz_params& q = d.params;
+    const int F = q.n_fields;
+    if (F < 1 || F > kMaxFields || q.seg_bits < 0 || q.seg_bits > kMaxSegBits ||
+        (q.mode != GPZ_EB_ABS && q.mode != GPZ_EB_REL) || !d.out || !aligned(d.out, 4) ||
+        (d.perm && !aligned(d.perm, 4)))
+        return GPZ_ERR_INVALID_ARG;
+    for (int f = 0; f < F; ++f)
+        if (!(q.eb[f] > 0.0) || !std::isfinite(q.eb[f])) return GPZ_ERR_INVALID_ARG;
+    for (int f = 0; f < F && d.n > 0; ++f)
+        if (!d.fields[f] || !aligned(d.fields[f], 4)) return GPZ_ERR_INVALID_ARG;
+    if (nblocks_of(d.n) + (uint64_t)F * d.n >= (1ull << 32)) return GPZ_ERR_UNSUPPORTED;
+    if (d.out_capacity < gpz_bound_size(d.n, F)) return GPZ_ERR_CAPACITY;
+    if (c.count() >= kMaxItems) return GPZ_ERR_UNSUPPORTED;
+    BatchChunk ch;
+    std::memset(&ch, 0, sizeof(ch));
+    bool vec = true;
+    for (int f = 0; f < F; ++f) {
+        ch.in[f] = d.n ? d.fields[f] : nullptr;
+        vec = vec && (d.n == 0 || aligned(d.fields[f], 16));
+        if (q.mode == GPZ_EB_REL)
+            ch.rel[f] = q.eb[f];
+        else
+            ch.params[f] = finalise(q.eb[f]);
+    }
+    ch.dst = static_cast<uint32_t*>(d.out);
+    ch.words = d.out_capacity / 4;
+    ch.n = d.n;
+    ch.perm = d.perm;
+    ch.nblocks = (uint32_t)nblocks_of(d.n);
+    ch.index = c.count();
+    ch.F = F;
+    ch.G = q.seg_bits;
+    ch.mode = q.mode;
+    ch.bulk_ok = vec ? 1 : 0;
+    c.kind = 0;
+    c.any_rel = c.any_rel || q.mode == GPZ_EB_REL;
+    c.chunks.push_back(ch);
+    return GPZ_OK;
+}
+
+gpz_status core_add_decompress(BatchCore& c, const gpz_decompress_chunk& d) {
+    const int F = d.n_fields;
+    if (!d.in || !aligned(d.in, 4) || F < 1 || F > kMaxFields) return GPZ_ERR_INVALID_ARG;
+    for (int f = 0; f < F && d.n > 0; ++f)
+        if (!d.fields[f] || !aligned(d.fields[f], 4)) return GPZ_ERR_INVALID_ARG;
+    if (d.in_size % 4 != 0 || d.in_size < 4ull * kHeaderWords) return GPZ_ERR_CORRUPT;
+    if (nblocks_of(d.n) + (uint64_t)F * d.n >= (1ull << 32)) return GPZ_ERR_UNSUPPORTED;
+    if (c.count() >= kMaxItems) return GPZ_ERR_UNSUPPORTED;
+    BatchChunk ch;
+    std::memset(&ch, 0, sizeof(ch));
+    for (int f = 0; f < F; ++f) ch.out[f] = d.n ? d.fields[f] : nullptr;
+    ch.src = static_cast<const uint32_t*>(d.in);
+    ch.words = d.in_size / 4;
+    ch.n = d.n;
+    ch.nblocks = (uint32_t)nblocks_of(d.n);
+    ch.index = c.count();
+    ch.F = F;
+    c.kind = 1;
+    c.chunks.push_back(ch);
+    return GPZ_OK;
+}
+
+gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
+    if (c.chunks.empty()) return GPZ_ERR_INVALID_ARG;
+    // group by field count, keeping the caller's order within a group
+    std::stable_sort(c.chunks.begin(), c.chunks.end(), [](const BatchChunk& a, const BatchChunk& b) { return a.F < b.F; });
+    c.groups.clear();
+    uint64_t blocks = 0, temp = 0;
+    for (uint32_t k = 0; k < c.count(); ++k) {
+        BatchChunk& ch = c.chunks[k];
+        if (c.groups.empty() || c.groups.back().F != ch.F) {
+            BatchGroup g{};
+            g.F = ch.F;
+            g.first = k;
+            g.block_first = (uint32_t)blocks;
+            c.groups.push_back(g);
+        }
+        BatchGroup& g = c.groups.back();
+        ++g.count;
+        ch.block_base = (uint32_t)blocks;
+        ch.temp_base = temp;
+        blocks += ch.nblocks;
+        g.blocks += ch.nblocks;
+        if (c.kind == 0) temp += (uint64_t)ch.nblocks * batch_slot_words(ch.F);
+        if (blocks >= kMaxItems) return GPZ_ERR_UNSUPPORTED;
+    }
+    c.total_blocks = (uint32_t)blocks;
+    c.temp_words = temp;
+    c.block_end.resize(c.count());
+    for (uint32_t k = 0; k < c.count(); ++k) c.block_end[k] = c.chunks[k].block_base + c.chunks[k].nblocks;
+    for (auto& g : c.groups) {
+        const gpz_status st = device_info(c.kind, g.F, &c.sms, &g.max_ctas);
+        if (st != GPZ_OK) return st;
+    }
+    c.cfg = clamp_cfg(c, cfg ? *cfg : gpz_batch_config{});
+    if (!lay_out_range(c)) return GPZ_ERR_UNSUPPORTED;
+
+    BatchLayout& L = c.L;
+    const uint64_t n = c.count();
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t at = o;
+        o += align_up(bytes, kAlign);
+        return at;
+    };
+    L = BatchLayout{};
+    L.ctrl = take(kCtrlBytes);
+    L.status = take(4 * n);
+    if (c.kind == 0) {
+        L.rkeys = take(4ull * kMaxFields * 2 * n);
+        L.rdone = take(4 * n);
+        L.ready = take(4 * n);
+        L.states = take(8 * ntiles_of(blocks));
+        L.zero_bytes = o;
+        L.rparams = take(sizeof(FieldParams) * kMaxFields * n);
+        L.offsets = take(8 * (blocks + 1));
+        L.sizes = take(4 * blocks);
+        L.list = take(4 * blocks);
+        L.out_sizes = take(8 * n);
+        L.temp = take(4 * temp);
+    } else {
+        L.zero_bytes = o;
+    }
+    L.total = o;
+    // kernels per run: per group the fused kernel and the general one (or the
+    // decoder) when the group has work, then the scan and the compaction
+    c.launches = c.kind == 0 ? 2u : 0u;
+    for (const auto& g : c.groups)
+        if ((c.kind == 0 && (uint64_t)g.range_items + g.blocks > 0) || (c.kind == 1 && g.blocks > 0))
+            c.launches += c.kind == 0 ? 2u : 1u;
+    return GPZ_OK;
+}
+
+gpz_status core_set_config(BatchCore& c, const gpz_batch_config& cfg, bool* redo) {
+    const gpz_batch_config v = clamp_cfg(c, cfg);
+    *redo = c.kind == 0 && c.any_rel && v.range_slice != c.cfg.range_slice;
+    c.cfg = v;
+    if (*redo && !lay_out_range(c)) return GPZ_ERR_UNSUPPORTED;
+    return GPZ_OK;
+}
+
+uint64_t core_device_bytes(const BatchCore& c) { return desc_offset(c, 2) + align_up(4ull * c.count(), kAlign); }
+
+void core_pack(const BatchCore& c, uint8_t* host) {
+    std::memcpy(host + desc_offset(c, 0), c.chunks.data(), sizeof(BatchChunk) * c.count());
+    std::memcpy(host + desc_offset(c, 1), c.range_end.data(), 4ull * c.count());
+    std::memcpy(host + desc_offset(c, 2), c.block_end.data(), 4ull * c.count());
+}
+
+BatchDevice core_device_view(const BatchCore& c, uint8_t* device) {
+    BatchDevice d;
+    d.chunks = reinterpret_cast<BatchChunk*>(device + desc_offset(c, 0));
+    d.range_end = reinterpret_cast<uint32_t*>(device + desc_offset(c, 1));
+    d.block_end = reinterpret_cast<uint32_t*>(device + desc_offset(c, 2));
+    return d;
+}
+
+gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws, uint64_t* d_out_sizes,
+                        cudaStream_t s, bool timed) {
+    const BatchLayout& L = c.L;
+    const gpz_batch_config& cfg = c.cfg;
+    uint32_t* ctrl = reinterpret_cast<uint32_t*>(ws + L.ctrl);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
+    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    Recorder rec(s);
+    if (timed) rec.begin((int)c.launches);
+    if (c.kind == 1) {
+        for (size_t k = 0; k < c.groups.size(); ++k) {
+            const BatchGroup& g = c.groups[k];
+            if (g.blocks == 0) continue;  // nothing to decode
+            BatchDecompressArgs a{};
+            a.chunks = dev.chunks;
+            a.first = g.first;
+            a.nchunks = g.count;
+            a.block_end = dev.block_end;
+            a.block_first = g.block_first;
+            a.total_blocks = g.blocks;
+            a.claim = cfg.claim;
+            a.ticket = ctrl + k;
+            a.chunk_status = status;
+            const uint32_t per_sm = std::min<uint32_t>(cfg.ctas_per_sm, (uint32_t)g.max_ctas);
+            const uint64_t want = ((uint64_t)g.blocks + cfg.claim - 1) / cfg.claim;
+            const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per_sm * c.sms, want));
+            if (launch_batch_decompress(a, g.F, grid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+            rec.mark("batch_decompress");
+        }
+        return GPZ_OK;
+    }
+    BatchCompressArgs a{};
+    a.chunks = dev.chunks;
+    a.range_end = dev.range_end;
+    a.block_end = dev.block_end;
+    a.slice = cfg.range_slice;
+    a.claim = cfg.claim;
+    a.rkeys = reinterpret_cast<uint32_t*>(ws + L.rkeys);
+    a.rdone = reinterpret_cast<uint32_t*>(ws + L.rdone);
+    a.ready = reinterpret_cast<uint32_t*>(ws + L.ready);
+    a.rparams = reinterpret_cast<FieldParams*>(ws + L.rparams);
+    a.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
+    a.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
+    a.chunk_status = status;
+    for (size_t k = 0; k < c.groups.size(); ++k) {
+        const BatchGroup& g = c.groups[k];
+        const uint64_t items = (uint64_t)g.range_items + g.blocks;
+        if (items == 0) continue;  // only empty absolute-bound chunks: the compaction writes their headers
+        a.first = g.first;
+        a.nchunks = g.count;
+        a.range_first = g.range_first;
+        a.range_items = g.range_items;
+        a.block_first = g.block_first;
+        a.total_blocks = g.blocks;
+        a.ticket = ctrl + k;
+        a.general_list = reinterpret_cast<uint32_t*>(ws + L.list) + g.block_first;
+        a.general_count = ctrl + 8 + k;
+        const uint32_t per_sm = std::min<uint32_t>(cfg.ctas_per_sm, (uint32_t)g.max_ctas);
+        const uint64_t want = g.range_items + ((uint64_t)g.blocks + cfg.claim - 1) / cfg.claim;
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per_sm * c.sms, want));
+        if (launch_batch_compress(a, g.F, grid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+        rec.mark("batch_qse");
+        const int ggrid = (int)std::max<uint32_t>(1, std::min<uint32_t>(g.blocks, 2u * (uint32_t)c.sms));
+        if (launch_batch_general(a, g.F, ggrid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+        rec.mark("batch_general");
+    }
+    BatchScanArgs sa{};
+    sa.sizes = a.sizes;
+    sa.total_blocks = c.total_blocks;
+    sa.offsets = reinterpret_cast<unsigned long long*>(ws + L.offsets);
+    sa.tile_state = reinterpret_cast<unsigned long long*>(ws + L.states);
+    sa.tile_counter = ctrl + 16;
+    sa.status = ctrl + 17;
+    if (launch_batch_scan(sa, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    rec.mark("batch_scan");
+    BatchCompactArgs ca{};
+    ca.chunks = dev.chunks;
+    ca.nchunks = c.count();
+    ca.block_end = dev.block_end;
+    ca.total_blocks = c.total_blocks;
+    ca.temp = a.temp;
+    ca.offsets = sa.offsets;
+    ca.rparams = a.rparams;
+    ca.ready = a.ready;
+    ca.out_sizes = reinterpret_cast<unsigned long long*>(d_out_sizes ? (void*)d_out_sizes : (void*)(ws + L.out_sizes));
+    ca.chunk_status = status;
+    const uint64_t warps = (uint64_t)c.total_blocks + c.count();
+    const uint64_t want = (warps + kCompactWarps - 1) / kCompactWarps;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)cfg.compact_ctas * c.sms, want));
+    if (launch_batch_compact(ca, grid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    rec.mark("batch_compact");
+    return GPZ_OK;
+}
+
+}  // namespace host
+}  // namespace gpz

@@ -44,6 +44,24 @@ class gpz_batch_config(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class gpz_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("lanes", C.c_uint32), ("max_batch", C.c_uint32),
+                ("max_batch_bytes", C.c_uint64), ("lane_bytes", C.c_uint64)]
+
+
+class gpz_request_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("kind", C.c_int), ("status", C.c_int), ("out", C.c_void_p),
+                ("out_bytes", C.c_uint64), ("field_stride", C.c_uint64), ("in_bytes", C.c_uint64),
+                ("t_submit_ns", C.c_uint64), ("t_start_ns", C.c_uint64), ("t_done_ns", C.c_uint64),
+                ("batch", C.c_uint32), ("batch_size", C.c_uint32)]
+
+
+class gpz_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("in_bytes", C.c_uint64), ("arena_peak", C.c_uint64), ("arena_in_use", C.c_uint64),
+                ("queued", C.c_uint64)]
+
+
 class GpzError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -100,6 +118,23 @@ def _load():
     L.gpz_batch_tune.restype = C.c_int
     L.gpz_batch_launches.argtypes = [vp]
     L.gpz_batch_launches.restype = C.c_uint32
+    # serving engine (include/gpz_serve.h)
+    L.gpz_server_create.argtypes = [P(gpz_server_config), P(gpz_server_config), P(vp)]
+    L.gpz_server_create.restype = C.c_int
+    L.gpz_server_submit_compress.argtypes = [vp, P(vp), u64, P(gpz_params), P(u64)]
+    L.gpz_server_submit_compress.restype = C.c_int
+    L.gpz_server_submit_decompress.argtypes = [vp, vp, u64, C.c_int, u64, P(u64)]
+    L.gpz_server_submit_decompress.restype = C.c_int
+    L.gpz_server_poll.argtypes = [vp, P(gpz_request_result), C.c_int, C.c_int]
+    L.gpz_server_poll.restype = C.c_int
+    L.gpz_server_release.argtypes = [vp, u64]
+    L.gpz_server_release.restype = C.c_int
+    L.gpz_server_stats_get.argtypes = [vp, P(gpz_server_stats)]
+    L.gpz_server_stats_get.restype = C.c_int
+    L.gpz_server_now_ns.argtypes = [vp]
+    L.gpz_server_now_ns.restype = u64
+    L.gpz_server_destroy.argtypes = [vp]
+    L.gpz_server_destroy.restype = None
     return L
 
 
@@ -452,6 +487,100 @@ class BatchDecompressor:
         if self.plan:
             gpz_batch_destroy(self.plan)
             self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A view of device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+
+def device_bytes(ptr, nbytes, device=None):
+    """A uint8 CUDA tensor viewing nbytes of device memory at ptr (no copy)."""
+    if nbytes == 0:
+        return torch.empty(0, dtype=torch.uint8, device=device or "cuda")
+    return torch.as_tensor(_DeviceArray(ptr, nbytes), device=device or "cuda")
+
+
+class Server:
+    """The serving engine (include/gpz_serve.h): submit compress / decompress
+    requests, poll results, release their memory.  Keeps the inputs of each
+    request alive until its result is polled."""
+
+    def __init__(self, budget_bytes, lanes=2, max_batch=64, max_batch_bytes=0, lane_bytes=0):
+        cfg = gpz_server_config(budget_bytes, lanes, max_batch, max_batch_bytes, lane_bytes)
+        used = gpz_server_config()
+        h = C.c_void_p()
+        st = lib.gpz_server_create(C.byref(cfg), C.byref(used), C.byref(h))
+        if st != OK:
+            raise GpzError(st, "gpz_server_create")
+        self.handle, self.config = h, used
+        self._inputs = {}
+        self._buf = (gpz_request_result * 256)()
+
+    def submit_compress(self, fields, params):
+        fields = _fields_list(fields)
+        n = fields[0].numel() if fields else 0
+        rid = C.c_uint64()
+        st = lib.gpz_server_submit_compress(self.handle, _ptr_array(fields), n, C.byref(params), C.byref(rid))
+        if st != OK:
+            raise GpzError(st, "gpz_server_submit_compress")
+        self._inputs[rid.value] = fields
+        return rid.value
+
+    def submit_decompress(self, stream_buf, size, n_fields, n):
+        rid = C.c_uint64()
+        st = lib.gpz_server_submit_decompress(self.handle, stream_buf.data_ptr(), size, n_fields, n, C.byref(rid))
+        if st != OK:
+            raise GpzError(st, "gpz_server_submit_decompress")
+        self._inputs[rid.value] = stream_buf
+        return rid.value
+
+    def poll(self, max_results=256, timeout_ms=100):
+        """Completed results as dicts (oldest first); their outputs stay valid until release()."""
+        k = lib.gpz_server_poll(self.handle, self._buf, min(max_results, len(self._buf)), timeout_ms)
+        out = []
+        for i in range(k):
+            r = self._buf[i]
+            self._inputs.pop(r.id, None)
+            out.append({name: getattr(r, name) for name, _ in gpz_request_result._fields_})
+        return out
+
+    def stream_of(self, result):
+        """A polled compress result's stream as a CUDA uint8 view (valid until release)."""
+        return device_bytes(result["out"], result["out_bytes"])
+
+    def fields_of(self, result, n_fields, n):
+        """Decompressed fields of a polled result as a [F, n] float32 CUDA tensor (a copy)."""
+        stride = result["field_stride"]
+        raw = device_bytes(result["out"], stride * n_fields)
+        return torch.stack([raw[f * stride:f * stride + 4 * n].view(torch.float32) for f in range(n_fields)])
+
+    def release(self, rid):
+        st = lib.gpz_server_release(self.handle, rid)
+        if st != OK:
+            raise GpzError(st, "gpz_server_release")
+
+    def stats(self):
+        s = gpz_server_stats()
+        lib.gpz_server_stats_get(self.handle, C.byref(s))
+        return {name: int(getattr(s, name)) for name, _ in gpz_server_stats._fields_}
+
+    def now_ns(self):
+        return int(lib.gpz_server_now_ns(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib.gpz_server_destroy(self.handle)
+            self.handle = None
+            self._inputs.clear()
 
     def __del__(self):
         try:

@@ -1,6 +1,6 @@
-"""The C ABI library loads and exports every entry point include/gpz.h and
-include/gpz_batch.h declare; host-side entry points behave without touching a
-GPU."""
+"""The C ABI library loads and exports every entry point include/gpz.h,
+include/gpz_batch.h and include/gpz_serve.h declare; host-side entry points
+behave without touching a GPU."""
 import ctypes as C
 import os
 import re
@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("gpz.h", "gpz_batch.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("gpz.h", "gpz_batch.h", "gpz_serve.h")]
 
 
 @pytest.fixture(scope="module")
@@ -108,17 +108,22 @@ def test_argument_errors_need_no_device(gpz):
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
 def test_batch_struct_layout_matches_the_header(gpz, tmp_path):
-    """The binding's ctypes descriptors have the header's sizes and offsets."""
+    """The binding's ctypes structures have the headers' sizes and offsets."""
     src = tmp_path / "sz.c"
     src.write_text("""
 #include <stdio.h>
 #include <stddef.h>
 #include "gpz_batch.h"
+#include "gpz_serve.h"
 int main(void) {
-    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gpz_compress_chunk), offsetof(gpz_compress_chunk, n),
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu ", sizeof(gpz_compress_chunk), offsetof(gpz_compress_chunk, n),
            offsetof(gpz_compress_chunk, params), offsetof(gpz_compress_chunk, out),
            offsetof(gpz_compress_chunk, perm), sizeof(gpz_decompress_chunk),
            offsetof(gpz_decompress_chunk, n_fields), offsetof(gpz_decompress_chunk, n), sizeof(gpz_batch_config));
+    printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gpz_server_config), offsetof(gpz_server_config, max_batch_bytes),
+           offsetof(gpz_server_config, lane_bytes),
+           sizeof(gpz_request_result), offsetof(gpz_request_result, out), offsetof(gpz_request_result, batch),
+           sizeof(gpz_server_stats));
     return 0;
 }
 """)
@@ -126,8 +131,11 @@ int main(void) {
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     cc, dc = gpz.gpz_compress_chunk, gpz.gpz_decompress_chunk
+    sc, rr = gpz.gpz_server_config, gpz.gpz_request_result
     want = [C.sizeof(cc), cc.n.offset, cc.params.offset, cc.out.offset, cc.perm.offset, C.sizeof(dc),
-            dc.n_fields.offset, dc.n.offset, C.sizeof(gpz.gpz_batch_config)]
+            dc.n_fields.offset, dc.n.offset, C.sizeof(gpz.gpz_batch_config),
+            C.sizeof(sc), sc.max_batch_bytes.offset, sc.lane_bytes.offset, C.sizeof(rr), rr.out.offset, rr.batch.offset,
+            C.sizeof(gpz.gpz_server_stats)]
     assert got == want
 
 
@@ -184,3 +192,25 @@ def test_batch_argument_errors_need_no_device(gpz):
     assert L.gpz_batch_get_config(None, C.byref(cfg)) == gpz.ERR_INVALID_ARG
     assert L.gpz_batch_tune(None, C.c_void_p(256), 1 << 20, None, 1, None, None, None) == gpz.ERR_INVALID_ARG
     L.gpz_batch_destroy(None)
+
+
+def test_server_argument_errors_need_no_device(gpz):
+    L = gpz.lib
+    h = C.c_void_p()
+    bad = [gpz.gpz_server_config(1 << 30, 0, 8, 0, 0), gpz.gpz_server_config(1 << 30, 9, 8, 0, 0),
+           gpz.gpz_server_config(1 << 30, 2, 0, 0, 0), gpz.gpz_server_config(1000, 2, 8, 0, 0)]
+    for cfg in bad:
+        assert L.gpz_server_create(C.byref(cfg), None, C.byref(h)) == gpz.ERR_INVALID_ARG
+        assert not h.value
+    assert L.gpz_server_create(None, None, C.byref(h)) == gpz.ERR_INVALID_ARG
+    rid = C.c_uint64()
+    p = gpz.make_params(3, 1e-3)
+    fields = (C.c_void_p * 3)(16, 32, 48)
+    assert L.gpz_server_submit_compress(None, fields, 10, C.byref(p), C.byref(rid)) == gpz.ERR_INVALID_ARG
+    assert L.gpz_server_submit_decompress(None, C.c_void_p(4096), 1024, 3, 10, C.byref(rid)) == gpz.ERR_INVALID_ARG
+    out = (gpz.gpz_request_result * 4)()
+    assert L.gpz_server_poll(None, out, 4, 0) == 0
+    assert L.gpz_server_release(None, 1) == gpz.ERR_INVALID_ARG
+    assert L.gpz_server_stats_get(None, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_server_now_ns(None) == 0
+    L.gpz_server_destroy(None)
