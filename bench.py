@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: requests per second")
-    ap.add_argument("--serve-arms", default="batched:2:64:0:64,plain:1:1:0:0",
+    ap.add_argument("--serve-arms", default="batched:2:64:256:64,plain:1:1:0:0",
                     help="served workload: name:lanes:max_batch:max_batch_MB:express_lane_MB, comma separated; "
                          "the first is reported as the served value, the one named plain as the comparison")
     ap.add_argument("--chunks", type=int, default=4096, help="batched workload: number of chunks")

@@ -125,12 +125,23 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 // block code (the block index is re-read from the slot where it is used).
 struct LoopState {
     uint32_t q, stop;      // current item, end of the claimed run
+    uint32_t seen;         // the block counter as of this CTA's last claim
     uint32_t rcur, bcur;   // group-relative chunk cursors of range and block items
+    uint32_t cbase, cend;  // global blocks [cbase, cend) of chunk bcur
     uint32_t loaded, ok;   // chunk whose arguments are in A, and whether its constants arrived
     uint32_t kind, c;      // 0: range item, 1: block; its chunk
     uint32_t local;        // range item within its chunk
     uint32_t slot[2];      // block within its chunk, global block id
 };
+
+// Blocks per claim: the configured run while plenty of blocks are left, then
+// smaller runs so that the CTAs finish together (guided self-scheduling on a
+// slightly stale view of the counter).
+__device__ __forceinline__ uint32_t claim_size(uint32_t claim, uint32_t total, uint32_t seen) {
+    const uint32_t left = total > seen ? total - seen : 0u;
+    const uint32_t k = left / (2u * gridDim.x);
+    return k < 1u ? 1u : (k < claim ? k : claim);
+}
 
 template <int F>
 __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCompressArgs g) {
@@ -141,8 +152,9 @@ __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCo
     __shared__ LoopState L;
     const int t = threadIdx.x;
     if (t == 0) {
-        L.q = L.stop = 0u;
+        L.q = L.stop = L.seen = 0u;
         L.rcur = L.bcur = 0u;
+        L.cbase = L.cend = 0u;
         L.loaded = 0xffffffffu;
         L.ok = 0u;
         L.kind = 0u;
@@ -158,9 +170,12 @@ __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCo
                     L.stop = b0 + 1u;
                 } else {
                     L.kind = 1u;
-                    b0 = g.range_items + atomicAdd(g.ticket, g.claim);
+                    const uint32_t k = claim_size(g.claim, g.total_blocks, L.seen);
+                    const uint32_t got = atomicAdd(g.ticket, k);
+                    L.seen = got + k;
+                    b0 = g.range_items + got;
                     L.q = b0;
-                    L.stop = total - min(b0, total) < g.claim ? total : b0 + g.claim;
+                    L.stop = total - min(b0, total) < k ? total : b0 + k;
                 }
             }
             const uint32_t q = L.q;
@@ -173,11 +188,15 @@ __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCo
                 L.local = r - g.chunks[g.first + rc].range_base;
             } else if (q < total) {
                 const uint32_t gb = g.block_first + (q - g.range_items);
-                const uint32_t bc = find_chunk(g.block_end + g.first, g.nchunks, gb, L.bcur);
-                L.bcur = bc;
+                if (gb < L.cbase || gb >= L.cend) {  // another chunk: search (usually one probe)
+                    const uint32_t bc = find_chunk(g.block_end + g.first, g.nchunks, gb, L.bcur);
+                    L.bcur = bc;
+                    L.cend = __ldg(g.block_end + g.first + bc);
+                    L.cbase = g.chunks[g.first + bc].block_base;
+                }
                 L.kind = 1u;
-                L.c = g.first + bc;
-                L.slot[0] = gb - g.chunks[g.first + bc].block_base;
+                L.c = g.first + L.bcur;
+                L.slot[0] = gb - L.cbase;
                 L.slot[1] = gb;
             }
         }

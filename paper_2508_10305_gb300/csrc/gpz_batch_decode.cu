@@ -12,7 +12,10 @@ namespace gpz {
 // item between barriers, so that no register stays live across the inlined
 // block code (the block index is re-read from the slot where it is used).
 struct DecLoopState {
-    uint32_t q, stop, cur, loaded, b;
+    uint32_t q, stop, seen;  // current block, end of the claimed run, the counter as of the last claim
+    uint32_t cur, loaded;    // chunk of the current block, chunk whose arguments are in A
+    uint32_t cbase, cend;    // global blocks [cbase, cend) of chunk cur
+    uint32_t b;              // block within its chunk
 };
 
 template <int F>
@@ -22,21 +25,30 @@ __global__ void __launch_bounds__(kDecThreads, 5) gpz_batch_decompress_kernel(Ba
     __shared__ DecLoopState L;
     const int t = threadIdx.x;
     if (t == 0) {
-        L.q = L.stop = L.cur = 0u;
+        L.q = L.stop = L.seen = L.cur = 0u;
+        L.cbase = L.cend = 0u;
         L.loaded = 0xffffffffu;
     }
     for (;;) {
         if (t == 0) {
-            if (L.q >= L.stop) {  // claim the next run of blocks
-                const uint32_t b0 = atomicAdd(g.ticket, g.claim);
+            if (L.q >= L.stop) {  // claim the next run of blocks (shorter runs near the end)
+                const uint32_t left = g.total_blocks > L.seen ? g.total_blocks - L.seen : 0u;
+                uint32_t k = left / (2u * gridDim.x);
+                k = k < 1u ? 1u : (k < g.claim ? k : g.claim);
+                const uint32_t b0 = atomicAdd(g.ticket, k);
+                L.seen = b0 + k;
                 L.q = b0;
-                L.stop = g.total_blocks - min(b0, g.total_blocks) < g.claim ? g.total_blocks : b0 + g.claim;
+                L.stop = g.total_blocks - min(b0, g.total_blocks) < k ? g.total_blocks : b0 + k;
             }
             if (L.q < g.total_blocks) {
                 const uint32_t gb = g.block_first + L.q;
-                const uint32_t cur = find_chunk(g.block_end + g.first, g.nchunks, gb, L.cur);
-                L.cur = cur;
-                L.b = gb - g.chunks[g.first + cur].block_base;
+                if (gb < L.cbase || gb >= L.cend) {  // another chunk: search (usually one probe)
+                    const uint32_t cur = find_chunk(g.block_end + g.first, g.nchunks, gb, L.cur);
+                    L.cur = cur;
+                    L.cend = __ldg(g.block_end + g.first + cur);
+                    L.cbase = g.chunks[g.first + cur].block_base;
+                }
+                L.b = gb - L.cbase;
             }
         }
         __syncthreads();
