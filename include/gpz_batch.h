@@ -1,6 +1,6 @@
 /*
  * gpz_batch.h -- batched compression and decompression in libgpz: many
- * independent particle arrays ("chunks") in a few persistent launches.
+ * independent particle arrays ("chunks") in a few launches.
  *
  * The paper compresses one array per call (Sections 3.2 and 4); it has no
  * batched form.  This interface is the system form of the same method for
@@ -8,16 +8,18 @@
  * tiles): every chunk's stream is byte-for-byte the one gpz_compress produces
  * for it alone, and every chunk's decompressed values are the ones
  * gpz_decompress produces alone.  Only the scheduling differs:
- *   - the chunks of one field count F form a group, served by ONE persistent
- *     launch (one CTA per SM slot) that first computes the value ranges of
- *     the group's relative-bound chunks and then runs the fused
- *     quantise/sort/encode stage (Sections 4.1-4.3) over every block of every
- *     chunk, CTAs claiming work items from an atomic ticket counter;
+ *   - the chunks of one field count F form a group; per group, ONE launch
+ *     computes the value ranges of the relative-bound chunks (one CTA per
+ *     slice of a field) and ONE launch runs the fused quantise/sort/encode
+ *     stage (Sections 4.1-4.3) over every block of every chunk, one CTA per
+ *     block, each finding its chunk through a block-to-chunk map;
  *   - one look-back prefix sum over the blocks of all chunks and one
  *     compaction pass (Section 4.4) place every block in its chunk's stream
  *     and write every chunk's header and block table;
+ *   - decompression is one launch per group, one CTA per block;
  *   - a plan can be captured once into a CUDA graph and replayed, and its
- *     launch shape (work-item sizes, CTAs per SM) can be tuned by timing.
+ *     launch shape (range slice, compaction and general-path grids) can be
+ *     tuned by timing.
  *
  * Conventions are those of gpz.h (device pointers d_*, caller-owned buffers,
  * stream-ordered work, no aborts).  A plan owns a small device copy of its
@@ -55,17 +57,16 @@ typedef struct {
 } gpz_decompress_chunk;
 
 /* Launch shape of a plan.  A zero field takes the default.
- *   ctas_per_sm:   CTAs per SM of the persistent launches (compression 1..4,
- *                  decompression 1..5; clamped to what fits).  Default: the most that fit.
- *   claim:         blocks per ticket, 1..64 (range slices are claimed one at a time).  Default 4.
- *   range_slice:   values per range work item (relative bounds), a multiple
- *                  of 1024 in 1024..2^24.  Default 65536.
- *   compact_ctas:  CTAs of the compaction launch, 8 warps each, per SM, 1..32.  Default 16. */
+ *   range_slice:   values per range work item (relative bounds: one CTA per
+ *                  slice of a field), a multiple of 1024 in 1024..2^24.  Default 65536.
+ *   compact_ctas:  CTAs of the compaction launch, 8 warps each, per SM, 1..32.  Default 16.
+ *   general_ctas:  CTAs per SM walking the list of general-path blocks, 1..4.  Default 2.
+ *   reserved:      0. */
 typedef struct {
-    uint32_t ctas_per_sm;
-    uint32_t claim;
     uint32_t range_slice;
     uint32_t compact_ctas;
+    uint32_t general_ctas;
+    uint32_t reserved;
 } gpz_batch_config;
 
 typedef struct gpz_batch gpz_batch; /* opaque plan */
@@ -116,7 +117,7 @@ gpz_status gpz_batch_sync_status(const gpz_batch* plan, const void* d_ws, uint32
 
 /* Time each candidate launch shape on this plan's own chunks (reps timed
  * runs each, after one untimed run, CUDA events on `stream`) and keep the
- * fastest.  Runs the plan about 20 * (reps + 1) times; the outputs are
+ * fastest.  Runs the plan up to 10 * (reps + 1) times; the outputs are
  * rewritten each time with the same values.  Writes the chosen shape and its
  * mean time per run (ms) when the pointers are not NULL. */
 gpz_status gpz_batch_tune(gpz_batch* plan, void* d_ws, uint64_t ws_size, uint64_t* d_out_sizes, int reps,

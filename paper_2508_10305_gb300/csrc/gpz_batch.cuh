@@ -1,20 +1,19 @@
 // gpz_batch.cuh -- device-side descriptors and argument blocks of the batched
 // path: many independent arrays ("chunks") compressed or decompressed by a
-// few persistent launches, each chunk producing exactly the stream (or the
-// values) a call of its own would produce.
+// few launches, each chunk producing exactly the stream (or the values) a
+// call of its own would produce.
 //
-// The chunks of one field count F form a group, served by one persistent
-// launch of the kernel compiled for that F.  Its work is claimed from the
-// group's atomic ticket counters over a flattened item list, ordered by
-// chunk: in compression the range-pass slices of the group's relative-bound
-// chunks come first (claimed one at a time from their own counter), then
-// every block of every chunk; in decompression every block of every chunk.
-// A CTA claims `claim` consecutive blocks per ticket and finds each item's
-// chunk by a forward search from the chunk of its previous item (tickets only
-// grow).  A block of a relative-bound chunk waits for that chunk's constants;
-// those come from range items claimed before any block (by CTAs that are
-// already running and never wait themselves), so the wait always ends (it is
-// bounded anyway).
+// The chunks of one field count F form a group, served by the kernels compiled
+// for that F.  Every block of every chunk has a global index (the chunks of
+// all groups one after another); a map kernel writes, for every global block,
+// the plan position of its chunk, so that a CTA finds its chunk with one load.
+// Compression of a group: one launch of range items (relative-bound chunks:
+// one slice of one field each; the last slice of a chunk to finish writes the
+// chunk's constants), one launch with one CTA per block (the fused
+// quantise/sort/encode of the single-array path), and the rare general-path
+// blocks; then one 64-bit look-back scan over all blocks and one compaction
+// pass for all chunks.  Decompression of a group: one launch with one CTA per
+// block.
 #pragma once
 
 #include "gpz_internal.cuh"
@@ -41,30 +40,32 @@ struct BatchChunk {
     int bulk_ok;                     // every field pointer 16-byte aligned
 };
 
-// One launch covers the chunks of one field count F (a "group"): chunk
-// indices c below are positions in the plan's chunk array, which holds the
-// groups one after another; the group is chunks [first, first + nchunks).
+// chunks[] holds the groups one after another; a group is chunks
+// [first, first + nchunks).
 struct BatchCompressArgs {
     const BatchChunk* chunks;    // the plan's chunk array
     uint32_t first, nchunks;     // the group
     const uint32_t* range_end;   // [all chunks] inclusive prefix of range items (plan order)
-    const uint32_t* block_end;   // [all chunks] inclusive prefix of blocks (plan order)
+    const uint32_t* block_map;   // [all blocks] plan position of each block's chunk
     uint32_t range_first;        // the group's first range item
     uint32_t range_items;        // the group's range items
     uint32_t block_first;        // the group's first block
     uint32_t total_blocks;       // the group's blocks
-    uint32_t slice;              // elements per range item
-    uint32_t claim;              // items per ticket
-    uint32_t* ticket;            // the group's block counter (ticket[24]: its range-item counter), zeroed
+    uint32_t slice;              // values per range item
     uint32_t* rkeys;             // [chunks][kMaxFields][2]: ~order key of the min, order key of the max; zeroed
     uint32_t* rdone;             // [chunks] range items finished; zeroed
-    uint32_t* ready;             // [chunks] 1 once the chunk's relative constants are written; zeroed
     FieldParams* rparams;        // [chunks][kMaxFields]
     uint32_t* temp;
     uint32_t* sizes;             // [all blocks] words per block
     uint32_t* general_list;      // [the group's blocks] global block ids left to the general kernel
     uint32_t* general_count;     // the group's count, zeroed
     uint32_t* chunk_status;      // [chunks] zeroed
+};
+
+struct BatchMapArgs {
+    const BatchChunk* chunks;
+    uint32_t nchunks;
+    uint32_t* block_map;         // [all blocks]
 };
 
 struct BatchScanArgs {
@@ -79,24 +80,20 @@ struct BatchScanArgs {
 struct BatchCompactArgs {
     const BatchChunk* chunks;
     uint32_t nchunks;
-    const uint32_t* block_end;
+    const uint32_t* block_map;
     uint32_t total_blocks;
     const uint32_t* temp;
     const unsigned long long* offsets;
     const FieldParams* rparams;
-    const uint32_t* ready;
     unsigned long long* out_sizes;  // [nchunks] stream bytes, in descriptor order (BatchChunk::index)
     uint32_t* chunk_status;
 };
 
 struct BatchDecompressArgs {
     const BatchChunk* chunks;    // the plan's chunk array
-    uint32_t first, nchunks;     // the group (one field count)
-    const uint32_t* block_end;   // [all chunks] inclusive prefix of blocks
+    const uint32_t* block_map;   // [all blocks]
     uint32_t block_first;        // the group's first block
     uint32_t total_blocks;       // the group's blocks
-    uint32_t claim;
-    uint32_t* ticket;            // the group's block counter (ticket[24]: its range-item counter), zeroed
     uint32_t* chunk_status;      // [chunks] zeroed
 };
 
@@ -105,39 +102,28 @@ __host__ __device__ constexpr uint32_t batch_slot_words(int F) {
     return (1u + (uint32_t)F * (uint32_t)kBlock + 3u) & ~3u;
 }
 
-// Smallest c >= lo with end[c] > item, for a non-decreasing end[0..nchunks)
-// whose last entry exceeds item (so the answer exists).  Galloping from lo, then a
-// binary search; at most 2 * 32 probes.
-__device__ __forceinline__ uint32_t find_chunk(const uint32_t* end, uint32_t nchunks, uint32_t item, uint32_t lo) {
-    if (__ldg(end + lo) > item) return lo;
-    uint32_t below = lo, step = 1, above = nchunks - 1;  // end[below] <= item < end[above]
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t probe = below + step;
-        if (probe >= nchunks - 1) break;
-        if (__ldg(end + probe) > item) {
-            above = probe;
-            break;
-        }
-        below = probe;
-        step <<= 1;
-    }
-    for (int k = 0; k < 32 && above - below > 1; ++k) {
-        const uint32_t mid = below + ((above - below) >> 1);
+// Smallest c in [0, n) with end[c] > item, for a non-decreasing end[] whose
+// last entry exceeds item: a binary search, at most 32 probes.
+__device__ __forceinline__ uint32_t search_chunk(const uint32_t* end, uint32_t n, uint32_t item) {
+    uint32_t lo = 0, hi = n - 1;
+    for (int k = 0; k < 32 && lo < hi; ++k) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
         if (__ldg(end + mid) > item)
-            above = mid;
+            hi = mid;
         else
-            below = mid;
+            lo = mid + 1;
     }
-    return above;
+    return lo;
 }
 
 // Launch wrappers (gpz_batch_compress.cu, gpz_batch_decode.cu).
-cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, int grid, cudaStream_t s);
+cudaError_t launch_batch_map(const BatchMapArgs& a, cudaStream_t s);
+cudaError_t launch_batch_range(const BatchCompressArgs& a, cudaStream_t s);
+cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, cudaStream_t s);
 cudaError_t launch_batch_general(const BatchCompressArgs& a, int F, int grid, cudaStream_t s);
 cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s);
 cudaError_t launch_batch_compact(const BatchCompactArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_batch_decompress(const BatchDecompressArgs& a, int F, int grid, cudaStream_t s);
-int batch_compress_max_ctas_per_sm(int F);   // 0 on error
-int batch_decompress_max_ctas_per_sm(int F);
+cudaError_t launch_batch_decompress(const BatchDecompressArgs& a, int F, cudaStream_t s);
+bool batch_prepare_kernels(int F);  // shared-memory attributes of the compression kernels; false on error
 
 }  // namespace gpz

@@ -29,8 +29,7 @@ namespace {
 constexpr uint64_t kAlign = 256;
 
 bool same_cfg(const gpz_batch_config& a, const gpz_batch_config& b) {
-    return a.ctas_per_sm == b.ctas_per_sm && a.claim == b.claim && a.range_slice == b.range_slice &&
-           a.compact_ctas == b.compact_ctas;
+    return a.range_slice == b.range_slice && a.compact_ctas == b.compact_ctas && a.general_ctas == b.general_ctas;
 }
 
 void drop_graph(gpz_batch* p) {
@@ -217,17 +216,20 @@ gpz_status gpz_batch_tune(gpz_batch* p, void* d_ws, uint64_t ws_size, uint64_t* 
     if (st != GPZ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const BatchCore& c = p->core;
-    int fit = 5;
-    for (const auto& g : c.groups) fit = std::min(fit, g.max_ctas);
-    std::vector<gpz_batch_config> cand;
-    for (uint32_t ctas = (uint32_t)fit; ctas >= 1 && ctas + 2 > (uint32_t)fit; --ctas)
-        for (uint32_t cl : {1u, 2u, 4u, 8u, 16u}) {
-            if (c.kind == 0 && c.any_rel) {
-                for (uint32_t sl : {16384u, 65536u, 262144u}) cand.push_back({ctas, cl, sl, 16});
-            } else {
-                cand.push_back({ctas, cl, 65536, 16});
-            }
-        }
+    // one parameter at a time, the others at their best so far: the range
+    // slice (relative bounds only), then the compaction grid
+    std::vector<std::vector<gpz_batch_config>> stages;
+    if (c.kind == 0 && c.any_rel) {
+        std::vector<gpz_batch_config> v;
+        for (uint32_t sl : {16384u, 65536u, 262144u, 1048576u}) v.push_back({sl, 0, 0, 0});
+        stages.push_back(v);
+    }
+    if (c.kind == 0) {
+        std::vector<gpz_batch_config> v;
+        for (uint32_t cc : {4u, 8u, 16u, 32u}) v.push_back({0, cc, 0, 0});
+        stages.push_back(v);
+    }
+    if (stages.empty()) stages.push_back({gpz_batch_config{}});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return GPZ_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -250,20 +252,12 @@ gpz_status gpz_batch_tune(gpz_batch* p, void* d_ws, uint64_t ws_size, uint64_t* 
     };
     gpz_batch_config best = c.cfg;
     float best_ms = 3.0e38f;
-    for (const auto& cfg : cand) {
-        float ms = 0.0f;
-        if ((st = time_cfg(cfg, &ms)) != GPZ_OK) break;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = p->core.cfg;
-        }
-    }
-    if (st == GPZ_OK && c.kind == 0) {
-        // then the compaction grid, with the rest fixed
+    for (const auto& stage : stages) {
         const gpz_batch_config base = best;
-        for (uint32_t cc : {4u, 8u, 32u}) {
+        for (const auto& cand : stage) {
             gpz_batch_config cfg = base;
-            cfg.compact_ctas = cc;
+            if (cand.range_slice) cfg.range_slice = cand.range_slice;
+            if (cand.compact_ctas) cfg.compact_ctas = cand.compact_ctas;
             float ms = 0.0f;
             if ((st = time_cfg(cfg, &ms)) != GPZ_OK) break;
             if (ms < best_ms) {
@@ -271,6 +265,7 @@ gpz_status gpz_batch_tune(gpz_batch* p, void* d_ws, uint64_t ws_size, uint64_t* 
                 best = p->core.cfg;
             }
         }
+        if (st != GPZ_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

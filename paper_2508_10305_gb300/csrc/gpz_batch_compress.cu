@@ -1,10 +1,10 @@
-// gpz_batch_compress.cu -- batched compression: every chunk of a batch in one
-// persistent launch (range pass of the relative-bound chunks + the fused
-// quantise/sort/encode of every block, Sections 4.1-4.3), then the rare
-// general-path blocks, one 64-bit look-back scan over all blocks and one
-// compaction pass that also writes every chunk's header and block table
-// (Section 4.4, steps 2 and 3).  Each chunk's stream is the one a call of its
-// own produces: the per-block code is the single-array code.
+// gpz_batch_compress.cu -- batched compression: for each group of chunks of
+// one field count, one launch of range items (relative bounds), one launch
+// with one CTA per block running the single-array fused quantise/sort/encode
+// code (Sections 4.1-4.3), and the rare general-path blocks; then one 64-bit
+// look-back scan over all blocks and one compaction pass that also writes
+// every chunk's header and block table (Section 4.4, steps 2 and 3).  Each
+// chunk's stream is the one a call of its own produces.
 #include "gpz_batch.cuh"
 #include "gpz_qse_block.cuh"
 
@@ -12,10 +12,12 @@ namespace gpz {
 
 namespace {
 
-// Per-chunk argument block of the per-block code, built in shared memory.
-// The constants are copied in (d_params stays null), read from L2: a
-// relative bound's constants were written during this launch.
-__device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint32_t c, QseArgs& A) {
+// Per-chunk argument block of the per-block code, built in shared memory by
+// the CTA's threads in parallel (d_params stays null: the constants are
+// copied in, read from L2).  Thread 64 also stores the block's index within
+// its chunk in *slot.
+__device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint32_t c, uint32_t gb, QseArgs& A,
+                                                uint32_t* slot) {
     const int t = threadIdx.x;
     const BatchChunk* ch = g.chunks + c;
     if (t < kMaxFields) A.fields[t] = ch->in[t];
@@ -26,6 +28,9 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         reinterpret_cast<uint32_t*>(A.params + f)[k] = __ldcg(src + k);
     }
     if (t == 64) {
+        const uint32_t base = ch->block_base;
+        slot[0] = gb - base;
+        slot[1] = gb;
         A.n = ch->n;
         A.nblocks = ch->nblocks;
         A.F = ch->F;
@@ -34,7 +39,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.d_params = nullptr;
         A.temp = g.temp + ch->temp_base;
         A.slot_words = batch_slot_words(ch->F);
-        A.sizes = g.sizes + ch->block_base;
+        A.sizes = g.sizes + base;
         A.perm = ch->perm;
         A.status = g.chunk_status + c;
         A.general_list = g.general_list;
@@ -44,7 +49,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
 
 // One range item: minimum and maximum of one slice of one field of a
 // relative-bound chunk, merged into the chunk's order keys; the CTA that
-// finishes the chunk's last item writes its constants and raises its flag.
+// finishes the chunk's last item writes the chunk's constants.
 __device__ __forceinline__ void range_item(const BatchCompressArgs& g, uint32_t c, uint32_t local, float2* red) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const BatchChunk* ch = g.chunks + c;
@@ -106,140 +111,43 @@ __device__ __forceinline__ void range_item(const BatchCompressArgs& g, uint32_t 
                 const float fhi = kmax ? from_order_key(kmax) : -INFINITY;
                 g.rparams[(size_t)c * kMaxFields + ff] = range_params(flo, fhi, ch->rel[ff]);
             }
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(g.ready + c), "r"(1u) : "memory");
         }
     }
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 }  // namespace
 
-// The loop state lives in shared memory: thread 0 claims and decodes each
-// item between barriers, so that no register stays live across the inlined
-// block code (the block index is re-read from the slot where it is used).
-struct LoopState {
-    uint32_t q, stop;      // current item, end of the claimed run
-    uint32_t seen;         // the block counter as of this CTA's last claim
-    uint32_t rcur, bcur;   // group-relative chunk cursors of range and block items
-    uint32_t cbase, cend;  // global blocks [cbase, cend) of chunk bcur
-    uint32_t loaded, ok;   // chunk whose arguments are in A, and whether its constants arrived
-    uint32_t kind, c;      // 0: range item, 1: block; its chunk
-    uint32_t local;        // range item within its chunk
-    uint32_t slot[2];      // block within its chunk, global block id
-};
-
-// Blocks per claim: the configured run while plenty of blocks are left, then
-// smaller runs so that the CTAs finish together (guided self-scheduling on a
-// slightly stale view of the counter).
-__device__ __forceinline__ uint32_t claim_size(uint32_t claim, uint32_t total, uint32_t seen) {
-    const uint32_t left = total > seen ? total - seen : 0u;
-    const uint32_t k = left / (2u * gridDim.x);
-    return k < 1u ? 1u : (k < claim ? k : claim);
+// The chunk of every global block (one CTA per chunk).
+__global__ void __launch_bounds__(256) gpz_batch_map_kernel(BatchMapArgs a) {
+    const BatchChunk* ch = a.chunks + blockIdx.x;
+    const uint32_t base = ch->block_base, nb = ch->nblocks;
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) a.block_map[base + j] = blockIdx.x;
 }
 
+// One CTA per range item of the group.
+__global__ void __launch_bounds__(kThreads) gpz_batch_range_kernel(BatchCompressArgs g) {
+    __shared__ float2 red[kWarps];
+    const uint32_t r = g.range_first + blockIdx.x;
+    const uint32_t c = g.first + search_chunk(g.range_end + g.first, g.nchunks, r);
+    range_item(g, c, r - g.chunks[c].range_base, red);
+}
+
+// One CTA per block of the group: the single-array fused kernel's code, with
+// the chunk's arguments in shared memory.
 template <int F>
 __global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCompressArgs g) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     __shared__ QseArgs A;
-    __shared__ float2 red[kWarps];
-    __shared__ LoopState L;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        L.q = L.stop = L.seen = 0u;
-        L.rcur = L.bcur = 0u;
-        L.cbase = L.cend = 0u;
-        L.loaded = 0xffffffffu;
-        L.ok = 0u;
-        L.kind = 0u;
-    }
-    for (;;) {
-        if (t == 0) {
-            const uint32_t total = g.range_items + g.total_blocks;
-            if (L.q >= L.stop) {  // claim: range items one at a time, then runs of blocks
-                uint32_t b0 = g.range_items;
-                if (L.kind != 1u) b0 = atomicAdd(g.ticket + 24, 1u);
-                if (b0 < g.range_items) {
-                    L.q = b0;
-                    L.stop = b0 + 1u;
-                } else {
-                    L.kind = 1u;
-                    const uint32_t k = claim_size(g.claim, g.total_blocks, L.seen);
-                    const uint32_t got = atomicAdd(g.ticket, k);
-                    L.seen = got + k;
-                    b0 = g.range_items + got;
-                    L.q = b0;
-                    L.stop = total - min(b0, total) < k ? total : b0 + k;
-                }
-            }
-            const uint32_t q = L.q;
-            if (q < g.range_items) {
-                const uint32_t r = g.range_first + q;
-                const uint32_t rc = find_chunk(g.range_end + g.first, g.nchunks, r, L.rcur);
-                L.rcur = rc;
-                L.kind = 0u;
-                L.c = g.first + rc;
-                L.local = r - g.chunks[g.first + rc].range_base;
-            } else if (q < total) {
-                const uint32_t gb = g.block_first + (q - g.range_items);
-                if (gb < L.cbase || gb >= L.cend) {  // another chunk: search (usually one probe)
-                    const uint32_t bc = find_chunk(g.block_end + g.first, g.nchunks, gb, L.bcur);
-                    L.bcur = bc;
-                    L.cend = __ldg(g.block_end + g.first + bc);
-                    L.cbase = g.chunks[g.first + bc].block_base;
-                }
-                L.kind = 1u;
-                L.c = g.first + L.bcur;
-                L.slot[0] = gb - L.cbase;
-                L.slot[1] = gb;
-            }
-        }
-        __syncthreads();
-        if (L.q >= g.range_items + g.total_blocks) break;
-        if (L.kind == 0u) {
-            range_item(g, L.c, L.local, red);
-        } else {
-            const uint32_t c = L.c;
-            if (c != L.loaded) {
-                __syncthreads();  // every thread has read L.loaded
-                if (t == 0) {
-                    uint32_t ok = 1u;
-                    if (g.chunks[c].mode) {  // wait for the chunk's relative constants
-                        const long long t0 = clock64();
-                        while (ld_acquire_u32(g.ready + c) == 0u) {
-                            if (clock64() - t0 > (1ll << 31)) {
-                                set_status(g.chunk_status + c, kStTimeout);
-                                ok = 0u;
-                                break;
-                            }
-                            __nanosleep(64);
-                        }
-                    }
-                    L.ok = ok;
-                    L.loaded = c;
-                }
-                __syncthreads();
-                load_chunk_args(g, c, A);
-                __syncthreads();
-            }
-            const SlotBlock idx{L.slot};
-            if (!L.ok) {
-                if (t == 0) A.sizes[idx.b()] = 0u;  // the chunk is reported as timed out
-            } else if ((uint64_t)(idx.b() + 1) * kBlock <= A.n) {
-                qse_block_fast<F, true>(A, dsm, S, idx);
-            } else {
-                qse_block_fast<F, false>(A, dsm, S, idx);
-            }
-        }
-        __syncthreads();
-        if (t == 0) L.q = L.q + 1u;
-    }
+    __shared__ uint32_t slot[2];  // block within its chunk, global block id
+    const uint32_t gb = g.block_first + blockIdx.x;
+    load_chunk_args(g, __ldg(g.block_map + gb), gb, A, slot);
+    __syncthreads();
+    const SlotBlock idx{slot};
+    if ((uint64_t)(idx.b() + 1) * kBlock <= A.n)
+        qse_block_fast<F, true>(A, dsm, S, idx);
+    else
+        qse_block_fast<F, false>(A, dsm, S, idx);
 }
 
 // Blocks the fast path left to the general one (rare); the grid walks the
@@ -249,13 +157,13 @@ __global__ void __launch_bounds__(kThreads, 2) gpz_batch_general_kernel(BatchCom
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseShared S;
     __shared__ QseArgs A;
+    __shared__ uint32_t slot[2];
     const uint32_t count = *(volatile const uint32_t*)g.general_count;
     for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
         const uint32_t gb = __ldcg(g.general_list + i);
-        const uint32_t c = g.first + find_chunk(g.block_end + g.first, g.nchunks, gb, 0);
-        load_chunk_args(g, c, A);
+        load_chunk_args(g, __ldg(g.block_map + gb), gb, A, slot);
         __syncthreads();
-        const uint32_t b = gb - g.chunks[c].block_base;
+        const uint32_t b = slot[0];
         if ((uint64_t)(b + 1) * kBlock <= A.n)
             qse_block_general<F, true>(A, dsm, S, b);
         else
@@ -350,10 +258,9 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCompactWarps;
     const uint32_t items = a.total_blocks + a.nchunks;
-    uint32_t cur = 0;
     for (uint32_t q = blockIdx.x * kCompactWarps + warp; q < items; q += nwarps) {
         if (q < a.total_blocks) {
-            cur = find_chunk(a.block_end, a.nchunks, q, cur);
+            const uint32_t cur = __ldg(a.block_map + q);
             const BatchChunk* ch = a.chunks + cur;
             const uint32_t F = (uint32_t)ch->F, nb = ch->nblocks, b = q - ch->block_base;
             const uint64_t n = ch->n;
@@ -433,33 +340,27 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
 // ------------------------------------------------------------------ launches
 
 template <int F>
-int max_ctas_f() {
-    int n = 0;
-    if (cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)qse_fast_smem_bytes()) != cudaSuccess ||
-        cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(gpz_batch_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)qse_smem_bytes(F)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gpz_batch_compress_kernel<F>, kThreads,
-                                                      qse_fast_smem_bytes()) != cudaSuccess)
-        return 0;
-    return n;
+bool prepare_f() {
+    return cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)qse_fast_smem_bytes()) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)qse_smem_bytes(F)) == cudaSuccess;
 }
 
-// Also sets the kernels' shared-memory attributes: call once before launching.
-int batch_compress_max_ctas_per_sm(int F) {
+bool batch_prepare_kernels(int F) {
     switch (F) {
-        case 1: return max_ctas_f<1>();
-        case 2: return max_ctas_f<2>();
-        case 3: return max_ctas_f<3>();
-        case 4: return max_ctas_f<4>();
-        case 5: return max_ctas_f<5>();
-        case 6: return max_ctas_f<6>();
-        case 7: return max_ctas_f<7>();
-        case 8: return max_ctas_f<8>();
+        case 1: return prepare_f<1>();
+        case 2: return prepare_f<2>();
+        case 3: return prepare_f<3>();
+        case 4: return prepare_f<4>();
+        case 5: return prepare_f<5>();
+        case 6: return prepare_f<6>();
+        case 7: return prepare_f<7>();
+        case 8: return prepare_f<8>();
     }
-    return 0;
+    return false;
 }
 
 template <int F>
@@ -485,8 +386,18 @@ cudaError_t launch_group(const BatchCompressArgs& a, int F, int grid, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, int grid, cudaStream_t s) {
-    return launch_group(a, F, grid, s, false);
+cudaError_t launch_batch_map(const BatchMapArgs& a, cudaStream_t s) {
+    gpz_batch_map_kernel<<<a.nchunks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_range(const BatchCompressArgs& a, cudaStream_t s) {
+    gpz_batch_range_kernel<<<a.range_items, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, cudaStream_t s) {
+    return launch_group(a, F, (int)a.total_blocks, s, false);
 }
 
 cudaError_t launch_batch_general(const BatchCompressArgs& a, int F, int grid, cudaStream_t s) {

@@ -14,56 +14,49 @@ namespace host {
 namespace {
 
 constexpr uint64_t kAlign = 256;
-// block tickets[8], general counts[8] (at 8), scan tile counter (16), scan
-// status (17), range-item tickets[8] (24): one word each, per group
+// general-list counts[8] (one per group), scan tile counter (16), scan status (17)
 constexpr uint64_t kCtrlBytes = 256;
 constexpr uint32_t kMaxItems = 1u << 31;
 
 uint64_t ntiles_of(uint64_t blocks) { return (blocks + 1 + kScanTile - 1) / kScanTile; }
 
-// Occupancy of the persistent kernels per field count (also sets their
-// shared-memory attributes), looked up once per device.
+// The SM count, and the compression kernels' shared-memory attributes set
+// once per device and field count.
 constexpr int kMaxDevices = 64;
-std::mutex g_occ_mu;
-int g_occ[kMaxDevices][2][kMaxFields + 1] = {};
+std::mutex g_dev_mu;
+bool g_prepared[kMaxDevices][kMaxFields + 1] = {};
 int g_sms[kMaxDevices] = {};
 
-gpz_status device_info(int kind, int F, int* sms, int* ctas) {
+gpz_status device_info(int kind, int F, int* sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GPZ_ERR_CUDA;
-    std::lock_guard<std::mutex> g(g_occ_mu);
+    std::lock_guard<std::mutex> g(g_dev_mu);
     if (!g_sms[dev] && (cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
                         g_sms[dev] < 1)) {
         g_sms[dev] = 0;
         return GPZ_ERR_CUDA;
     }
-    int& o = g_occ[dev][kind][F];
-    if (!o) o = kind == 0 ? batch_compress_max_ctas_per_sm(F) : batch_decompress_max_ctas_per_sm(F);
-    if (o < 1) {
-        o = 0;
-        return GPZ_ERR_CUDA;
+    if (kind == 0 && !g_prepared[dev][F]) {
+        if (!batch_prepare_kernels(F)) return GPZ_ERR_CUDA;
+        g_prepared[dev][F] = true;
     }
     *sms = g_sms[dev];
-    *ctas = o;
     return GPZ_OK;
 }
 
-gpz_batch_config clamp_cfg(const BatchCore& c, gpz_batch_config cfg) {
-    int fit = 5;
-    for (const auto& g : c.groups) fit = std::min(fit, g.max_ctas);
-    if (fit < 1) fit = 1;
-    if (cfg.ctas_per_sm == 0 || cfg.ctas_per_sm > (uint32_t)fit) cfg.ctas_per_sm = (uint32_t)fit;
-    if (cfg.claim == 0) cfg.claim = 4;
-    cfg.claim = std::min<uint32_t>(cfg.claim, 64);
+gpz_batch_config clamp_cfg(gpz_batch_config cfg) {
     if (cfg.range_slice == 0) cfg.range_slice = 65536;
     cfg.range_slice = std::min<uint32_t>(std::max<uint32_t>(cfg.range_slice / 1024 * 1024, 1024), 1u << 24);
     if (cfg.compact_ctas == 0) cfg.compact_ctas = 16;
     cfg.compact_ctas = std::min<uint32_t>(cfg.compact_ctas, 32);
+    if (cfg.general_ctas == 0) cfg.general_ctas = 2;
+    cfg.general_ctas = std::min<uint32_t>(cfg.general_ctas, 4);
+    cfg.reserved = 0;
     return cfg;
 }
 
 // Range items of every relative-bound chunk for the current slice.  False
-// when the items do not fit the 31-bit ticket space.
+// when a launch's items would not fit a 31-bit grid.
 bool lay_out_range(BatchCore& c) {
     uint64_t r = 0;
     c.range_end.assign(c.count(), 0);
@@ -86,9 +79,8 @@ bool lay_out_range(BatchCore& c) {
     return r < kMaxItems;
 }
 
-uint64_t desc_offset(const BatchCore& c, int part) {  // 0 chunks, 1 range_end, 2 block_end
-    const uint64_t a = align_up(sizeof(BatchChunk) * c.count(), kAlign), b = align_up(4ull * c.count(), kAlign);
-    return part == 0 ? 0 : part == 1 ? a : a + b;
+uint64_t desc_offset(const BatchCore& c, int part) {  // 0 chunks, 1 range_end
+    return part == 0 ? 0 : align_up(sizeof(BatchChunk) * c.count(), kAlign);
 }
 
 }  // namespace
@@ -182,13 +174,11 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
     }
     c.total_blocks = (uint32_t)blocks;
     c.temp_words = temp;
-    c.block_end.resize(c.count());
-    for (uint32_t k = 0; k < c.count(); ++k) c.block_end[k] = c.chunks[k].block_base + c.chunks[k].nblocks;
     for (auto& g : c.groups) {
-        const gpz_status st = device_info(c.kind, g.F, &c.sms, &g.max_ctas);
+        const gpz_status st = device_info(c.kind, g.F, &c.sms);
         if (st != GPZ_OK) return st;
     }
-    c.cfg = clamp_cfg(c, cfg ? *cfg : gpz_batch_config{});
+    c.cfg = clamp_cfg(cfg ? *cfg : gpz_batch_config{});
     if (!lay_out_range(c)) return GPZ_ERR_UNSUPPORTED;
 
     BatchLayout& L = c.L;
@@ -205,9 +195,9 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
     if (c.kind == 0) {
         L.rkeys = take(4ull * kMaxFields * 2 * n);
         L.rdone = take(4 * n);
-        L.ready = take(4 * n);
         L.states = take(8 * ntiles_of(blocks));
         L.zero_bytes = o;
+        L.map = take(4 * blocks);
         L.rparams = take(sizeof(FieldParams) * kMaxFields * n);
         L.offsets = take(8 * (blocks + 1));
         L.sizes = take(4 * blocks);
@@ -216,38 +206,37 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
         L.temp = take(4 * temp);
     } else {
         L.zero_bytes = o;
+        L.map = take(4 * blocks);
     }
     L.total = o;
-    // kernels per run: per group the fused kernel and the general one (or the
-    // decoder) when the group has work, then the scan and the compaction
-    c.launches = c.kind == 0 ? 2u : 0u;
+    // kernels per run: the map when there are blocks; per group the range
+    // items, the blocks and the general list (or the decoder) when it has
+    // them; the scan and the compaction
+    c.launches = (blocks > 0 ? 1u : 0u) + (c.kind == 0 ? 2u : 0u);
     for (const auto& g : c.groups)
-        if ((c.kind == 0 && (uint64_t)g.range_items + g.blocks > 0) || (c.kind == 1 && g.blocks > 0))
-            c.launches += c.kind == 0 ? 2u : 1u;
+        c.launches += c.kind == 0 ? (g.range_items > 0) + 2u * (g.blocks > 0) : (g.blocks > 0);
     return GPZ_OK;
 }
 
 gpz_status core_set_config(BatchCore& c, const gpz_batch_config& cfg, bool* redo) {
-    const gpz_batch_config v = clamp_cfg(c, cfg);
+    const gpz_batch_config v = clamp_cfg(cfg);
     *redo = c.kind == 0 && c.any_rel && v.range_slice != c.cfg.range_slice;
     c.cfg = v;
     if (*redo && !lay_out_range(c)) return GPZ_ERR_UNSUPPORTED;
     return GPZ_OK;
 }
 
-uint64_t core_device_bytes(const BatchCore& c) { return desc_offset(c, 2) + align_up(4ull * c.count(), kAlign); }
+uint64_t core_device_bytes(const BatchCore& c) { return desc_offset(c, 1) + align_up(4ull * c.count(), kAlign); }
 
 void core_pack(const BatchCore& c, uint8_t* host) {
     std::memcpy(host + desc_offset(c, 0), c.chunks.data(), sizeof(BatchChunk) * c.count());
     std::memcpy(host + desc_offset(c, 1), c.range_end.data(), 4ull * c.count());
-    std::memcpy(host + desc_offset(c, 2), c.block_end.data(), 4ull * c.count());
 }
 
 BatchDevice core_device_view(const BatchCore& c, uint8_t* device) {
     BatchDevice d;
     d.chunks = reinterpret_cast<BatchChunk*>(device + desc_offset(c, 0));
     d.range_end = reinterpret_cast<uint32_t*>(device + desc_offset(c, 1));
-    d.block_end = reinterpret_cast<uint32_t*>(device + desc_offset(c, 2));
     return d;
 }
 
@@ -257,27 +246,28 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
     const gpz_batch_config& cfg = c.cfg;
     uint32_t* ctrl = reinterpret_cast<uint32_t*>(ws + L.ctrl);
     uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
+    uint32_t* map = reinterpret_cast<uint32_t*>(ws + L.map);
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return GPZ_ERR_CUDA;
     Recorder rec(s);
     if (timed) rec.begin((int)c.launches);
+    if (c.total_blocks > 0) {
+        BatchMapArgs ma{};
+        ma.chunks = dev.chunks;
+        ma.nchunks = c.count();
+        ma.block_map = map;
+        if (launch_batch_map(ma, s) != cudaSuccess) return GPZ_ERR_CUDA;
+        rec.mark("batch_map");
+    }
     if (c.kind == 1) {
-        for (size_t k = 0; k < c.groups.size(); ++k) {
-            const BatchGroup& g = c.groups[k];
+        for (const BatchGroup& g : c.groups) {
             if (g.blocks == 0) continue;  // nothing to decode
             BatchDecompressArgs a{};
             a.chunks = dev.chunks;
-            a.first = g.first;
-            a.nchunks = g.count;
-            a.block_end = dev.block_end;
+            a.block_map = map;
             a.block_first = g.block_first;
             a.total_blocks = g.blocks;
-            a.claim = cfg.claim;
-            a.ticket = ctrl + k;
             a.chunk_status = status;
-            const uint32_t per_sm = std::min<uint32_t>(cfg.ctas_per_sm, (uint32_t)g.max_ctas);
-            const uint64_t want = ((uint64_t)g.blocks + cfg.claim - 1) / cfg.claim;
-            const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per_sm * c.sms, want));
-            if (launch_batch_decompress(a, g.F, grid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+            if (launch_batch_decompress(a, g.F, s) != cudaSuccess) return GPZ_ERR_CUDA;
             rec.mark("batch_decompress");
         }
         return GPZ_OK;
@@ -285,37 +275,35 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
     BatchCompressArgs a{};
     a.chunks = dev.chunks;
     a.range_end = dev.range_end;
-    a.block_end = dev.block_end;
+    a.block_map = map;
     a.slice = cfg.range_slice;
-    a.claim = cfg.claim;
     a.rkeys = reinterpret_cast<uint32_t*>(ws + L.rkeys);
     a.rdone = reinterpret_cast<uint32_t*>(ws + L.rdone);
-    a.ready = reinterpret_cast<uint32_t*>(ws + L.ready);
     a.rparams = reinterpret_cast<FieldParams*>(ws + L.rparams);
     a.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
     a.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
     a.chunk_status = status;
     for (size_t k = 0; k < c.groups.size(); ++k) {
         const BatchGroup& g = c.groups[k];
-        const uint64_t items = (uint64_t)g.range_items + g.blocks;
-        if (items == 0) continue;  // only empty absolute-bound chunks: the compaction writes their headers
         a.first = g.first;
         a.nchunks = g.count;
         a.range_first = g.range_first;
         a.range_items = g.range_items;
         a.block_first = g.block_first;
         a.total_blocks = g.blocks;
-        a.ticket = ctrl + k;
         a.general_list = reinterpret_cast<uint32_t*>(ws + L.list) + g.block_first;
-        a.general_count = ctrl + 8 + k;
-        const uint32_t per_sm = std::min<uint32_t>(cfg.ctas_per_sm, (uint32_t)g.max_ctas);
-        const uint64_t want = g.range_items + ((uint64_t)g.blocks + cfg.claim - 1) / cfg.claim;
-        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per_sm * c.sms, want));
-        if (launch_batch_compress(a, g.F, grid, s) != cudaSuccess) return GPZ_ERR_CUDA;
-        rec.mark("batch_qse");
-        const int ggrid = (int)std::max<uint32_t>(1, std::min<uint32_t>(g.blocks, 2u * (uint32_t)c.sms));
-        if (launch_batch_general(a, g.F, ggrid, s) != cudaSuccess) return GPZ_ERR_CUDA;
-        rec.mark("batch_general");
+        a.general_count = ctrl + k;
+        if (g.range_items > 0) {
+            if (launch_batch_range(a, s) != cudaSuccess) return GPZ_ERR_CUDA;
+            rec.mark("batch_range");
+        }
+        if (g.blocks > 0) {
+            if (launch_batch_compress(a, g.F, s) != cudaSuccess) return GPZ_ERR_CUDA;
+            rec.mark("batch_qse");
+            const int ggrid = (int)std::max<uint32_t>(1, std::min<uint32_t>(g.blocks, cfg.general_ctas * (uint32_t)c.sms));
+            if (launch_batch_general(a, g.F, ggrid, s) != cudaSuccess) return GPZ_ERR_CUDA;
+            rec.mark("batch_general");
+        }
     }
     BatchScanArgs sa{};
     sa.sizes = a.sizes;
@@ -329,12 +317,11 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
     BatchCompactArgs ca{};
     ca.chunks = dev.chunks;
     ca.nchunks = c.count();
-    ca.block_end = dev.block_end;
+    ca.block_map = map;
     ca.total_blocks = c.total_blocks;
     ca.temp = a.temp;
     ca.offsets = sa.offsets;
     ca.rparams = a.rparams;
-    ca.ready = a.ready;
     ca.out_sizes = reinterpret_cast<unsigned long long*>(d_out_sizes ? (void*)d_out_sizes : (void*)(ws + L.out_sizes));
     ca.chunk_status = status;
     const uint64_t warps = (uint64_t)c.total_blocks + c.count();

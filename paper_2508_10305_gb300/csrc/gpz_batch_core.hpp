@@ -23,25 +23,23 @@ struct BatchGroup {
     uint32_t first, count;              // plan positions of the group's chunks
     uint32_t range_first, range_items;  // the group's range items
     uint32_t block_first, blocks;       // the group's blocks
-    int max_ctas;                       // CTAs per SM that fit
 };
 
 struct BatchLayout {  // byte offsets into the workspace
-    uint64_t ctrl, status, rkeys, rdone, ready, states, zero_bytes;
-    uint64_t rparams, offsets, sizes, list, out_sizes, temp, total;
+    uint64_t ctrl, status, rkeys, rdone, states, zero_bytes;
+    uint64_t map, rparams, offsets, sizes, list, out_sizes, temp, total;
 };
 
 struct BatchDevice {  // the device copy of the descriptors
     BatchChunk* chunks;
     uint32_t* range_end;
-    uint32_t* block_end;
 };
 
 struct BatchCore {
     int kind = 0;  // 0 compression, 1 decompression
     std::vector<BatchChunk> chunks;  // caller order until finish(), then plan order
     std::vector<BatchGroup> groups;
-    std::vector<uint32_t> range_end, block_end;  // inclusive prefixes, plan order
+    std::vector<uint32_t> range_end;  // inclusive prefix of range items, plan order
     uint32_t total_blocks = 0;
     uint64_t temp_words = 0;
     bool any_rel = false;
@@ -59,7 +57,8 @@ gpz_status core_add_compress(BatchCore& c, const gpz_compress_chunk& d);
 gpz_status core_add_decompress(BatchCore& c, const gpz_decompress_chunk& d);
 
 // Group by field count, number the blocks and range items, lay out the
-// workspace.  Queries the current device (SM count, occupancy; cached).
+// workspace.  Queries the current device (SM count; cached) and sets the
+// kernels' shared-memory attributes (once per device and field count).
 gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg);
 
 // Change the launch shape; re-lays the range items (the descriptors change:

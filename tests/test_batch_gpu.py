@@ -104,12 +104,12 @@ def test_batch_unaligned_fields(gpz, oracle):
     bc.close()
 
 
-@pytest.mark.parametrize("ctas,claim,slice_", [(1, 1, 1024), (4, 3, 4096), (2, 64, 1 << 20)])
-def test_batch_launch_shapes_and_graph(gpz, oracle, ctas, claim, slice_):
+@pytest.mark.parametrize("slice_,compact,general", [(1024, 1, 1), (4096, 4, 4), (1 << 20, 32, 2)])
+def test_batch_launch_shapes_and_graph(gpz, oracle, slice_, compact, general):
     """Any launch shape (and the graph replays of it) gives the same bytes;
     small slices split every relative-bound field into many range items."""
     chunks = make_chunks(14, 20)
-    cfg = gpz.gpz_batch_config(ctas, claim, slice_, 2)
+    cfg = gpz.gpz_batch_config(slice_, compact, general, 0)
     bc, streams, perms, _ = compress_batch(gpz, chunks, use_graph=True, cfg=cfg)
     assert_oracle(oracle, chunks, streams, perms)
     for _ in range(2):  # replays of the captured graph
@@ -167,7 +167,7 @@ def test_batch_tune_keeps_the_bytes(gpz, oracle):
     chunks = make_chunks(17, 16)
     bc, streams, perms, _ = compress_batch(gpz, chunks, use_graph=False)
     cfg, ms = bc.tune(reps=1)
-    assert ms > 0 and 1 <= cfg.claim <= 64 and cfg.ctas_per_sm >= 1
+    assert ms > 0 and cfg.range_slice % 1024 == 0 and 1 <= cfg.compact_ctas <= 32
     bc.sizes.zero_()
     bc()
     assert bc.status()[0] == gpz.OK
