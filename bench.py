@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--chunks", type=int, default=4096, help="batched workload: number of chunks")
     ap.add_argument("--chunk-lo", type=int, default=10_000)
     ap.add_argument("--chunk-hi", type=int, default=4_000_000)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="batched workload: time the batched plans only (default shapes; no tuning, no per-chunk "
+                         "arm, no parity pass): for profiling")
     return ap.parse_args()
 
 
@@ -475,6 +478,29 @@ def run_batched(args):
     if st != gpz.OK:
         raise gpz.GpzError(st, "batched decompress")
 
+    def batched_step():
+        bc(stream)
+        bd(stream)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    if args.batched_only:
+        ms = timed(batched_step, args.steps, args.warmup)
+        print(json.dumps({"workload": "batched (plans only, default shapes)", "chunks": wl.count,
+                          "input_gb": in_bytes / 1e9, "ms_per_step": ms,
+                          "gbs": in_bytes / (ms / 1e3) / 1e9}), flush=True)
+        return
+
     # tuned launch shapes (the outputs are rewritten with the same bytes)
     ccfg, cms = bc.tune(reps=2)
     dcfg, dms = bd.tune(reps=2)
@@ -502,10 +528,6 @@ def run_batched(args):
         oracle_equal += int(np.array_equal(streams[c].cpu().numpy(), rs))
     del scratch
 
-    def batched_step():
-        bc(stream)
-        bd(stream)
-
     # one call per chunk through the public API (same buffers, same order of
     # work: every chunk compressed, then every chunk decompressed)
     d_size = torch.zeros(wl.count, dtype=torch.int64, device=dev)
@@ -524,18 +546,6 @@ def run_batched(args):
             gpz.lib.gpz_compress(a[0], a[1], a[2], a[3], a[4], a[5], None, None, ws.data_ptr(), ws_max, s_handle)
         for a in dec_args:
             gpz.lib.gpz_decompress(a[0], a[1], a[2], a[3], a[4], dec_ws.data_ptr(), dec_ws.numel(), s_handle)
-
-    def timed(fn, steps, warm):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
 
     gpz.gpz_launch_count(reset=True)
     with ClockSampler(0) as clk:
