@@ -101,21 +101,26 @@ def load_peaks():
 
 def recorded_traffic(kernel):
     """Per-launch DRAM bytes from the committed ncu summary of `kernel`, or
-    None when the kernel's source changed since the counters were taken."""
+    None when any source the kernel is built from changed since the counters
+    were taken (the summary lists the files and their sha256)."""
     path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel)
     if not os.path.exists(path):
         return None
-    info = {}
+    info, hashes = {}, {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, _, v = line.partition(":")
-            info[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2508_10305_gb300", "csrc", info.get("source", ""))
-    if not os.path.exists(src):
+            k, v = k.strip(), v.strip()
+            if k.startswith("sha256 "):
+                hashes[k[len("sha256 "):]] = v
+            else:
+                info[k] = v
+    if not hashes:
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if digest != info.get("source_sha256"):
-        return None
+    for name, digest in hashes.items():
+        src = os.path.join(ROOT, "paper_2508_10305_gb300", "csrc", name)
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != digest:
+            return None
     try:
         return float(info["dram_bytes_per_launch_full_size"])
     except (KeyError, ValueError):

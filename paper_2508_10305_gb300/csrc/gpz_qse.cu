@@ -9,7 +9,9 @@
 //   1. coalesced streaming loads; per-field exact fp32 minimum (Section 4.1:
 //      per-thread, then warp reduction, then a shared atomic per warp);
 //   2. quantisation q = floor(fma(x - min, 1/s, 1/2)) with the stream
-//      format's fp32 verification and candidate fallback; for codes below
+//      format's fp32 verification (skipped for blocks where it provably
+//      passes); blocks that need a fallback candidate, codes >= 2^23 or
+//      records wider than 128 bits go to the general kernel; for codes below
 //      2^23 the floor and the int<->float conversions are one add in
 //      round-down mode against 2^23 (full-rate pipes);
 //   3. segId / segOffset by shift and mask (Section 5.1), the linearised
@@ -20,9 +22,11 @@
 //      histogram; a CTA-wide scan over (bin, warp) gives every element its
 //      sorted position.  The non-empty bins are the run-length code (unique
 //      ids and counts, Section 4.3);
-//   5. fixed-length coding (Section 4.3) by word-owner gather: thread k builds
-//      output words k, k+256, ... from the sorted records in shared memory and
-//      stores them coalesced;
+//   5. fixed-length coding (Section 4.3): the sorted records are scattered
+//      to shared memory, and each thread packs its run of deltas, counts and
+//      records into zeroed staging words with a thread-serial bit appender
+//      (words shared with a neighbour are merged with atomicOr); the
+//      encoded block is copied out with 16-byte stores;
 //   6. the block goes to its temporary slot with its word count (step 1 of
 //      the three-step compaction, Section 4.4).
 #include "gpz_qse_block.cuh"

@@ -533,9 +533,28 @@ struct QseFastShared {
     uint32_t warp_tot[kWarps], warp_nz[kWarps];
 };
 
-// Quantise the thread's 4 values of field f (fast candidate only), add the
-// field's segId to the key and append its code to the record words.
-template <int NW>
+// Whether every first candidate of a field's block is certain to pass the
+// verification |RN(x - RN(fma(q, s, min)))| <= ebchk, so that it need not be
+// computed.  With Q the largest code (< 2^k) and M the largest |x| of the
+// block, the rounding of d = RN(x - min), of t = RN(fma(d, 1/s, 1/2)) (t <
+// 2^(k+1)), of 1/s and of the reconstruction add up to at most
+// s 2^(k-23) + 3.0001 ulp(M) + 2 ulp(s) beyond the half step s/2 <= eb 63/64,
+// and the check passes whenever the total stays below eb (1 - 2^-20).  For
+// k <= 15 and ulp(M) <= eb/512 the total is at most 0.0136 eb + s/2, inside
+// the 1/64 margin (about 13% to spare).
+__device__ __forceinline__ bool first_candidate_exact(uint32_t bits, float mn, float mx, float eb) {
+    const float M = fmaxf(fabsf(mn), fabsf(mx));
+    const float ulp = fmaxf(__uint_as_float(__float_as_uint(M) & 0x7f800000u) * 1.1920928955078125e-7f,
+                            1.40129846e-45f);  // 2^(exponent - 23), at least the smallest subnormal
+    return bits <= 15u && __fmul_rn(ulp, 512.0f) <= eb;
+}
+
+// Quantise the thread's 4 values of field f (first candidate only), add the
+// field's segId to the key and append its code to the record words.  With
+// VERIFY the candidate is checked as the format requires and `pend` is set
+// when one fails; without, the caller has shown that none can fail
+// (first_candidate_exact).
+template <int NW, bool VERIFY>
 __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool (&valid)[4], float mn,
                                                 const FieldParams& p, bool pos, uint32_t o, uint32_t ks,
                                                 uint32_t wf, uint32_t (&key)[4], uint32_t (&rw)[4][4],
@@ -545,8 +564,10 @@ __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool 
         const float tt = __fmaf_rn(__fsub_rn(x[r], mn), p.inv, 0.5f);
         const float u = __fadd_rd(tt, 8388608.0f);  // 2^23 + floor(t), t < 2^23 here
         uint32_t q = __float_as_uint(u) - kMagic23;
-        const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), p.s, mn);
-        pend |= valid[r] && !(fabsf(__fsub_rn(x[r], xh)) <= p.ebchk);
+        if (VERIFY) {
+            const float xh = __fmaf_rn(__fsub_rn(u, 8388608.0f), p.s, mn);
+            pend |= valid[r] && !(fabsf(__fsub_rn(x[r], xh)) <= p.ebchk);
+        }
         q = valid[r] ? q : 0u;
         uint32_t code = q;
         if (pos) {
@@ -636,17 +657,19 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     // largest code is q0 of the block maximum
     float mn[F];
     uint32_t bits[F], o[F], wf[F], kshift[F], W = 0, keybits = 0;
-    bool big = false;
+    bool big = false, exact = true;
     {
         uint32_t g[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
             const float m = from_order_key(S.minkey[f]);
+            const float mx = from_order_key(S.maxkey[f]);
             mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
-            const float tq = __fmaf_rn(__fsub_rn(from_order_key(S.maxkey[f]), mn[f]), p.inv, 0.5f);
+            const float tq = __fmaf_rn(__fsub_rn(mx, mn[f]), p.inv, 0.5f);
             big |= !(tq < 8388608.0f);
             bits[f] = bit_width(__float_as_uint(__fadd_rd(tq, 8388608.0f)) - kMagic23);
+            exact = exact && first_candidate_exact(bits[f], mn[f], mx, p.eb);
             g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
             o[f] = f < P ? bits[f] - g[f] : 0u;
             wf[f] = f < P ? o[f] : bits[f];
@@ -672,20 +695,36 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
 #pragma unroll
     for (int r = 0; r < 4; ++r) rw[r][0] = rw[r][1] = rw[r][2] = rw[r][3] = 0u;
     bool pend = false;
-    if (W <= 64u) {
+    if (exact) {  // uniform: no first candidate of the block can fail its check
+        if (W <= 64u) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
-            quantise_append<2>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            for (int f = 0; f < F; ++f) {
+                const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+                quantise_append<2, false>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+                quantise_append<4, false>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            }
         }
     } else {
+        if (W <= 64u) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-            const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
-            quantise_append<4>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            for (int f = 0; f < F; ++f) {
+                const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+                quantise_append<2, true>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
+                quantise_append<4, true>(x[f], valid, mn[f], p, f < P, o[f], kshift[f], wf[f], key, rw, pend);
+            }
         }
+        if (__any_sync(0xffffffffu, pend) && lane == 0) atomicOr(&S.flags, 2u);
     }
-    if (__any_sync(0xffffffffu, pend) && lane == 0) atomicOr(&S.flags, 2u);
 
     // ---- 4. stable counting sort: warp-local ranks in storage order
     uint16_t* myhist = hist + w * kMaxBins;

@@ -242,3 +242,22 @@ def test_lidar_200m_sampled(gpz, oracle):
     x = synth.lidar(200_000_000, seed=3, device="cuda")
     size = _full_size_check(gpz, oracle, x, 1e-3, 0, 3, n_samples=300, seed=2)
     assert x.numel() * 4 / size > 2.0
+
+
+def test_unchecked_first_candidates_boundary(gpz, oracle):
+    """Blocks at the edge of the condition under which the fast path skips
+    the check of first candidates (codes just below 2^15, ulp(max |x|) just
+    below eb/512), with values on and around the midpoints between lattice
+    points: the stream must equal the oracle's, which always checks."""
+    from tests.test_first_candidate_bound import adversarial_block
+    rng = np.random.default_rng(77)
+    cases = 0
+    while cases < 24:
+        eb = 10.0 ** rng.uniform(-5, 1)
+        blk = adversarial_block(rng, eb, int(rng.integers(13, 16)), 512)
+        if blk is None:
+            continue
+        x1 = blk[0]
+        x = np.stack([x1, rng.permutation(x1), rng.permutation(x1)]).astype(np.float32)
+        assert_parity(gpz, oracle, x, float(blk[2]), 0, 3)
+        cases += 1
