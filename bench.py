@@ -309,6 +309,7 @@ def run_gpz(args, rank, world, local):
     ebs = [float(hdr[16 + 2 * f].view(np.float32)) for f in range(F)]
     psnr, worst = psnr_and_error(x, out, perm, ebs)
     ratio = x.numel() * 4 / size
+    out_ref_host = out.cpu() if not args.no_e2e else None
     del chk, perm, out
     torch.cuda.empty_cache()
 
@@ -401,10 +402,17 @@ def run_gpz(args, rank, world, local):
     }
 
     # end to end through the public API with host buffers: H2D input ->
-    # compress -> D2H stream -> H2D stream -> decompress -> D2H output
+    # compress -> D2H stream -> H2D stream -> decompress -> D2H output, every
+    # step.  Timed twice: one step after another on one stream, and pipelined
+    # (two buffer sets; the next step's uploads overlap this step's downloads
+    # and kernels on separate copy and compute streams), the form a user
+    # streaming snapshots through the library would run.
     if not args.no_e2e:
         h_in = torch.empty((F, n), dtype=torch.float32, pin_memory=True)
         h_in.copy_(x)
+        k = max(3, min(20, args.steps // 10))
+
+        # (a) one step after another
         h_stream = torch.empty(comp.capacity, dtype=torch.uint8, pin_memory=True)
         h_out = torch.empty((F, n), dtype=torch.float32, pin_memory=True)
         d_in = torch.empty_like(x)
@@ -421,20 +429,91 @@ def run_gpz(args, rank, world, local):
 
         e2e_step()
         torch.cuda.synchronize()
-        k = max(3, min(20, args.steps // 10))
         t0 = time.perf_counter()
         for _ in range(k):
             sz = e2e_step()
         torch.cuda.synchronize()
+        dt_seq = (time.perf_counter() - t0) / k
+        del h_stream, h_out, d_in, d_stream
+        del comp, dec
+        torch.cuda.empty_cache()
+
+        # (b) pipelined: buffer set j = i % 2 per step i
+        # uploads, kernels, downloads
+        s_up, s_run, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        sets = []
+        for j in range(2):
+            c_ = gpz.Compressor(n, F, REL_EB, gpz.EB_REL, SEG_BITS, want_perm=False, device=dev)
+            sets.append({"comp": c_, "dec": gpz.Decompressor(n, F, device=dev), "d_in": torch.empty_like(x),
+                         "d_stream": torch.empty_like(c_.out),
+                         "h_stream": torch.empty(c_.capacity, dtype=torch.uint8, pin_memory=True),
+                         "h_out": torch.empty((F, n), dtype=torch.float32, pin_memory=True),
+                         "h_size": torch.zeros(1, dtype=torch.int64, pin_memory=True),
+                         "in_ready": torch.cuda.Event(), "in_free": torch.cuda.Event(),
+                         "size_ready": torch.cuda.Event(), "stream_down": torch.cuda.Event(),
+                         "stream_up": torch.cuda.Event(), "decoded": torch.cuda.Event(), "out_down": torch.cuda.Event()})
+        for b in sets:  # nothing to wait for at the start
+            for name in ("in_free", "stream_down", "decoded", "out_down"):
+                b[name].record(s_run)
+
+        def upload_input(i):
+            b = sets[i % 2]
+            s_up.wait_event(b["in_free"])
+            with torch.cuda.stream(s_up):
+                b["d_in"].copy_(h_in, non_blocking=True)
+            b["in_ready"].record(s_up)
+
+        def run_pipelined(steps):
+            upload_input(0)
+            for i in range(steps):
+                b = sets[i % 2]
+                s_run.wait_event(b["in_ready"])
+                s_run.wait_event(b["stream_down"])  # the previous use of this set's output buffer is on the host
+                b["comp"]([b["d_in"][f] for f in range(F)], s_run, sync=False)
+                b["in_free"].record(s_run)
+                with torch.cuda.stream(s_run):
+                    b["h_size"].copy_(b["comp"].d_size, non_blocking=True)
+                b["size_ready"].record(s_run)
+                if i + 1 < steps:
+                    upload_input(i + 1)  # overlaps this step's downloads and kernels
+                b["size_ready"].synchronize()
+                sz_ = int(b["h_size"].item())
+                s_down.wait_event(b["size_ready"])
+                with torch.cuda.stream(s_down):
+                    b["h_stream"][:sz_].copy_(b["comp"].out[:sz_], non_blocking=True)
+                b["stream_down"].record(s_down)
+                s_up.wait_event(b["stream_down"])
+                s_up.wait_event(b["decoded"])  # the previous decode of this set has read d_stream
+                with torch.cuda.stream(s_up):
+                    b["d_stream"][:sz_].copy_(b["h_stream"][:sz_], non_blocking=True)
+                b["stream_up"].record(s_up)
+                s_run.wait_event(b["stream_up"])
+                s_run.wait_event(b["out_down"])  # the previous output of this set is on the host
+                o_ = b["dec"](b["d_stream"], sz_, s_run, check=False)
+                b["decoded"].record(s_run)
+                s_down.wait_event(b["decoded"])
+                with torch.cuda.stream(s_down):
+                    b["h_out"].copy_(o_, non_blocking=True)
+                b["out_down"].record(s_down)
+            return sz_
+
+        run_pipelined(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sz = run_pipelined(k)
+        torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / k
-        e = torch.tensor([dt], dtype=torch.float64, device=dev)
+        # the pipelined steps' outputs are the same values as the device path's
+        ok_e2e = bool(torch.equal(sets[(k - 1) % 2]["h_out"], out_ref_host)) if out_ref_host is not None else None
+        e = torch.tensor([dt, dt_seq], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(e, op=dist.ReduceOp.MAX)
-        dt = float(e.item())
+        dt, dt_seq = float(e[0].item()), float(e[1].item())
         result["e2e"] = {"value": world * in_bytes / dt / 1e9, "unit": "GB/s",
                          "h2d_bytes_per_step": int(in_bytes + sz), "d2h_bytes_per_step": int(in_bytes + sz + 8),
-                         "ms_per_step": 1e3 * dt}
-        del h_in, h_stream, h_out, d_in, d_stream
+                         "ms_per_step": 1e3 * dt, "pipelined": True, "output_checked": ok_e2e,
+                         "sequential": {"value": world * in_bytes / dt_seq / 1e9, "ms_per_step": 1e3 * dt_seq}}
+        del sets, h_in
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, npart = host_sample(x, every=4)

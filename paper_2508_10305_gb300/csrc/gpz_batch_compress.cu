@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) gpz_batch_range_kernel(BatchCompress
 // One CTA per block of the group: the single-array fused kernel's code, with
 // the chunk's arguments in shared memory.
 template <int F>
-__global__ void __launch_bounds__(kThreads, 4) gpz_batch_compress_kernel(BatchCompressArgs g) {
+__global__ void __launch_bounds__(kThreads, 5) gpz_batch_compress_kernel(BatchCompressArgs g) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     __shared__ QseArgs A;

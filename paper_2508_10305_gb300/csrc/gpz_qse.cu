@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 2) gpz_qse_general_kernel(QseArgs a)
 }
 
 template <int F>
-__global__ void __launch_bounds__(kThreads, 4) gpz_qse_kernel(QseArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) gpz_qse_kernel(QseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)

@@ -519,11 +519,15 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
 
 // ------------------------------------------------------------------ fast path
 
-constexpr uint32_t kFastRegion = kHistBytes + kBlock * 16u;  // histograms + 128-bit sorted records
+// Fast-path shared memory: the 128-bit sorted records, the unique ids and
+// counts, the sorted permutation, and the staging words of the encoded block,
+// whose first 8 KB hold the per-warp histograms until the scatter is done.
+constexpr uint32_t kFastRecords = 0u;
+constexpr uint32_t kFastUniq = kFastRecords + kBlock * 16u;
+constexpr uint32_t kFastStage = kFastUniq + kMaxBins * 2u + kMaxBins * 2u + kBlock * 2u;
+static_assert(kHistBytes <= kStageWords * 4u, "the histograms live in the staging words");
 
-__host__ __device__ constexpr uint32_t qse_fast_smem_bytes() {
-    return kFastRegion + kMaxBins * 2u + kMaxBins * 2u + kBlock * 2u + kStageWords * 4u;
-}
+__host__ __device__ constexpr uint32_t qse_fast_smem_bytes() { return kFastStage + kStageWords * 4u; }
 
 struct QseFastShared {
     uint32_t minkey[kMaxFields];
@@ -591,12 +595,12 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int n_b = FULL ? kBlock : (int)(a.n - (uint64_t)idx.b() * kBlock);
-    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm);                     // [8][512]
-    uint4* recs = reinterpret_cast<uint4*>(dsm + kHistBytes);               // [1024] 128-bit records
-    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastRegion);        // [512]
+    uint4* recs = reinterpret_cast<uint4*>(dsm + kFastRecords);             // [1024] 128-bit records
+    uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastUniq);          // [512]
     uint16_t* cnt = uniq + kMaxBins;                                         // [512]
     uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
-    uint32_t* stage = reinterpret_cast<uint32_t*>(sperm + kBlock);           // [kStageWords]
+    uint32_t* stage = reinterpret_cast<uint32_t*>(dsm + kFastStage);        // [kStageWords]
+    uint16_t* hist = reinterpret_cast<uint16_t*>(stage);                    // [8][512], until the scatter
 
     if (t < F) {
         S.minkey[t] = 0xffffffffu;
@@ -611,7 +615,6 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
 #pragma unroll
         for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
-        for (uint32_t k = t; k < kStageWords; k += kThreads) stage[k] = 0u;
     }
 
     // ---- 1. load (coalesced, streaming); block minimum and maximum
@@ -830,7 +833,10 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
 
     // ---- 5. block header and the three arrays (Section 4.3), assembled in the
-    // zeroed staging words by thread-serial appenders, then copied out
+    // staging words (zeroed now: they held the histograms) by thread-serial
+    // appenders, then copied out
+    for (uint32_t k = t; k < enc; k += kThreads) stage[k] = 0u;
+    __syncthreads();
     if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
     if (t >= 1 && t <= F) {
         float m = 0.0f;
