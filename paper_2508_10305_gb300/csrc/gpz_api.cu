@@ -25,7 +25,7 @@ std::atomic<uint64_t> g_launches{0};
 namespace {
 
 constexpr uint64_t kAlign = 256;
-constexpr int kRangeGridMax = 152 * 4;
+constexpr int kRangeGridMax = 152 * 8;  // range-pass CTAs: 8 per SM of a GB300 (full occupancy)
 constexpr uint64_t kCtrlBytes = 256;    // status, tile counter, range counter, out size
 constexpr uint64_t kParamBytes = 256;   // FieldParams[8]
 

@@ -11,7 +11,7 @@ namespace gpz {
 
 // One CTA per block of the group.
 template <int F>
-__global__ void __launch_bounds__(kDecThreads, 6) gpz_batch_decompress_kernel(BatchDecompressArgs g) {
+__global__ void __launch_bounds__(kDecThreads, 8) gpz_batch_decompress_kernel(BatchDecompressArgs g) {
     __shared__ DecShared S;
     __shared__ DecArgs A;
     __shared__ uint32_t s_b;  // block within its chunk

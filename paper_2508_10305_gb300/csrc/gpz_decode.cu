@@ -21,7 +21,7 @@
 namespace gpz {
 
 template <int F>
-__global__ void __launch_bounds__(kDecThreads, 6) gpz_decompress_kernel(DecArgs a) {
+__global__ void __launch_bounds__(kDecThreads, 8) gpz_decompress_kernel(DecArgs a) {
     __shared__ DecShared S;
     decode_block<F>(a, S, DecGridBlock{});
 }

@@ -44,8 +44,18 @@ __global__ void __launch_bounds__(kRangeThreads) gpz_range_kernel(RangeArgs a) {
         if (a.vec_ok) {
             const float4* x4 = reinterpret_cast<const float4*>(x);
             const uint64_t n4 = a.n >> 2;
-            for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
-                float4 v = __ldcs(x4 + i);
+            const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+            uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid;
+            for (; i + 3 * stride < n4; i += 4 * stride) {  // four 16-byte loads in flight per thread
+                const float4 v0 = __ldcs(x4 + i), v1 = __ldcs(x4 + i + stride), v2 = __ldcs(x4 + i + 2 * stride),
+                             v3 = __ldcs(x4 + i + 3 * stride);
+                lo = fminf(lo, fminf(fminf(fminf(v0.x, v0.y), fminf(v0.z, v0.w)), fminf(fminf(v1.x, v1.y), fminf(v1.z, v1.w))));
+                lo = fminf(lo, fminf(fminf(fminf(v2.x, v2.y), fminf(v2.z, v2.w)), fminf(fminf(v3.x, v3.y), fminf(v3.z, v3.w))));
+                hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v0.x, v0.y), fmaxf(v0.z, v0.w)), fmaxf(fmaxf(v1.x, v1.y), fmaxf(v1.z, v1.w))));
+                hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v2.x, v2.y), fmaxf(v2.z, v2.w)), fmaxf(fmaxf(v3.x, v3.y), fmaxf(v3.z, v3.w))));
+            }
+            for (; i < n4; i += stride) {
+                const float4 v = __ldcs(x4 + i);
                 lo = fminf(fminf(lo, v.x), fminf(v.y, fminf(v.z, v.w)));
                 hi = fmaxf(fmaxf(hi, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
             }
@@ -84,20 +94,29 @@ __global__ void __launch_bounds__(kRangeThreads) gpz_range_kernel(RangeArgs a) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (tid < a.F) {
-        const int f = tid;
+    for (int f = 0; f < a.F; ++f) {  // all threads fold the CTAs' partials of field f
         float lo = INFINITY, hi = -INFINITY;
-        for (unsigned c = 0; c < gridDim.x; ++c) {
-            float2 p = __ldcg(a.partials + (size_t)c * a.F + f);
+        for (unsigned c = tid; c < gridDim.x; c += blockDim.x) {
+            const float2 p = __ldcg(a.partials + (size_t)c * a.F + f);
             lo = fminf(lo, p.x);
             hi = fmaxf(hi, p.y);
         }
-        double rel = a.rel[0];
+        lo = warp_min_f32(lo);
+        hi = warp_max_f32(hi);
+        if (lane == 0) red[warp] = make_float2(lo, hi);
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kRangeThreads / 32; ++w) {
+                lo = fminf(lo, red[w].x);
+                hi = fmaxf(hi, red[w].y);
+            }
+            double rel = a.rel[0];
 #pragma unroll
-        for (int k = 1; k < kMaxFields; ++k)
-            if (k == f) rel = a.rel[k];
-        const FieldParams p = range_params(lo, hi, rel);
-        a.d_params[f] = p;
+            for (int k = 1; k < kMaxFields; ++k)
+                if (k == f) rel = a.rel[k];
+            a.d_params[f] = range_params(lo, hi, rel);
+        }
+        __syncthreads();
     }
 }
 
