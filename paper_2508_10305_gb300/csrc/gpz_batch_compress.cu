@@ -281,13 +281,12 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
             uint32_t* out = dst + payload_start + rel;
             const uint32_t L = (uint32_t)len;
             uint32_t k = lane;
-            for (; k + 96 < L; k += 128) {
-                const uint32_t x0 = __ldcs(src + k), x1 = __ldcs(src + k + 32), x2 = __ldcs(src + k + 64),
-                               x3 = __ldcs(src + k + 96);
-                out[k] = x0;
-                out[k + 32] = x1;
-                out[k + 64] = x2;
-                out[k + 96] = x3;
+            for (; k + 224 < L; k += 256) {  // eight words in flight per lane
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcs(src + k + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) out[k + 32 * u] = v[u];
             }
             for (; k < L; k += 32) out[k] = __ldcs(src + k);
         } else {

@@ -154,13 +154,12 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
         const uint32_t* src = a.temp + (size_t)b * a.slot_words;
         uint32_t* dst = payload + __ldcg(a.table + b);
         uint32_t k = lane;
-        for (; k + 96 < len; k += 128) {
-            const uint32_t x0 = __ldcs(src + k), x1 = __ldcs(src + k + 32), x2 = __ldcs(src + k + 64),
-                           x3 = __ldcs(src + k + 96);
-            dst[k] = x0;
-            dst[k + 32] = x1;
-            dst[k + 64] = x2;
-            dst[k + 96] = x3;
+        for (; k + 224 < len; k += 256) {  // eight words in flight per lane
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(src + k + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dst[k + 32 * u] = v[u];
         }
         for (; k < len; k += 32) dst[k] = __ldcs(src + k);
     }
