@@ -27,7 +27,7 @@ GB/s of each.
 
 measures the batched form instead (one line, not the headline): 4,096 chunks
 with log-uniform particle counts in 10K-4M, 3 or 6 fields, relative bounds
-1e-3 / 1e-4, compressed and decompressed by the persistent batched launches
+1e-3 / 1e-4, compressed and decompressed by the batched launches
 replayed as CUDA graphs with a tuned launch shape, against the same chunks
 through one gpz_compress / gpz_decompress call each (eager, and captured in
 one CUDA graph).
@@ -185,6 +185,25 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- ranks
+
+def ranks_max(values, device):
+    """Element-wise max of a list of floats over the ranks of the default
+    process group; the values themselves when there is one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_gbs(world, bytes_per_rank_step, steps, seconds):
+    """Whole-job GB/s of input: each rank processes its own snapshot every step
+    (replicas, weak scaling) and the job lasts as long as the slowest rank."""
+    return world * bytes_per_rank_step * steps / seconds / 1e9
 
 
 # ----------------------------------------------------------------------------- workload
@@ -351,12 +370,9 @@ def run_gpz(args, rank, world, local):
         if st != gpz.OK:
             raise gpz.GpzError(st, "timed region")
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms = ranks_max([elapsed_ms], dev)[0]
     in_bytes = 4.0 * n * F
-    value = world * in_bytes * args.steps / (elapsed_ms / 1e3) / 1e9
+    value = job_gbs(world, in_bytes, args.steps, elapsed_ms / 1e3)
 
     comp_ms = sum(stages[k][0] for k in ("range", "qse", "scan", "compact") if k in stages) / args.steps
     dec_ms = stages.get("decompress", (0.0, 1))[0] / args.steps
@@ -505,14 +521,11 @@ def run_gpz(args, rank, world, local):
         dt = (time.perf_counter() - t0) / k
         # the pipelined steps' outputs are the same values as the device path's
         ok_e2e = bool(torch.equal(sets[(k - 1) % 2]["h_out"], out_ref_host)) if out_ref_host is not None else None
-        e = torch.tensor([dt, dt_seq], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e, op=dist.ReduceOp.MAX)
-        dt, dt_seq = float(e[0].item()), float(e[1].item())
-        result["e2e"] = {"value": world * in_bytes / dt / 1e9, "unit": "GB/s",
+        dt, dt_seq = ranks_max([dt, dt_seq], dev)
+        result["e2e"] = {"value": job_gbs(world, in_bytes, 1, dt), "unit": "GB/s",
                          "h2d_bytes_per_step": int(in_bytes + sz), "d2h_bytes_per_step": int(in_bytes + sz + 8),
                          "ms_per_step": 1e3 * dt, "pipelined": True, "output_checked": ok_e2e,
-                         "sequential": {"value": world * in_bytes / dt_seq / 1e9, "ms_per_step": 1e3 * dt_seq}}
+                         "sequential": {"value": job_gbs(world, in_bytes, 1, dt_seq), "ms_per_step": 1e3 * dt_seq}}
         del sets, h_in
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -9,8 +9,8 @@
  * fixed-length coding (Section 4.3) and the three-step compaction (temporary
  * per-block output, prefix sum of sizes, copy; Section 4.4) -- plus the
  * decompressor, which undoes them without sorting (Section 3.2, last
- * paragraph).  Where the paper is silent or ambiguous the stream-format
- * readings of the design notes are applied; each is marked "Reading R<k>".
+ * paragraph).  Where the paper is silent or ambiguous, the choice made is
+ * stated where it is applied, marked "Reading of the paper".
  *
  * Built with -O2 -ffp-contract=off -fno-fast-math: every fp32 operation is
  * the single IEEE operation written here (fmaf is the fused one).
@@ -31,7 +31,7 @@ const uint32_t STREAM_VERSION = 1;
 const uint32_t STREAM_HEADER_WORDS = 16;
 const int MAX_FIELDS = 8;
 const int MAX_SEG_BITS = 3;
-/* Reading R5: values are quantised only while (p-min)/(2eb)+1/2 < 2^31. */
+/* Reading of the paper: values are quantised only while (p-min)/(2eb)+1/2 < 2^31. */
 const float Q_LIMIT = 2147483648.0f;
 
 uint32_t bits_of(float f) {
@@ -65,7 +65,7 @@ float float_round_down(double y) {
     return f;
 }
 
-/* Reading R2: the constants of one field from its bound eb (double).  The
+/* Reading of the paper: the constants of one field from its bound eb (double).  The
  * step is 2 eb shrunk by 1/64 (eb * 63/32, one double product): with the
  * step at exactly 2 eb a value half-way between two lattice points is eb
  * from both, and the fp32 rounding of the reconstruction then pushes both
@@ -92,7 +92,7 @@ bool within_bound(float p, uint32_t q, const gpzo_field_params& fp, float bounda
     return err <= fp.ebchk;
 }
 
-/* Reading R5: q = floor((p - min) * (1/(2 eb)) + 1/2) with one fused
+/* Reading of the paper: q = floor((p - min) * (1/(2 eb)) + 1/2) with one fused
  * multiply-add (Section 5.1), then verified; on failure q-1, then q+1.
  * Returns false when no code meets the bound (the block then goes raw). */
 bool quantise(float p, float boundary_min, const gpzo_field_params& fp, uint32_t* q_out) {
@@ -144,7 +144,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
     st->seg_id.assign(F, std::vector<uint32_t>(n_b, 0));
     st->seg_off.assign(F, std::vector<uint32_t>(n_b, 0));
 
-    /* Reading R4: a block holding any NaN or infinity is stored raw. */
+    /* Reading of the paper: a block holding any NaN or infinity is stored raw. */
     for (int f = 0; f < F; ++f)
         for (int i = 0; i < n_b; ++i)
             if (!std::isfinite(fields[f][i])) {
@@ -159,9 +159,9 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
             mn = std::min(mn, fields[f][i]);
             mx = std::max(mx, fields[f][i]);
         }
-        (void)mx; /* Reading R13: only the minimum is stored; the maximum code's
+        (void)mx; /* Reading of the paper: only the minimum is stored; the maximum code's
                      width replaces the maximum. */
-        if (mn == 0.0f) mn = 0.0f; /* Reading R4: a zero minimum is stored as +0 */
+        if (mn == 0.0f) mn = 0.0f; /* Reading of the paper: a zero minimum is stored as +0 */
         st->boundary_min[f] = mn;
     }
 
@@ -180,7 +180,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
         st->bits[f] = bit_width(qmax);
     }
 
-    /* Reading R1: segment size m = 2^o with o = bits - min(G, bits), so each
+    /* Reading of the paper: segment size m = 2^o with o = bits - min(G, bits), so each
      * axis has at most 2^G segments and m grows with the block's extent.
      * m * segId + segOffset = q. */
     for (int f = 0; f < P; ++f) {
@@ -193,7 +193,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
         }
     }
 
-    /* Reading R7: the per-axis segIds are linearised row-major, axis 0 most
+    /* Reading of the paper: the per-axis segIds are linearised row-major, axis 0 most
      * significant: key = (segId_0 * 2^g1 + segId_1) * 2^g2 + segId_2. */
     st->key.assign(n_b, 0);
     for (int i = 0; i < n_b; ++i) {
@@ -203,7 +203,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
     }
 
     /* ---------------- Stage 2: spatial sorting (Section 4.2) ---------------- */
-    /* Reading R8: sort by segId only; a radix sort is stable, so equal
+    /* Reading of the paper: sort by segId only; a radix sort is stable, so equal
      * segIds keep their storage order. */
     st->perm.resize(n_b);
     for (int i = 0; i < n_b; ++i) st->perm[i] = (uint32_t)i;
@@ -225,7 +225,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
             st->counts.back() += 1;
         }
     }
-    /* Delta coding of the unique ids (Reading R10: literal differences, the
+    /* Delta coding of the unique ids (our reading of the paper: literal differences, the
      * first against 0; counts stored as they are). */
     const size_t U = st->uniq.size();
     st->delta.assign(U, 0);
@@ -239,7 +239,7 @@ void compute_stages(const float* const* fields, int F, int n_b, int G,
     st->w_delta = bit_width(dmax);
     st->w_count = bit_width(cmax);
 
-    /* Reading R11: the per-particle record is the linearised segOffset of
+    /* Reading of the paper: the per-particle record is the linearised segOffset of
      * the position axes followed by the codes of the extra fields, field 0
      * most significant; its width is the sum of the per-field widths. */
     uint32_t W = 0;
@@ -287,7 +287,7 @@ uint32_t encoded_words_needed(int F, const BlockStages& st, int n_b) {
 }
 
 /* The words of one block: encoded, or raw when the encoder must fall back
- * or when the encoding would not be smaller (Reading R14). */
+ * or when the encoding would not be smaller (our reading of the paper). */
 std::vector<uint32_t> encode_block(const float* const* fields, int F, int n_b, int G,
                                    const gpzo_field_params* params, std::vector<uint32_t>* perm_b) {
     BlockStages st;
@@ -376,6 +376,10 @@ bool decode_block(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, con
         W += f < P ? o[f] : bits[f];
     }
     if (U < 1 || U > (uint32_t)n_b || U > (1u << key_bits)) return false;
+    /* The deltas are at most 2^key_bits - 1 and the counts at most BLOCK
+       (Section 4.3), so a width above key_bits or bit_width(BLOCK) is never
+       written. */
+    if (w_delta > key_bits || w_count > bit_width(BLOCK)) return false;
     const uint32_t d_len = ceil_div((uint64_t)U * w_delta, 32);
     const uint32_t c_len = ceil_div((uint64_t)U * w_count, 32);
     const uint32_t r_len = ceil_div((uint64_t)n_b * W, 32);
@@ -394,6 +398,7 @@ bool decode_block(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, con
         if (id >= (1ull << key_bits)) return false;
         uniq[k] = (uint32_t)id;
         counts[k] = get_bits(c_words, (uint64_t)k * w_count, w_count);
+        if (counts[k] == 0) return false; /* a run holds at least one particle */
         total += counts[k];
     }
     if (total != (uint64_t)n_b) return false;
@@ -440,7 +445,7 @@ int gpzo_params_abs(double eb, gpzo_field_params* out) {
 
 int gpzo_params_rel(double rel, const float* x, uint64_t n, gpzo_field_params* out) {
     if (!out || !(rel > 0.0) || !std::isfinite(rel) || (n > 0 && !x)) return GPZO_ERR_INVALID_ARG;
-    /* Reading R3: range over the non-NaN values; when it is not a finite
+    /* Reading of the paper: range over the non-NaN values; when it is not a finite
      * positive number the relative bound is used as an absolute one. */
     bool any = false;
     float lo = 0.0f, hi = 0.0f;

@@ -1,6 +1,6 @@
 // gpz_decode_block.cuh -- the per-block body of GPZ decompression (Section
 // 3.2: the reverse of compression, without sorting), shared by the
-// single-stream kernel (gpz_decode.cu) and the batched persistent kernel
+// single-stream kernel (gpz_decode.cu) and the batched kernel
 // (gpz_batch_decode.cu).  See gpz_decode.cu for the design.
 #pragma once
 
@@ -126,8 +126,8 @@ struct DecShared {
 };
 
 // Where a CTA gets its block's index: the grid (one CTA per block), or a
-// shared-memory slot written by a persistent loop and re-read at each use,
-// so that the index holds no register through the block code.
+// shared-memory slot (the batched kernel's block within its chunk) re-read at
+// each use, so that the index holds no register through the block code.
 struct DecGridBlock {
     __device__ __forceinline__ uint32_t b() const { return blockIdx.x; }
 };
@@ -225,7 +225,10 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
             keybits += g;
             W += f < P ? bits[f] - g : bits[f];
         }
-        ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) &&
+        // ids are below 2^keybits and counts at most 1024, so their widths are
+        // at most keybits and 11 bits: the deltas and counts then fit the
+        // words reserved for them in the staging area
+        ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) && wd <= keybits && wc <= 11u &&
              nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
     }
     if (!ok) {

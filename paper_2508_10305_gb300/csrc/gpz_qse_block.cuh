@@ -1,7 +1,7 @@
 // gpz_qse_block.cuh -- the per-block body of the fused compression kernel
 // (quantisation, sorting, encoding; Sections 4.1-4.3), shared by the
-// single-array kernels (gpz_qse.cu) and the batched persistent kernels
-// (gpz_batch.cu).  See gpz_qse.cu for the design.
+// single-array kernels (gpz_qse.cu) and the batched kernels
+// (gpz_batch_compress.cu).  See gpz_qse.cu for the design.
 #pragma once
 
 #include "gpz_internal.cuh"
@@ -40,8 +40,9 @@ struct QseShared {
 };
 
 // Where the fast path gets its block's index: the grid (one CTA per block),
-// or a shared-memory slot written by a persistent loop and re-read at each
-// use, so that the index holds no register through the block code.
+// or a shared-memory slot (the batched kernel's block within its chunk)
+// re-read at each use, so that the index holds no register through the
+// block code.
 struct GridBlock {
     __device__ __forceinline__ uint32_t b() const { return blockIdx.x; }   // block within its array
     __device__ __forceinline__ uint32_t id() const { return blockIdx.x; }  // entry for the general list

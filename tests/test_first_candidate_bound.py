@@ -1,8 +1,8 @@
 """The fast compression path skips the check of a block's first candidates
 when first_candidate_exact() holds (csrc/gpz_qse_block.cuh): every code of the
 block below 2^15 and ulp(max |x|) <= eb/512.  That is only sound if, under the
-condition, the format's check (Section 4.1 quantisation with the readings R2
-and R5: q = floor(RN(fma(RN(x - min), 1/s, 1/2))), then
+condition, the format's check (Section 4.1 quantisation with the step and
+rounding used here: q = floor(RN(fma(RN(x - min), 1/s, 1/2))), then
 |RN(x - RN(fma(q, s, min)))| <= ebchk) can never fail.
 
 This test checks the claim with exact arithmetic over adversarial blocks that

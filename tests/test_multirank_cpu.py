@@ -1,0 +1,67 @@
+"""The benchmark's multi-rank path on CPU: two processes over the gloo
+backend (the GPU run uses one process per GPU over NCCL; the host logic is
+the same).  Ranks are replicas: each draws its own snapshot, no collective
+touches the data, and the job's time is the slowest rank's."""
+import json
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, outdir):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    r = {"env": list(bench.dist_env())}
+    # the slowest rank's time, element by element
+    r["max"] = bench.ranks_max([1.0 + rank, 10.0 - rank, 0.5], "cpu")
+    # each rank's own snapshot: identical shape, different values
+    x = bench.make_workload(4096, rank, "cpu")
+    sums = [torch.zeros(1, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(sums, x.double().sum().reshape(1))
+    r["sums"] = [float(s.item()) for s in sums]
+    r["shape"] = list(x.shape)
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(outdir, "rank%d.json" % rank), "w") as fh:
+        json.dump(r, fh)
+
+
+def test_two_gloo_ranks(tmp_path):
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / ("rank%d.json" % r))) for r in range(world)]
+    for r in range(world):
+        assert res[r]["env"] == [r, world, 0]
+        assert res[r]["max"] == [2.0, 10.0, 0.5]
+        assert res[r]["shape"] == [6, 4096]
+        assert res[r]["sums"] == res[0]["sums"]
+    assert res[0]["sums"][0] != res[0]["sums"][1]
+
+
+def test_job_throughput_is_weak_scaling():
+    import bench
+    one = bench.job_gbs(1, 1.6e9, 10, 0.02)
+    assert one == pytest.approx(800.0)
+    # two ranks, same per-rank work, slowest rank 10% slower: 2 x 1.6 GB x 10 / 0.022 s
+    assert bench.job_gbs(2, 1.6e9, 10, 0.022) == pytest.approx(2 * 800.0 / 1.1)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    import bench
+
+    class A:
+        n, steps, warmup, gpus = 4096, 1, 0, 2
+    bench.run_reference(A, 1, 2)  # rank 1: no work, no output
+    assert capsys.readouterr().out == ""

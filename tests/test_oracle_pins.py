@@ -159,7 +159,7 @@ def test_error_bound_rel(oracle):
 @pytest.mark.parametrize("name", [n for n in gold.all_names() if "codes" in gold.load(n)])
 def test_golden_quantiser_codes(oracle, name):
     """Hand-worked cases where the first candidate fails the fp32 check and
-    the next one is kept (Reading R5)."""
+    the next one is kept (our reading of the paper)."""
     g = gold.load(name)
     st = oracle.block_stages(g["fields"], g["seg_bits"], _params(oracle, g))
     assert not st["raw"]
@@ -407,3 +407,49 @@ def test_corrupt_streams_rejected(oracle):
         k = rng.integers(0, w.size)
         bad[k] ^= np.uint32(1 << int(rng.integers(0, 32)))
         assert status(bad) in (oracle.OK, oracle.ERR_CORRUPT)
+
+
+def test_width_and_count_rules(oracle):
+    """Section 4.3: unique ids lie below 2^keybits and a run holds 1..1024
+    particles, so the encoder never writes a delta width above keybits, a
+    count width above 11 bits or a zero count.  Streams that break exactly
+    one of these rules (sizes and offsets kept consistent) are rejected;
+    wider-than-needed widths within the rules decode to the same values."""
+    from tests import _stream_edit as se
+    rng = np.random.default_rng(21)
+    x = _random_block(rng, 3, 5000, "uniform")
+    stream, _ = oracle.compress(x, 1e-2, 0, 3)
+    w = stream.view(np.uint32).copy()
+    ref = oracle.decompress(w.view(np.uint8), 3, 5000)
+
+    def decode(words):
+        out = np.zeros((3, 5000), np.float32)
+        st = oracle.decompress_status(words.view(np.uint8), 3, 5000)
+        if st == oracle.OK:
+            out = oracle.decompress(words.view(np.uint8), 3, 5000)
+        return st, out
+
+    blocks = se.encoded_blocks(w, 3, 3)
+    assert blocks
+    for b in blocks:
+        p = se.parse_block(se.block_words(w, 3, b), 3, 3)
+        assert se.rebuild_block(p) == se.block_words(w, 3, b)  # the helper round-trips
+        assert p["wd"] <= p["keybits"] and p["wc"] <= 11 and min(p["counts"]) >= 1
+        assert sum(p["counts"]) == min(1024, 5000 - 1024 * b)
+    b = blocks[0]
+    p = se.parse_block(se.block_words(w, 3, b), 3, 3)
+    assert p["U"] >= 2 and p["wd"] < p["keybits"] < 31
+    ok_cases = [dict(wd=p["keybits"]), dict(wc=11)]
+    bad_cases = [dict(wd=p["keybits"] + 1), dict(wc=12)]
+    for kw in ok_cases:
+        st, out = decode(se.replace_block(w, 3, b, se.rebuild_block(p, **kw)))
+        assert st == oracle.OK, kw
+        assert np.array_equal(out.view(np.uint32), ref.view(np.uint32)), kw
+    for kw in bad_cases:
+        st, _ = decode(se.replace_block(w, 3, b, se.rebuild_block(p, **kw)))
+        assert st == oracle.ERR_CORRUPT, kw
+    counts = list(p["counts"])
+    counts[1] += counts[0]
+    counts[0] = 0
+    st, _ = decode(se.replace_block(w, 3, b, se.rebuild_block(p, counts=counts, wc=11)))
+    assert st == oracle.ERR_CORRUPT
