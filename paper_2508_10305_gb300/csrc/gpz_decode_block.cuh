@@ -36,11 +36,9 @@ __device__ __forceinline__ uint32_t extract_s(const uint32_t* A, uint32_t k, uin
 }
 
 struct DecLayout {
-    uint32_t rs[kMaxFields];  // bit offset of the field in the record
-    uint32_t ks[kMaxFields];  // bit offset of the axis' segId in the key
-    uint32_t of[kMaxFields];  // segOffset bits of a position axis
-    uint32_t gm[kMaxFields];  // segId mask
-    uint32_t cm[kMaxFields];  // code mask
+    uint32_t wf[kMaxFields];   // bits of the field in the record
+    uint32_t g[kMaxFields];    // segId bits of a position axis in the key
+    uint32_t gmo[kMaxFields];  // segId mask, shifted above the segOffset bits
 };
 
 // (float)q for q < 2^23 with two full-rate operations.
@@ -114,6 +112,44 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
             qv[e] = f < P ? (code | (((key[e] >> kacc[f]) & gm) << wfv[f])) : code;
         }
         store4(a.out[f] + first + j0, qv, bf, sf, mnf, n_b - j0);
+    }
+}
+
+// Codes of fields F-1 .. 0 of four records, consumed from the least
+// significant end: field F-1 sits at bit 0 of the record and field 0 at the
+// top.  rr[e] holds record e in its low bits (two words when W <= 64, else
+// four); after each field the record is shifted right by the field's width
+// and the key right by the axis' segId bits.  q = segId * 2^o + segOffset for
+// a position axis, the whole code otherwise.
+template <int F, bool WIDE>
+__device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4][4], uint32_t (&key)[4],
+                                              const DecLayout& L, const uint32_t (&bits)[F], const float (&s)[F],
+                                              const float (&mn)[F], uint64_t first, int left) {
+    constexpr int P = F < 3 ? F : 3;
+#pragma unroll
+    for (int f = F - 1; f >= 0; --f) {
+        const uint32_t wf = L.wf[f], cm = mask_bits(wf);
+        uint32_t qv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t q = rr[e][0] & cm;
+            if (f < P) {
+                q |= (key[e] << wf) & L.gmo[f];
+                key[e] >>= L.g[f];
+            }
+            qv[e] = q;
+            if (f > 0) {
+                rr[e][0] = __funnelshift_r(rr[e][0], rr[e][1], wf);
+                if (WIDE) {
+                    rr[e][1] = __funnelshift_r(rr[e][1], rr[e][2], wf);
+                    rr[e][2] = __funnelshift_r(rr[e][2], rr[e][3], wf);
+                    rr[e][3] >>= wf;
+                } else {
+                    rr[e][1] >>= wf;
+                }
+            }
+        }
+        store4(a.out[f] + first, qv, bits[f], s[f], mn[f], left);
     }
 }
 
@@ -327,71 +363,48 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
         key[e] = uniq[run];
     }
-    // per-field layout (uniform): record shift, key shift, offset bits, masks
+    // per-field layout (uniform): record bits, segId bits and mask
     DecLayout L;
-    {
-        uint32_t r = 0, k = 0;
 #pragma unroll
-        for (int f = F - 1; f >= 0; --f) {
-            const uint32_t g = f < P ? min(G, bits[f]) : 0u;
-            const uint32_t wf = f < P ? bits[f] - g : bits[f];
-            L.rs[f] = r;
-            L.ks[f] = k;
-            L.of[f] = f < P ? wf : 0u;
-            L.gm[f] = mask_bits(g);
-            L.cm[f] = mask_bits(wf);
-            r += wf;
-            k += g;
-        }
+    for (int f = 0; f < F; ++f) {
+        const uint32_t g = f < P ? min(G, bits[f]) : 0u;
+        const uint32_t wf = f < P ? bits[f] - g : bits[f];
+        L.wf[f] = wf;
+        L.g[f] = g;
+        L.gmo[f] = mask_bits(g) << wf;  // g + wf = bits <= 31
     }
     if (!fast) {
         decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, G, j0, n_b, (uint64_t)idx.b() * kBlock, key[0], key[1],
                        key[2], key[3]);
         return;
     }
+    // records j0..j0+3 from the staged words; words past the record array
+    // read as 0 (their bits lie above W and are never consumed)
+    const bool wide = W > 64u;
     uint32_t rr[4][4];
-    {
-        // masks of the record's four words
-        const uint32_t m0 = mask_bits(min(W, 32u));
-        const uint32_t m1 = W > 32u ? mask_bits(min(W - 32u, 32u)) : 0u;
-        const uint32_t m2 = W > 64u ? mask_bits(min(W - 64u, 32u)) : 0u;
-        const uint32_t m3 = W > 96u ? mask_bits(W - 96u) : 0u;
-        const bool wide = W > 64u;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t p = (uint32_t)(j0 + e) * W;
-            const uint32_t wi = p >> 5, sh = p & 31u;
-            // words past the record array read as 0 (the array is staged whole)
-            const uint32_t x0 = sR[wi];
-            const uint32_t x1 = wi + 1 < rwords ? sR[wi + 1] : 0u;
-            const uint32_t x2 = wi + 2 < rwords ? sR[wi + 2] : 0u;
-            rr[e][0] = __funnelshift_r(x0, x1, sh) & m0;
-            rr[e][1] = __funnelshift_r(x1, x2, sh) & m1;
-            if (wide) {
-                const uint32_t x3 = wi + 3 < rwords ? sR[wi + 3] : 0u;
-                const uint32_t x4 = wi + 4 < rwords ? sR[wi + 4] : 0u;
-                rr[e][2] = __funnelshift_r(x2, x3, sh) & m2;
-                rr[e][3] = __funnelshift_r(x3, x4, sh) & m3;
-            } else {
-                rr[e][2] = rr[e][3] = 0u;
-            }
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t p = (uint32_t)(j0 + e) * W;
+        const uint32_t wi = p >> 5, sh = p & 31u;
+        const uint32_t x0 = sR[wi];
+        const uint32_t x1 = wi + 1 < rwords ? sR[wi + 1] : 0u;
+        const uint32_t x2 = wi + 2 < rwords ? sR[wi + 2] : 0u;
+        rr[e][0] = __funnelshift_r(x0, x1, sh);
+        rr[e][1] = __funnelshift_r(x1, x2, sh);
+        if (wide) {
+            const uint32_t x3 = wi + 3 < rwords ? sR[wi + 3] : 0u;
+            const uint32_t x4 = wi + 4 < rwords ? sR[wi + 4] : 0u;
+            rr[e][2] = __funnelshift_r(x2, x3, sh);
+            rr[e][3] = __funnelshift_r(x3, x4, sh);
+        } else {
+            rr[e][2] = rr[e][3] = 0u;
         }
     }
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        // the field starts in record word kw at bit kb (uniform); a zero-width
-        // field at the very top may sit at bit 128 and reads nothing
-        const uint32_t kw = min(L.rs[f] >> 5, 3u), kb = L.rs[f] & 31u;
-        uint32_t qv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t lo = kw == 0u ? rr[e][0] : kw == 1u ? rr[e][1] : kw == 2u ? rr[e][2] : rr[e][3];
-            const uint32_t hi = kw == 0u ? rr[e][1] : kw == 1u ? rr[e][2] : kw == 2u ? rr[e][3] : 0u;
-            const uint32_t code = __funnelshift_r(lo, hi, kb) & L.cm[f];
-            qv[e] = f < P ? (code | (((key[e] >> L.ks[f]) & L.gm[f]) << L.of[f])) : code;
-        }
-        store4(a.out[f] + (uint64_t)idx.b() * kBlock + j0, qv, bits[f], s[f], mn[f], n_b - j0);
-    }
+    const uint64_t first = (uint64_t)idx.b() * kBlock + j0;
+    if (wide)
+        decode_fields<F, true>(a, rr, key, L, bits, s, mn, first, n_b - j0);
+    else
+        decode_fields<F, false>(a, rr, key, L, bits, s, mn, first, n_b - j0);
 }
 
 }  // namespace gpz
