@@ -141,6 +141,31 @@ def test_nonfinite_blocks(gpz, oracle):
     assert_parity(gpz, oracle, x, 1e-3)
 
 
+@pytest.mark.parametrize("case", range(6))
+def test_nonfinite_variants(gpz, oracle, case):
+    """Non-finite values anywhere in a block (first or last particle of a
+    thread's row, a partial last block, any field), negative NaN and NaN
+    payloads, blocks that are entirely +Inf or -Inf, and the largest finite
+    magnitudes next to them: such blocks are stored raw, the others not."""
+    rng = np.random.default_rng(300 + case)
+    F = [6, 3, 1, 8, 2, 6][case]
+    n = [5000, 4100, 3000, 2500, 1024, 7000][case]
+    x = (rng.random((F, n)) * 100).astype(np.float32)
+    u = x.view(np.uint32)
+    picks = rng.integers(0, n, 6)
+    u[rng.integers(0, F), 0] = 0xFFC00000  # negative NaN at a block's first particle
+    u[F - 1, n - 1] = 0x7F800001           # signalling-pattern NaN at the last particle
+    u[0, picks[0]] = 0x7FBFFFFF            # NaN with payload
+    x[F // 2, picks[1]] = np.inf
+    x[F - 1, picks[2]] = -np.inf
+    x[0, picks[3]] = np.float32(3.4028235e38)    # finite extremes
+    x[F - 1, picks[4]] = np.float32(-3.4028235e38)
+    if n >= 3072:
+        x[:, 1024:2048] = np.inf if case % 2 else -np.inf  # a whole block
+    s, _, o = assert_parity(gpz, oracle, x, 1e-2)
+    assert np.isnan(o).sum() == np.isnan(x).sum() >= 2
+
+
 def test_out_of_range_and_coarse(gpz, oracle):
     y = np.array([[0.0, 3e38, -3e38] * 400], np.float32)
     assert_parity(gpz, oracle, y, 1e-6)
