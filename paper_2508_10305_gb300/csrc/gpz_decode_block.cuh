@@ -35,12 +35,6 @@ __device__ __forceinline__ uint32_t extract_s(const uint32_t* A, uint32_t k, uin
     return __funnelshift_r(A[wi], hi, sh) & mask_bits(w);
 }
 
-struct DecLayout {
-    uint32_t wf[kMaxFields];   // bits of the field in the record
-    uint32_t g[kMaxFields];    // segId bits of a position axis in the key
-    uint32_t gmo[kMaxFields];  // segId mask, shifted above the segOffset bits
-};
-
 // (float)q for q < 2^23 with two full-rate operations.
 __device__ __forceinline__ float small_u2f(uint32_t q) {
     return __fsub_rn(__uint_as_float(q + 0x4B000000u), 8388608.0f);
@@ -115,6 +109,19 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
     }
 }
 
+struct DecShared {
+    uint16_t uniq[kMaxBins];
+    uint32_t mask[32], mpre[32];
+    uint32_t warp_u[kDecWarps], warp_c[kDecWarps];
+    uint32_t bad;
+    // the block's constants, checked by warp 0 and read by every warp
+    uint32_t ok, raw, U, wd, wc, W, keybits, G;
+    uint4 lay[kMaxFields];      // per field: bits in the record, segId bits of a position axis,
+                                // segId mask shifted above the segOffset bits, code width
+    float2 ms[kMaxFields];      // per field: block minimum, step
+    alignas(16) uint32_t stage[kDecStageWords];
+};
+
 // Codes of fields F-1 .. 0 of four records, consumed from the least
 // significant end: field F-1 sits at bit 0 of the record and field 0 at the
 // top.  rr[e] holds record e in its low bits (two words when W <= 64, else
@@ -123,19 +130,19 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
 // a position axis, the whole code otherwise.
 template <int F, bool WIDE>
 __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4][4], uint32_t (&key)[4],
-                                              const DecLayout& L, const uint32_t (&bits)[F], const float (&s)[F],
-                                              const float (&mn)[F], uint64_t first, int left) {
+                                              const DecShared& L, uint64_t first, int left) {
     constexpr int P = F < 3 ? F : 3;
 #pragma unroll
     for (int f = F - 1; f >= 0; --f) {
-        const uint32_t wf = L.wf[f], cm = mask_bits(wf);
+        const uint4 lay = L.lay[f];
+        const uint32_t wf = lay.x, cm = mask_bits(wf);
         uint32_t qv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             uint32_t q = rr[e][0] & cm;
             if (f < P) {
-                q |= (key[e] << wf) & L.gmo[f];
-                key[e] >>= L.g[f];
+                q |= (key[e] << wf) & lay.z;
+                key[e] >>= lay.y;
             }
             qv[e] = q;
             if (f > 0) {
@@ -149,17 +156,11 @@ __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4
                 }
             }
         }
-        store4(a.out[f] + first, qv, bits[f], s[f], mn[f], left);
+        const float2 ms = L.ms[f];
+        store4(a.out[f] + first, qv, lay.w, ms.y, ms.x, left);
     }
 }
 
-struct DecShared {
-    uint16_t uniq[kMaxBins];
-    uint32_t mask[32], mpre[32];
-    uint32_t warp_u[kDecWarps], warp_c[kDecWarps];
-    uint32_t bad;
-    alignas(16) uint32_t stage[kDecStageWords];
-};
 
 // Where a CTA gets its block's index: the grid (one CTA per block), or a
 // shared-memory slot (the batched kernel's block within its chunk) re-read at
@@ -193,87 +194,105 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
     if (t < 32) mask[t] = 0u;
     if (t == 0) s_bad = 0u;
 
-    // ---- 1. checks, in every warp (broadcast loads; no serial phase)
-    // round trip 1: header words and, when the header fits, the block's table entries
+    // ---- 1. where the block is (every warp, one round trip): the payload
+    // size and the block's two table entries, checked only as far as staging
+    // the block safely needs
     const bool header_fits = payload_start <= a.total_words;
     uint32_t hw = 0;
-    if (lane < kHeaderWords) hw = __ldg(Sw + lane);
-    else if (lane < kHeaderWords + 2 && header_fits) hw = __ldg(Sw + table_start + b + (lane - kHeaderWords));
-    bool ok = true;
-    switch (lane) {
-        case 0: ok = hw == kMagic; break;
-        case 1: ok = hw == kVersion; break;
-        case 2: ok = hw == (uint32_t)F; break;
-        case 3: ok = hw <= (uint32_t)kMaxSegBits; break;
-        case 4: ok = hw == (uint32_t)kBlock; break;
-        case 5: ok = hw <= 1u; break;
-        case 6: ok = hw == (uint32_t)(a.n & 0xffffffffull); break;
-        case 7: ok = hw == (uint32_t)(a.n >> 32); break;
-        case 8: ok = hw == a.nblocks; break;
-        case 9: break;
-        default: ok = lane >= 10 + 6 || hw == 0u; break;
-    }
-    const uint32_t G = __shfl_sync(0xffffffffu, hw, 3);
-    const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 9);
-    const uint32_t off = __shfl_sync(0xffffffffu, hw, kHeaderWords);
-    const uint32_t end = __shfl_sync(0xffffffffu, hw, kHeaderWords + 1);
-    ok = __all_sync(0xffffffffu, ok) && header_fits && payload_start + payload_words <= a.total_words &&
-         off <= end && end <= payload_words && !(b == 0 && off != 0) &&
-         !(b + 1 == a.nblocks && end != payload_words) && end != off;
+    if (header_fits && lane < 3) hw = __ldg(lane == 0 ? Sw + 9 : Sw + table_start + b + (uint32_t)(lane - 1));
+    const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 0);
+    const uint32_t off = __shfl_sync(0xffffffffu, hw, 1);
+    const uint32_t end = __shfl_sync(0xffffffffu, hw, 2);
+    const bool inside =
+        header_fits && payload_start + payload_words <= a.total_words && off <= end && end <= payload_words;
     const uint32_t* blk = Sw + payload_start + off;
     const uint32_t nw = end - off;
-    // round trip 2: the block header (mode word, minima, width bytes), the steps,
-    // and the block's words after its header staged in shared memory (all of
-    // them when they fit; the deltas and counts always fit)
-    if (ok && nw > hdr) {
+    // round trip 2: the block's words after its header, staged in shared
+    // memory (all of them when they fit; the deltas and counts always fit)
+    if (inside && nw > hdr) {
         const uint32_t nst = min(nw - hdr, kDecStageWords);
         for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
     }
-    uint32_t bw = 0;
-    if (ok && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
-    float step = 0.0f;
-    if (ok && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
-    const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
-    const bool raw = ok && (mode & 1u);
-    if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
-    uint32_t U = 0, wd = 0, wc = 0, W = 0, keybits = 0;
-    uint32_t bits[F];
-    float mn[F], s[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const uint32_t word = __shfl_sync(0xffffffffu, bw, 1 + F + (f >> 2));
-        bits[f] = (word >> (8 * (f & 3))) & 0xffu;
-        mn[f] = __uint_as_float(__shfl_sync(0xffffffffu, bw, 1 + f));
-        s[f] = __shfl_sync(0xffffffffu, step, f);
-    }
-    if (ok && !raw) {
-        U = (mode >> 1) & 0x7ffu;
-        wd = (mode >> 12) & 31u;
-        wc = (mode >> 17) & 31u;
-        ok = (mode >> 22) == 0u && nw >= hdr;
-        // padding bytes of the last width word are zero
-        const uint32_t lastw = __shfl_sync(0xffffffffu, bw, hdr - 1);
-        if ((F & 3) != 0) ok = ok && (lastw >> (8 * (F & 3))) == 0u;
-#pragma unroll
-        for (int f = F - 1; f >= 0; --f) {
-            ok = ok && bits[f] <= 31u;
-            const uint32_t g = f < P ? min(G, bits[f]) : 0u;
-            keybits += g;
-            W += f < P ? bits[f] - g : bits[f];
+
+    // ---- the format checks and the block's constants: warp 0 alone, into
+    // shared memory (the other warps go straight on to the barrier)
+    if (w == 0) {
+        uint32_t hv = 0;
+        if (lane < kHeaderWords) hv = __ldg(Sw + lane);  // the host checked total_words >= kHeaderWords
+        bool ok = true;
+        switch (lane) {
+            case 0: ok = hv == kMagic; break;
+            case 1: ok = hv == kVersion; break;
+            case 2: ok = hv == (uint32_t)F; break;
+            case 3: ok = hv <= (uint32_t)kMaxSegBits; break;
+            case 4: ok = hv == (uint32_t)kBlock; break;
+            case 5: ok = hv <= 1u; break;
+            case 6: ok = hv == (uint32_t)(a.n & 0xffffffffull); break;
+            case 7: ok = hv == (uint32_t)(a.n >> 32); break;
+            case 8: ok = hv == a.nblocks; break;
+            case 9: break;
+            default: ok = lane >= 10 + 6 || hv == 0u; break;
         }
-        // ids are below 2^keybits and counts at most 1024, so their widths are
-        // at most keybits and 11 bits: the deltas and counts then fit the
-        // words reserved for them in the staging area
-        ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) && wd <= keybits && wc <= 11u &&
-             nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
+        const uint32_t G = __shfl_sync(0xffffffffu, hv, 3);
+        ok = __all_sync(0xffffffffu, ok) && inside && !(b == 0 && off != 0) &&
+             !(b + 1 == a.nblocks && end != payload_words) && end != off;
+        // the block header (mode word, minima, width bytes) and the steps
+        uint32_t bw = 0;
+        if (ok && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
+        float step = 0.0f;
+        if (ok && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
+        const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
+        const bool raw = ok && (mode & 1u);
+        if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
+        // lane f holds field f: its code width, minimum and step, and its
+        // layout -- bits in the record, segId bits and mask
+        const bool fl = lane < F;
+        const uint32_t wword = __shfl_sync(0xffffffffu, bw, (1 + F + (lane >> 2)) & 31);
+        const uint32_t bits = fl ? (wword >> (8 * (lane & 3))) & 0xffu : 0u;
+        const float mn = __uint_as_float(__shfl_sync(0xffffffffu, bw, (1 + lane) & 31));
+        const uint32_t bf = bits <= 31u ? bits : 0u;
+        const uint32_t g = lane < P ? min(G, bf) : 0u;
+        const uint32_t wf = fl ? bf - g : 0u;
+        uint32_t U = 0, wd = 0, wc = 0, W = 0, keybits = 0;
+        if (ok && !raw) {
+            U = (mode >> 1) & 0x7ffu;
+            wd = (mode >> 12) & 31u;
+            wc = (mode >> 17) & 31u;
+            ok = (mode >> 22) == 0u && nw >= hdr && !__any_sync(0xffffffffu, bits > 31u);
+            // padding bytes of the last width word are zero
+            const uint32_t lastw = __shfl_sync(0xffffffffu, bw, hdr - 1);
+            if ((F & 3) != 0) ok = ok && (lastw >> (8 * (F & 3))) == 0u;
+            keybits = __reduce_add_sync(0xffffffffu, g);
+            W = __reduce_add_sync(0xffffffffu, wf);
+            // ids are below 2^keybits and counts at most 1024, so their widths
+            // are at most keybits and 11 bits: the deltas and counts then fit
+            // the words reserved for them in the staging area
+            ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) && wd <= keybits && wc <= 11u &&
+                 nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
+        }
+        if (lane == 0) {
+            S.ok = ok;
+            S.raw = raw;
+            S.U = U;
+            S.wd = wd;
+            S.wc = wc;
+            S.W = W;
+            S.keybits = keybits;
+            S.G = G;
+        }
+        if (fl) {
+            S.lay[lane] = make_uint4(wf, g, mask_bits(g) << wf, bf);  // g + wf = bits <= 31
+            S.ms[lane] = make_float2(mn, step);
+        }
     }
-    if (!ok) {
+    __syncthreads();
+    if (!S.ok) {
         if (t == 0) set_status(a.status, kStCorrupt);
-        return;  // uniform across the CTA: every warp reached the same verdict
+        return;  // uniform across the CTA
     }
 
     // ---- 2. raw block
-    if (raw) {
+    if (S.raw) {
 #pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = t; i < n_b; i += kDecThreads)
@@ -281,14 +300,14 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         return;
     }
 
+    const uint32_t U = S.U, wd = S.wd, wc = S.wc, W = S.W, keybits = S.keybits;
     const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc), rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t idlimit = 1u << keybits;
 
-    // round trip 3: stage the deltas, counts and (when at most 128 bits wide)
-    // the records in shared memory, coalesced; they are contiguous in the stream
+    // the deltas, counts and (when at most 128 bits wide) the records are in
+    // the staging area, contiguous as in the stream
     const bool fast = W <= 128u;  // then dwords + cwords + rwords <= the staged words
     const uint32_t ndc = dwords + cwords;
-    __syncthreads();
     const uint32_t* sD = stage;
     const uint32_t* sC = stage + dwords;
     const uint32_t* sR = stage + ndc;
@@ -363,19 +382,9 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
         key[e] = uniq[run];
     }
-    // per-field layout (uniform): record bits, segId bits and mask
-    DecLayout L;
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const uint32_t g = f < P ? min(G, bits[f]) : 0u;
-        const uint32_t wf = f < P ? bits[f] - g : bits[f];
-        L.wf[f] = wf;
-        L.g[f] = g;
-        L.gmo[f] = mask_bits(g) << wf;  // g + wf = bits <= 31
-    }
     if (!fast) {
-        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, G, j0, n_b, (uint64_t)idx.b() * kBlock, key[0], key[1],
-                       key[2], key[3]);
+        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)idx.b() * kBlock, key[0],
+                       key[1], key[2], key[3]);
         return;
     }
     // records j0..j0+3 from the staged words; words past the record array
@@ -402,9 +411,9 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
     }
     const uint64_t first = (uint64_t)idx.b() * kBlock + j0;
     if (wide)
-        decode_fields<F, true>(a, rr, key, L, bits, s, mn, first, n_b - j0);
+        decode_fields<F, true>(a, rr, key, S, first, n_b - j0);
     else
-        decode_fields<F, false>(a, rr, key, L, bits, s, mn, first, n_b - j0);
+        decode_fields<F, false>(a, rr, key, S, first, n_b - j0);
 }
 
 }  // namespace gpz
