@@ -12,6 +12,9 @@ namespace gpz {
 constexpr int kDecWarps = kDecThreads / 32;
 // deltas (<= 512 x 9 bits) + counts (<= 512 x 11 bits) + records (<= 1024 x 128 bits)
 constexpr uint32_t kDecStageWords = 144u + 176u + 4096u;
+// words read past the staged ones: a value or record is extracted from a
+// window of words that may reach past its array; those bits are never used
+constexpr uint32_t kDecStagePad = 8u;
 
 
 __device__ __forceinline__ uint32_t mask_bits(uint32_t w) { return w >= 32u ? 0xffffffffu : ((1u << w) - 1u); }
@@ -26,13 +29,13 @@ __device__ __forceinline__ uint32_t extract(const uint32_t* A, uint32_t k, uint3
     return __funnelshift_r(lo, hi, sh) & mask_bits(w);
 }
 
-// Value k of a fixed-length array of width w (<= 31) held in shared memory.
+// Value k of a fixed-length array of width w (<= 31) held in shared memory
+// (the word after the value's first may lie past the array: its bits are
+// masked off).
 __device__ __forceinline__ uint32_t extract_s(const uint32_t* A, uint32_t k, uint32_t w) {
-    if (w == 0u) return 0u;
     const uint32_t p = k * w;
     const uint32_t wi = p >> 5, sh = p & 31u;
-    const uint32_t hi = (sh + w > 32u) ? A[wi + 1] : 0u;
-    return __funnelshift_r(A[wi], hi, sh) & mask_bits(w);
+    return __funnelshift_r(A[wi], A[wi + 1], sh) & mask_bits(w);
 }
 
 // (float)q for q < 2^23 with two full-rate operations.
@@ -112,14 +115,14 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
 struct DecShared {
     uint16_t uniq[kMaxBins];
     uint32_t mask[32], mpre[32];
-    uint32_t warp_u[kDecWarps], warp_c[kDecWarps];
+    uint32_t warp_uc[kDecWarps];  // per warp: id sum | count sum << 15
     uint32_t bad;
     // the block's constants, checked by warp 0 and read by every warp
     uint32_t ok, raw, U, wd, wc, W, keybits, G;
     uint4 lay[kMaxFields];      // per field: bits in the record, segId bits of a position axis,
                                 // segId mask shifted above the segOffset bits, code width
     float2 ms[kMaxFields];      // per field: block minimum, step
-    alignas(16) uint32_t stage[kDecStageWords];
+    alignas(16) uint32_t stage[kDecStageWords + kDecStagePad];
 };
 
 // Codes of fields F-1 .. 0 of four records, consumed from the least
@@ -179,8 +182,6 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
     uint16_t* uniq = S.uniq;
     uint32_t* mask = S.mask;
     uint32_t* mpre = S.mpre;
-    uint32_t* warp_u = S.warp_u;
-    uint32_t* warp_c = S.warp_c;
     uint32_t& s_bad = S.bad;
     uint32_t* stage = S.stage;
     constexpr int P = F < 3 ? F : 3;
@@ -321,17 +322,17 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         bool bad = (v0 && (d0 >= idlimit || c0 == 0u || c0 > (uint32_t)n_b || (k0 > 0 && d0 == 0u))) ||
                    (v1 && (d1 >= idlimit || c1 == 0u || c1 > (uint32_t)n_b || d1 == 0u));
         if (bad) d0 = d1 = c0 = c1 = 0u;  // keep the sums small; the block is rejected below
+        // one scan of both sums: a warp's id sum is below 2^15 (32 x 2 x 511)
+        // and its count sum at most 2^16 (32 x 2 x 1024), so they share a word
         const uint32_t su = d0 + d1, sc = c0 + c1;
-        const uint32_t iu = warp_incl_sum(su), ic = warp_incl_sum(sc);
-        if (lane == 31) {
-            warp_u[w] = iu;
-            warp_c[w] = ic;
-        }
+        const uint32_t iuc = warp_incl_sum(su | (sc << 15));
+        const uint32_t iu = iuc & 0x7fffu, ic = iuc >> 15;
+        if (lane == 31) S.warp_uc[w] = iuc;
         __syncthreads();
         uint32_t bu = 0, bc = 0, total = 0;
 #pragma unroll
         for (int ww = 0; ww < kDecWarps; ++ww) {
-            const uint32_t cu = warp_u[ww], cc = warp_c[ww];
+            const uint32_t uc = S.warp_uc[ww], cu = uc & 0x7fffu, cc = uc >> 15;
             if (ww < w) {
                 bu += cu;
                 bc += cc;
@@ -388,21 +389,18 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         return;
     }
     // records j0..j0+3 from the staged words; words past the record array
-    // read as 0 (their bits lie above W and are never consumed)
+    // (inside the staging pad) hold bits above W, which are never consumed
     const bool wide = W > 64u;
     uint32_t rr[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const uint32_t p = (uint32_t)(j0 + e) * W;
         const uint32_t wi = p >> 5, sh = p & 31u;
-        const uint32_t x0 = sR[wi];
-        const uint32_t x1 = wi + 1 < rwords ? sR[wi + 1] : 0u;
-        const uint32_t x2 = wi + 2 < rwords ? sR[wi + 2] : 0u;
+        const uint32_t x0 = sR[wi], x1 = sR[wi + 1], x2 = sR[wi + 2];
         rr[e][0] = __funnelshift_r(x0, x1, sh);
         rr[e][1] = __funnelshift_r(x1, x2, sh);
         if (wide) {
-            const uint32_t x3 = wi + 3 < rwords ? sR[wi + 3] : 0u;
-            const uint32_t x4 = wi + 4 < rwords ? sR[wi + 4] : 0u;
+            const uint32_t x3 = sR[wi + 3], x4 = sR[wi + 4];
             rr[e][2] = __funnelshift_r(x2, x3, sh);
             rr[e][3] = __funnelshift_r(x3, x4, sh);
         } else {
