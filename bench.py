@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_PARTICLES, help="particles (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served"])
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused-compaction comparison")
+    ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served", "sweep"])
     ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: requests per second")
@@ -417,6 +418,37 @@ def run_gpz(args, rank, world, local):
         "clocks": clk.summary(),
     }
 
+    # the fused compaction (blocks placed from the fused kernel by a
+    # decoupled look-back over blocks) on the same workload, against the
+    # three-step form timed above; the stream must be the same bytes
+    if not args.no_fused:
+        ref_stream = comp.out[:size].clone()
+        prev = gpz.gpz_set_fused_compaction(True)
+        try:
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            kf = min(args.steps, 60)
+            gpz.gpz_set_stage_timing(True)
+            gpz.gpz_stage_times()
+            ev0.record(stream)
+            for _ in range(kf):
+                step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            st_f = gpz.gpz_stage_times()
+            gpz.gpz_set_stage_timing(False)
+            deferred = gpz.compress_deferred_blocks(comp.ws)
+            same = bool(torch.equal(comp.out[:size], ref_stream))
+        finally:
+            gpz.gpz_set_fused_compaction(prev)
+        ms_f = ranks_max([ev0.elapsed_time(ev1) / kf], dev)[0]
+        result["fused_compaction"] = {
+            "value": job_gbs(world, in_bytes, 1, ms_f / 1e3), "unit": "GB/s", "ms_per_step": ms_f, "steps": kf,
+            "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st_f.items()},
+            "blocks_not_placed": deferred, "blocks": (n + 1023) // 1024, "same_stream": same}
+        del ref_stream
+
     # end to end through the public API with host buffers: H2D input ->
     # compress -> D2H stream -> H2D stream -> decompress -> D2H output, every
     # step.  Timed twice: one step after another on one stream, and pipelined
@@ -694,7 +726,7 @@ def run_batched(args):
                       "achieved_gbs": ach, "frac": ach / peak if ach else None}
     dom = max((k for k in kernels if k in algo), key=lambda k: kernels[k]["ms_per_run"])
     line = {
-        "metric": "batched compress+decompress GB/s (persistent graph-replayed plans vs one call per chunk)",
+        "metric": "batched compress+decompress GB/s (graph-replayed batched plans vs one call per chunk)",
         "value": in_bytes / (batched_ms / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -884,6 +916,63 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Ratio, quality and throughput over error bounds and segment bits G on
+    the three single-array workloads (the paper's rate-distortion view,
+    Fig. 7, on synthetic stand-ins): per point the compression ratio, bits
+    per value, PSNR, max |error| / eb and compress / decompress GB/s (CUDA
+    events, stage timing).  One JSON line."""
+    import torch
+    from paper_2508_10305_gb300 import build
+    build.build()
+    from paper_2508_10305_gb300 import gpz, synth
+
+    dev = torch.device("cuda", 0)
+    workloads = [
+        ("uniform 1e6 x 3, absolute eb", lambda: synth.uniform_box_torch(1_000_000, seed=0, device=dev),
+         gpz.EB_ABS, [1e-1, 1e-2, 1e-3, 1e-4]),
+        ("cosmology 2^26 x 6, relative eb", lambda: synth.cosmology(1 << 26, seed=2, device=dev),
+         gpz.EB_REL, [1e-2, 1e-3, 1e-4, 1e-5]),
+        ("LiDAR 2e8 x 3, absolute eb (m)", lambda: synth.lidar(200_000_000, seed=3, device=dev),
+         gpz.EB_ABS, [1e-1, 1e-2, 1e-3]),
+    ]
+    points = []
+    for name, make, mode, ebs in workloads:
+        x = make()
+        F, n = x.shape
+        fields = [x[f] for f in range(F)]
+        in_bytes = 4.0 * n * F
+        dec = gpz.Decompressor(n, F, device=dev)
+        for eb in ebs:
+            for G in (0, 1, 2, 3):
+                comp = gpz.Compressor(n, F, eb, mode, G, want_perm=True, device=dev)
+                size = comp(fields)
+                out = dec(comp.out, size)
+                hdr = comp.out[:4 * (16 + 2 * F)].cpu().numpy().view(np.uint32)
+                ebf = [float(hdr[16 + 2 * f].view(np.float32)) for f in range(F)]
+                psnr, worst = psnr_and_error(x, out, comp.perm[:n].long(), ebf)
+                reps = 5
+                gpz.gpz_set_stage_timing(True)
+                gpz.gpz_stage_times()
+                for _ in range(reps):
+                    comp(fields, sync=False)
+                    dec(comp.out, size, check=False)
+                torch.cuda.synchronize()
+                st = gpz.gpz_stage_times()
+                gpz.gpz_set_stage_timing(False)
+                c_ms = sum(st[k][0] for k in ("range", "qse", "scan", "compact") if k in st) / reps
+                d_ms = st.get("decompress", (0.0, 1))[0] / reps
+                points.append({"workload": name, "eb": eb, "G": G, "ratio": in_bytes / size,
+                               "bits_per_value": 8.0 * size / (n * F), "psnr_db": psnr, "max_err_over_eb": worst,
+                               "compress_gbs": in_bytes / c_ms / 1e6, "decompress_gbs": in_bytes / d_ms / 1e6})
+                del comp, out
+                torch.cuda.empty_cache()
+        del x, fields, dec
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "sweep", "unit": "GB/s of input; ratio = input / stream bytes",
+                      "data": "synthetic", "points": points}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -895,6 +984,9 @@ def main():
     elif args.workload == "served":
         if rank == 0:
             run_served(args)
+    elif args.workload == "sweep":
+        if rank == 0:
+            run_sweep(args)
     else:
         run_gpz(args, rank, world, local)
 

@@ -159,6 +159,19 @@ gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_f
 /* Static text for a status code. */
 const char* gpz_status_str(gpz_status s);
 
+/* Compaction form of later gpz_compress calls (per process; default 0).
+ *   0: Section 4.4's three steps: every block is encoded into a temporary
+ *      slot, a scan computes the offsets, a copy kernel moves the blocks.
+ *   1: fused compaction: every block publishes its size and looks back over
+ *      its predecessors' sizes (a decoupled look-back over blocks); a block
+ *      whose offset is known is written straight into the stream, and only
+ *      the others go through the temporary slots and the copy.  A block left
+ *      to the general path breaks the chain for the blocks behind it.
+ * The stream is the same byte for byte.  Word 8 of the compression workspace
+ * (bytes 32..35) holds, after a fused call, the number of blocks that were not
+ * placed directly (a diagnostic).  Returns the previous setting. */
+int gpz_set_fused_compaction(int enable);
+
 /* Measurement hooks.  When enabled (per process), every later call records
  * CUDA events on its stream before its first kernel and after each kernel
  * (up to 8192 events between reads).  gpz_stage_times synchronises on the

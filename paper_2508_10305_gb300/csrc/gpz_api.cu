@@ -26,7 +26,9 @@ namespace {
 
 constexpr uint64_t kAlign = 256;
 constexpr int kRangeGridMax = 152 * 8;  // range-pass CTAs: 8 per SM of a GB300 (full occupancy)
-constexpr uint64_t kCtrlBytes = 256;    // status, tile counter, range counter, out size
+constexpr uint64_t kCtrlBytes = 256;    // words: 0 status, 1 scan tile counter, 2 range counter,
+                                        // 3 general-list count, 4-5 out size, 8 blocks not placed
+                                        // directly (fused compaction)
 constexpr uint64_t kParamBytes = 256;   // FieldParams[8]
 
 uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * kBlock, 4); }
@@ -34,8 +36,10 @@ uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * k
 uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kScanTile; }
 
 struct WsLayout {
-    uint64_t ctrl, params, states, partials, sizes, list, temp, total, zero_bytes;
+    uint64_t ctrl, params, states, bstates, partials, sizes, list, temp, total, zero_bytes;
 };
+
+std::atomic<int> g_fused{0};  // gpz_set_fused_compaction
 
 WsLayout layout_of(uint64_t n, int F) {
     WsLayout L{};
@@ -47,7 +51,9 @@ WsLayout layout_of(uint64_t n, int F) {
     o += kParamBytes;
     L.states = o;
     o += align_up(ntiles_of(nb) * 8, kAlign);
-    L.zero_bytes = o;  // ctrl + params + look-back states are cleared per call
+    L.bstates = o;  // per-block look-back states of the fused compaction
+    o += align_up(nb * 8, kAlign);
+    L.zero_bytes = o;  // ctrl + params + both look-back state arrays are cleared per call
     L.partials = o;
     o += align_up((uint64_t)kRangeGridMax * F * sizeof(float2), kAlign);
     L.sizes = o;
@@ -84,6 +90,8 @@ uint64_t gpz_compress_workspace_size(uint64_t n, int F) {
 }
 
 uint64_t gpz_decompress_workspace_size(void) { return kCtrlBytes; }
+
+int gpz_set_fused_compaction(int enable) { return g_fused.exchange(enable ? 1 : 0); }
 
 const char* gpz_status_str(gpz_status s) {
     switch (s) {
@@ -243,14 +251,22 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         qa.status = status;
         qa.general_list = reinterpret_cast<uint32_t*>(ws + L.list);
         qa.general_count = status + 3;
+        const bool fused = g_fused.load() != 0;
+        const uint32_t table_start = (uint32_t)(kHeaderWords + 2 * F);
+        if (fused) {
+            const uint64_t payload_start = table_start + nb + 1;
+            qa.direct = static_cast<uint32_t*>(d_out) + payload_start;
+            qa.direct_capacity = out_capacity / 4 - payload_start;  // out_capacity >= the bound
+            qa.bstate = reinterpret_cast<unsigned long long*>(ws + L.bstates);
+            qa.deferred_count = status + 8;
+        }
         if (nb > 0) {
-            if ((rc = cuda_status(launch_qse(qa, s))) != GPZ_OK) break;
+            if ((rc = cuda_status(fused ? launch_qse_direct(qa, s) : launch_qse(qa, s))) != GPZ_OK) break;
             rec.mark("qse");
             ++g_launches;  // launch_qse enqueues two kernels: the fast path and the general list
         }
 
         uint32_t* stream_words = static_cast<uint32_t*>(d_out);
-        const uint32_t table_start = (uint32_t)(kHeaderWords + 2 * F);
         ScanArgs sa{};
         sa.sizes = qa.sizes;
         sa.nblocks = (uint32_t)nb;

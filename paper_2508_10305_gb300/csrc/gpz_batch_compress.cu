@@ -44,6 +44,10 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.status = g.chunk_status + c;
         A.general_list = g.general_list;
         A.general_count = g.general_count;
+        A.direct = nullptr;  // the batched form keeps the three-step compaction
+        A.direct_capacity = 0;
+        A.bstate = nullptr;
+        A.deferred_count = nullptr;
     }
 }
 

@@ -1,6 +1,8 @@
 // gpz_compact.cu -- steps 2 and 3 of GPZ's three-step compaction (Section
 // 4.4, Table 1 "C."): a device-level prefix sum of the per-block word counts,
-// then a copy of every block from its temporary slot to its final offset.
+// then a copy of every block from its temporary slot to its final offset --
+// except, with fused compaction, the blocks the fused kernel already wrote
+// into the stream (kPlaced in their word count).
 //
 // The prefix sum is a single-pass decoupled look-back scan: CTAs take tiles
 // in order from an atomic counter, publish their aggregate, then walk back
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kScanThreads) gpz_scan_kernel(ScanArgs a) {
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = min(v[k], start + k + 1 == a.nblocks ? raw_last : raw_full);
+        v[k] = min(v[k] & ~kPlaced, start + k + 1 == a.nblocks ? raw_last : raw_full);
         sum += v[k];
     }
     const uint32_t incl = warp_incl_sum(sum);
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
     }
     uint32_t* payload = a.stream + a.payload_start;
     for (uint32_t b = blockIdx.x * kCompactWarps + warp; b < a.nblocks; b += nwarps) {
+        if (__ldcg(a.sizes + b) & kPlaced) continue;  // written into the stream by the fused kernel
         const uint32_t len = __ldcg(a.table + b + 1) - __ldcg(a.table + b);  // clamped by the scan
         const uint32_t* src = a.temp + (size_t)b * a.slot_words;
         uint32_t* dst = payload + __ldcg(a.table + b);

@@ -66,7 +66,16 @@ struct QseArgs {
     uint32_t* status;
     uint32_t* general_list;     // [nblocks] blocks left to the general kernel
     uint32_t* general_count;    // zeroed
+    // Fused compaction only (gpz_qse_direct_kernel): the stream's payload,
+    // the words it can hold, the per-block look-back states (zeroed) and a
+    // count of the blocks that could not be placed directly.
+    uint32_t* direct;
+    uint64_t direct_capacity;
+    unsigned long long* bstate;
+    uint32_t* deferred_count;
 };
+
+constexpr uint32_t kPlaced = 0x80000000u;  // in a block's word count: already in the stream
 
 struct ScanArgs {
     const uint32_t* sizes;      // [nblocks]
@@ -277,7 +286,9 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // ---------------------------------------------------------------- launch wrappers (defined in the .cu files)
 
 cudaError_t launch_range(const RangeArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);
+cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);         // fast kernel, then the general list
+cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s);  // the same with blocks placed directly
+cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);

@@ -162,9 +162,15 @@ cudaError_t launch_qse_f(const QseArgs& a, cudaStream_t s) {
     gpz_qse_kernel<F><<<a.nblocks, kThreads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the blocks left to the general path (usually none); the grid walks the list
+    return launch_qse_general(a, s);
+}
+
+// the blocks left to the general path (usually none); the grid walks the list
+template <int F>
+cudaError_t launch_qse_general_f(const QseArgs& a, cudaStream_t s) {
     const size_t gsmem = qse_smem_bytes(F);
-    e = cudaFuncSetAttribute(gpz_qse_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(gpz_qse_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
     if (e != cudaSuccess) return e;
     const unsigned ggrid = a.nblocks < 2u * 152u ? a.nblocks : 2u * 152u;
     gpz_qse_general_kernel<F><<<ggrid, kThreads, gsmem, s>>>(a);
@@ -182,6 +188,21 @@ cudaError_t launch_qse(const QseArgs& a, cudaStream_t s) {
         case 6: return launch_qse_f<6>(a, s);
         case 7: return launch_qse_f<7>(a, s);
         case 8: return launch_qse_f<8>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s) {
+    if (a.nblocks == 0) return cudaSuccess;
+    switch (a.F) {
+        case 1: return launch_qse_general_f<1>(a, s);
+        case 2: return launch_qse_general_f<2>(a, s);
+        case 3: return launch_qse_general_f<3>(a, s);
+        case 4: return launch_qse_general_f<4>(a, s);
+        case 5: return launch_qse_general_f<5>(a, s);
+        case 6: return launch_qse_general_f<6>(a, s);
+        case 7: return launch_qse_general_f<7>(a, s);
+        case 8: return launch_qse_general_f<8>(a, s);
     }
     return cudaErrorInvalidValue;
 }

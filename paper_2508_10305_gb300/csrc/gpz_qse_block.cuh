@@ -536,7 +536,68 @@ struct QseFastShared {
     uint32_t flags;                 // bit 0: non-finite value, bit 1: a value needs a fallback candidate
     uint32_t maxcnt, maxdelta;
     uint32_t warp_tot[kWarps], warp_nz[kWarps];
+    uint32_t offset;                // fused compaction: the block's offset in the payload, or kNotPlaced
 };
+
+// ---- fused compaction (an alternative to Section 4.4's three steps):
+// every block publishes its size as soon as it is known, then looks back
+// over its predecessors' published sizes (a decoupled look-back over
+// blocks).  A block that finds its exclusive prefix writes itself into the
+// stream at once; the scan and copy kernels that follow then only fill the
+// offset table and move the other blocks.  A block left to the general path
+// has no size yet and breaks the chain, as does a predecessor that has not
+// published within the wait bound: the blocks behind it go to their
+// temporary slots as in the three-step form.
+constexpr unsigned long long kBlkAgg = 1ull << 62;     // size published, prefix not known
+constexpr unsigned long long kBlkIncl = 2ull << 62;    // inclusive prefix published
+constexpr unsigned long long kBlkBroken = 3ull << 62;  // no prefix will follow
+constexpr uint32_t kNotPlaced = 0xffffffffu;
+constexpr long long kLookbackCycles = 1ll << 17;       // about 60 us
+
+// Exclusive prefix of the sizes of blocks 0..b-1 (every lane of one warp),
+// or kNotPlaced when the chain is broken.
+static __device__ __noinline__ uint32_t block_lookback(const QseArgs& a, uint32_t b) {
+    const int lane = threadIdx.x & 31;
+    uint32_t excl = 0;
+    for (int base = (int)b - 1;; base -= 32) {
+        const int j = base - lane;
+        unsigned long long st = kBlkIncl;  // before block 0: prefix 0
+        if (j >= 0) {
+            const long long t0 = clock64();
+            for (;;) {
+                st = ld_acquire_u64(a.bstate + j);
+                if (st >> 62) break;
+                if (clock64() - t0 > kLookbackCycles) {
+                    st = kBlkBroken;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        const uint32_t flag = (uint32_t)(st >> 62);
+        const uint32_t stop = __ballot_sync(0xffffffffu, flag >= 2u);
+        if (stop) {  // the nearest predecessor with a prefix, or a break
+            const int first = __ffs(stop) - 1;
+            if (__shfl_sync(0xffffffffu, flag, first) == 3u) return kNotPlaced;
+            return excl + __reduce_add_sync(0xffffffffu, lane <= first ? (uint32_t)st : 0u);
+        }
+        excl += __reduce_add_sync(0xffffffffu, (uint32_t)st);
+    }
+}
+
+// A block stored raw (its words go to the temporary slot).  With fused
+// compaction it publishes its size and then, so that the blocks behind it
+// need not walk past it, its inclusive prefix (warp 0).
+template <int F, bool DIRECT>
+__device__ __forceinline__ void raw_block(const QseArgs& a, uint32_t b, int n_b, int t) {
+    const uint32_t raw_words = 1u + (uint32_t)F * (uint32_t)n_b;
+    if (DIRECT && t == 0) st_release_u64(a.bstate + b, (b == 0 ? kBlkIncl : kBlkAgg) | raw_words);
+    write_raw<F>(a, b, n_b, t);
+    if (DIRECT && b != 0 && (t >> 5) == 0) {
+        const uint32_t off = block_lookback(a, b);
+        if (t == 0) st_release_u64(a.bstate + b, off == kNotPlaced ? kBlkBroken : (kBlkIncl | (off + raw_words)));
+    }
+}
 
 // Whether every first candidate of a field's block is certain to pass the
 // verification |RN(x - RN(fma(q, s, min)))| <= ebchk, so that it need not be
@@ -591,7 +652,7 @@ __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool 
 
 // Block b of the array described by a; a block the fast path cannot take is
 // appended to a.general_list as list_id.
-template <int F, bool FULL, class Idx>
+template <int F, bool FULL, class Idx, bool DIRECT = false>
 __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, Idx idx) {
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -652,7 +713,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
     __syncthreads();  // A
     if (S.flags & 1u) {
-        write_raw<F>(a, idx.b(), n_b, t);
+        raw_block<F, DIRECT>(a, idx.b(), n_b, t);
         return;
     }
 
@@ -689,7 +750,10 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     if (big || W > kFastRecordBits) {
         // left to the general kernel (uniform decision)
-        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
+        if (t == 0) {
+            if (DIRECT) st_release_u64(a.bstate + idx.b(), kBlkBroken);
+            a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
+        }
         return;
     }
 
@@ -745,7 +809,10 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     __syncthreads();  // C
     if (S.flags & 2u) {
-        if (t == 0) a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
+        if (t == 0) {
+            if (DIRECT) st_release_u64(a.bstate + idx.b(), kBlkBroken);
+            a.general_list[atomicAdd(a.general_count, 1u)] = idx.id();
+        }
         return;
     }
 
@@ -829,9 +896,10 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     const uint32_t rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t enc = hdr + dwords + cwords + rwords;
     if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
-        write_raw<F>(a, idx.b(), n_b, t);
+        raw_block<F, DIRECT>(a, idx.b(), n_b, t);
         return;
     }
+    if (DIRECT && t == 0) st_release_u64(a.bstate + idx.b(), (idx.b() == 0 ? kBlkIncl : kBlkAgg) | enc);
 
     // ---- 5. block header and the three arrays (Section 4.3), assembled in the
     // staging words (zeroed now: they held the histograms) by thread-serial
@@ -886,17 +954,37 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         }
     }
     __syncthreads();
+    uint32_t off = kNotPlaced;
+    if constexpr (DIRECT) {  // the block's offset from its predecessors' sizes
+        if (w == 0) {
+            const uint32_t b = idx.b();
+            uint32_t o = b == 0 ? 0u : block_lookback(a, b);
+            if (o != kNotPlaced && (uint64_t)o + enc > a.direct_capacity) o = kNotPlaced;
+            if (lane == 0) {
+                if (b != 0) st_release_u64(a.bstate + b, o == kNotPlaced ? kBlkBroken : (kBlkIncl | (o + enc)));
+                if (o == kNotPlaced) atomicAdd(a.deferred_count, 1u);
+                S.offset = o;
+            }
+        }
+        __syncthreads();
+        off = S.offset;
+    }
     {
         const uint32_t b = idx.b();
-        uint32_t* out = a.temp + (size_t)b * a.slot_words;
-        const uint4* s4 = reinterpret_cast<const uint4*>(stage);
-        uint4* o4 = reinterpret_cast<uint4*>(out);
-        for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
-        for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+        if (off != kNotPlaced) {  // straight into the stream (word-aligned)
+            uint32_t* out = a.direct + off;
+            for (uint32_t k = t; k < enc; k += kThreads) out[k] = stage[k];
+        } else {
+            uint32_t* out = a.temp + (size_t)b * a.slot_words;
+            const uint4* s4 = reinterpret_cast<const uint4*>(stage);
+            uint4* o4 = reinterpret_cast<uint4*>(out);
+            for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
+            for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+        }
         const uint64_t first = (uint64_t)b * kBlock;
         if (a.perm)
             for (int j = t; j < n_b; j += kThreads) a.perm[first + j] = (uint32_t)first + sperm[j];
-        if (t == 0) a.sizes[b] = enc;
+        if (t == 0) a.sizes[b] = enc | (off != kNotPlaced ? kPlaced : 0u);
     }
 }
 

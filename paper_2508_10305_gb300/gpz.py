@@ -93,6 +93,8 @@ def _load():
     L.gpz_status_str.restype = C.c_char_p
     L.gpz_set_stage_timing.argtypes = [C.c_int]
     L.gpz_set_stage_timing.restype = None
+    L.gpz_set_fused_compaction.argtypes = [C.c_int]
+    L.gpz_set_fused_compaction.restype = C.c_int
     L.gpz_stage_times.argtypes = [P(C.c_char_p), P(C.c_float), P(C.c_int), C.c_int]
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
@@ -161,6 +163,16 @@ def gpz_status_str(status):
 
 def gpz_set_stage_timing(enable):
     lib.gpz_set_stage_timing(1 if enable else 0)
+
+
+def gpz_set_fused_compaction(enable):
+    """Select the compaction form of later gpz_compress calls; returns the previous one."""
+    return bool(lib.gpz_set_fused_compaction(1 if enable else 0))
+
+
+def compress_deferred_blocks(ws):
+    """After a fused-compaction call: the blocks that went through the copy kernel."""
+    return int(ws[32:36].view(torch.int32).item())
 
 
 def gpz_stage_times(max_stages=8):

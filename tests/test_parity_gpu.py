@@ -269,6 +269,68 @@ def test_lidar_200m_sampled(gpz, oracle):
     assert x.numel() * 4 / size > 2.0
 
 
+@pytest.fixture
+def fused(gpz):
+    prev = gpz.gpz_set_fused_compaction(True)
+    yield
+    gpz.gpz_set_fused_compaction(prev)
+
+
+@pytest.mark.parametrize("case", ["all_fast", "raw_blocks", "general_block"])
+def test_fused_compaction(gpz, oracle, fused, case):
+    """Fused compaction writes a block straight into the stream once every
+    block before it has published its size.  Raw blocks (non-finite values)
+    keep that chain going; a block left to the general path breaks it, and
+    the blocks behind it go through the temporary slots and the copy kernel.
+    Either way the stream is the oracle's, bit for bit."""
+    rng = np.random.default_rng({"all_fast": 1, "raw_blocks": 2, "general_block": 3}[case])
+    F, n = 3, 300_000
+    x = (rng.random((F, n)) * 256).astype(np.float32)
+    if case == "raw_blocks":
+        x[1, 2 * 1024 + 5] = np.nan
+        x[0, 40 * 1024 + 7] = np.inf
+    if case == "general_block":
+        x[0, 5 * 1024:6 * 1024] *= 1e5  # codes far above 2^23 at eb 1e-2: the general path
+    nb = (n + 1023) // 1024
+    xd = torch.from_numpy(x).cuda()
+    c = gpz.Compressor(n, F, 1e-2, 0, 3, want_perm=True)
+    size = c([xd[f] for f in range(F)])
+    torch.cuda.synchronize()
+    rs, rp = oracle.compress(x, 1e-2, 0, 3)
+    assert size == rs.size and np.array_equal(c.out[:size].cpu().numpy(), rs)
+    assert np.array_equal(c.perm[:n].cpu().numpy().astype(np.uint32), rp)
+    deferred = gpz.compress_deferred_blocks(c.ws)
+    if case == "general_block":
+        assert 0 < deferred <= nb - 6
+    else:
+        assert deferred == 0  # every block found its offset (ordinary launch order)
+
+
+@pytest.mark.parametrize("n,F,G,mode,kind,eb,seed", CASES[:16])
+def test_fused_compaction_random(gpz, oracle, fused, n, F, G, mode, kind, eb, seed):
+    rng = np.random.default_rng(seed)
+    assert_parity(gpz, oracle, gen(kind, F, n, rng), eb, mode, G)
+
+
+def test_fused_compaction_full_size(gpz):
+    """The 2^26 x 6 cosmology snapshot: the fused and the three-step
+    compaction write the same bytes."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.cosmology(1 << 26, seed=2, device="cuda")
+    F, n = x.shape
+    c = gpz.Compressor(n, F, 1e-4, gpz.EB_REL, 3)
+    size = c([x[f] for f in range(F)])
+    ref = c.out[:size].clone()
+    prev = gpz.gpz_set_fused_compaction(True)
+    try:
+        size2 = c([x[f] for f in range(F)])
+        deferred = gpz.compress_deferred_blocks(c.ws)
+    finally:
+        gpz.gpz_set_fused_compaction(prev)
+    assert size2 == size and torch.equal(c.out[:size], ref)
+    assert deferred < n // 1024 // 100
+
+
 def test_unchecked_first_candidates_boundary(gpz, oracle):
     """Blocks at the edge of the condition under which the fast path skips
     the check of first candidates (codes just below 2^15, ulp(max |x|) just
