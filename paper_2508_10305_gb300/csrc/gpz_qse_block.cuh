@@ -523,10 +523,10 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
 // Fast-path shared memory: the 128-bit sorted records, the unique ids and
 // counts, the sorted permutation, and the staging words of the encoded block,
 // whose first 8 KB hold the per-warp histograms until the scatter is done.
-constexpr uint32_t kFastRecords = 0u;
-constexpr uint32_t kFastUniq = kFastRecords + kBlock * 16u;
+constexpr uint32_t kFastHist = 0u;
+constexpr uint32_t kFastUniq = kFastHist + kHistBytes;
 constexpr uint32_t kFastStage = kFastUniq + kMaxBins * 2u + kMaxBins * 2u + kBlock * 2u;
-static_assert(kHistBytes <= kStageWords * 4u, "the histograms live in the staging words");
+static_assert(kFastStage % 16u == 0u && kStageWords % 4u == 0u, "the staging words are cleared 16 bytes at a time");
 
 __host__ __device__ constexpr uint32_t qse_fast_smem_bytes() { return kFastStage + kStageWords * 4u; }
 
@@ -535,7 +535,7 @@ struct QseFastShared {
     uint32_t maxkey[kMaxFields];
     uint32_t flags;                 // bit 0: non-finite value, bit 1: a value needs a fallback candidate
     uint32_t maxcnt, maxdelta;
-    uint32_t warp_tot[kWarps], warp_nz[kWarps];
+    uint32_t warp_tot[kWarps], warp_nz[kWarps], warp_last[kWarps];
     uint32_t offset;                // fused compaction: the block's offset in the payload, or kNotPlaced
 };
 
@@ -657,12 +657,11 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int n_b = FULL ? kBlock : (int)(a.n - (uint64_t)idx.b() * kBlock);
-    uint4* recs = reinterpret_cast<uint4*>(dsm + kFastRecords);             // [1024] 128-bit records
+    uint16_t* hist = reinterpret_cast<uint16_t*>(dsm + kFastHist);          // [8][512] per-warp histograms
     uint16_t* uniq = reinterpret_cast<uint16_t*>(dsm + kFastUniq);          // [512]
     uint16_t* cnt = uniq + kMaxBins;                                         // [512]
     uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
-    uint32_t* stage = reinterpret_cast<uint32_t*>(dsm + kFastStage);        // [kStageWords]
-    uint16_t* hist = reinterpret_cast<uint16_t*>(stage);                    // [8][512], until the scatter
+    uint32_t* stage = reinterpret_cast<uint32_t*>(dsm + kFastStage);        // [kStageWords] the encoded block
 
     if (t < F) {
         S.minkey[t] = 0xffffffffu;
@@ -677,6 +676,9 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         uint32_t* h32 = reinterpret_cast<uint32_t*>(hist + w * kMaxBins);
 #pragma unroll
         for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
+        // the encoded block is assembled by OR into cleared words
+        uint4* s4 = reinterpret_cast<uint4*>(stage);
+        for (uint32_t k = t; k < kStageWords / 4u; k += kThreads) s4[k] = make_uint4(0u, 0u, 0u, 0u);
     }
 
     // ---- 1. load (coalesced, streaming); block minimum and maximum
@@ -835,22 +837,34 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     const uint32_t incl_tot = warp_incl_sum(tot);
     const uint32_t incl_nz = warp_incl_sum(nz);
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
+    // the last non-empty bin up to this thread's (0 when none: a first id's
+    // delta is the id itself), for the deltas of the unique ids
+    uint32_t last = c1 ? (uint32_t)b0 + 1u : (c0 ? (uint32_t)b0 : 0u);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) last = max(last, __shfl_up_sync(0xffffffffu, last, o));
     if (lane == 31) {
         S.warp_tot[w] = incl_tot;
         S.warp_nz[w] = incl_nz;
+        S.warp_last[w] = last;
     }
     if (lane == 0) atomicMax(&S.maxcnt, cmax);
     __syncthreads();  // D
-    uint32_t base_tot = 0, base_nz = 0, U = 0;
+    uint32_t base_tot = 0, base_nz = 0, U = 0, prev = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
-        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww];
+        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww], vl = S.warp_last[ww];
         if (ww < w) {
             base_tot += vt;
             base_nz += vn;
+            prev = max(prev, vl);
         }
         U += vn;
     }
+    {
+        const uint32_t up = __shfl_up_sync(0xffffffffu, last, 1);
+        if (lane > 0) prev = max(prev, up);  // the last non-empty bin before b0
+    }
+    uint32_t dmax = 0;
     if (b0 < nbins) {
         const uint32_t start0 = base_tot + incl_tot - tot, start1 = start0 + c0;
         const uint32_t idx0 = base_nz + incl_nz - nz, idx1 = idx0 + (c0 ? 1u : 0u);
@@ -866,28 +880,12 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
             uniq[idx1] = (uint16_t)(b0 + 1);
             cnt[idx1] = (uint16_t)c1;
         }
+        if (c0) dmax = (uint32_t)b0 - prev;
+        if (c1) dmax = max(dmax, (uint32_t)b0 + 1u - (c0 ? (uint32_t)b0 : prev));
     }
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
     __syncthreads();  // E
-
-    // ---- 4c. scatter to sorted order; deltas of the unique ids
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (valid[r]) {
-            const uint32_t dest = myhist[key[r]] + rank[r];
-            recs[dest] = make_uint4(rw[r][0], rw[r][1], rw[r][2], rw[r][3]);
-            if (a.perm) sperm[dest] = (uint16_t)(128 * w + 32 * r + lane);
-        }
-    }
-    {
-        uint32_t dmax = 0;
-        for (uint32_t k = t; k < U; k += kThreads) {
-            const uint32_t d = (uint32_t)uniq[k] - (k ? (uint32_t)uniq[k - 1] : 0u);
-            dmax = max(dmax, d);
-        }
-        dmax = __reduce_max_sync(0xffffffffu, dmax);
-        if (lane == 0 && dmax) atomicMax(&S.maxdelta, dmax);
-    }
-    __syncthreads();  // F
 
     // ---- encoded size; raw when not smaller (keeps the bound size a bound)
     const uint32_t wd = bit_width(S.maxdelta), wc = bit_width(S.maxcnt);
@@ -902,10 +900,9 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     if (DIRECT && t == 0) st_release_u64(a.bstate + idx.b(), (idx.b() == 0 ? kBlkIncl : kBlkAgg) | enc);
 
     // ---- 5. block header and the three arrays (Section 4.3), assembled in the
-    // staging words (zeroed now: they held the histograms) by thread-serial
-    // appenders, then copied out
-    for (uint32_t k = t; k < enc; k += kThreads) stage[k] = 0u;
-    __syncthreads();
+    // staging words (cleared at the start) -- the deltas and counts by
+    // thread-serial appenders, the records each at its sorted position --
+    // then copied out
     if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
     if (t >= 1 && t <= F) {
         float m = 0.0f;
@@ -936,21 +933,22 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
             ap.finish(stage);
         }
     }
-    const uint32_t len = (uint32_t)n_b;
+    // the records: each thread ORs its own four at their sorted positions
     {
-        const uint32_t j0 = 4u * (uint32_t)t;
-        if (j0 < len && W) {
-            BitAppender ap(32u * (hdr + dwords + cwords) + j0 * W);
-            const uint32_t w0 = min(W, 32u), w1 = min(W - w0, 32u), w2 = min(W - w0 - w1, 32u), w3 = W - w0 - w1 - w2;
+        const uint32_t rbase = 32u * (hdr + dwords + cwords);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint4 v = (j0 + e < len) ? recs[j0 + e] : make_uint4(0u, 0u, 0u, 0u);
-                ap.put(stage, v.x, w0);
-                if (w1) ap.put(stage, v.y, w1);
-                if (w2) ap.put(stage, v.z, w2);
-                if (w3) ap.put(stage, v.w, w3);
-            }
-            ap.finish(stage);
+        for (int r = 0; r < 4; ++r) {
+            if (!valid[r]) continue;
+            const uint32_t dest = myhist[key[r]] + rank[r];  // sorted position
+            if (a.perm) sperm[dest] = (uint16_t)(128 * w + 32 * r + lane);
+            if (W == 0u) continue;
+            const uint32_t bp = rbase + dest * W, wi = bp >> 5, sh = bp & 31u, end = sh + W;
+            // the record is W bits, least significant word first, zero above W
+            atomicOr(stage + wi, rw[r][0] << sh);
+            if (end > 32u) atomicOr(stage + wi + 1, __funnelshift_l(rw[r][0], rw[r][1], sh));
+            if (end > 64u) atomicOr(stage + wi + 2, __funnelshift_l(rw[r][1], rw[r][2], sh));
+            if (end > 96u) atomicOr(stage + wi + 3, __funnelshift_l(rw[r][2], rw[r][3], sh));
+            if (end > 128u) atomicOr(stage + wi + 4, __funnelshift_l(rw[r][3], 0u, sh));
         }
     }
     __syncthreads();
