@@ -36,7 +36,7 @@ uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * k
 uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kScanTile; }
 
 struct WsLayout {
-    uint64_t ctrl, params, states, bstates, partials, sizes, list, temp, total, zero_bytes;
+    uint64_t ctrl, params, states, bstates, partials, bext, sizes, list, temp, total, zero_bytes;
 };
 
 std::atomic<int> g_fused{0};  // gpz_set_fused_compaction
@@ -56,6 +56,8 @@ WsLayout layout_of(uint64_t n, int F) {
     L.zero_bytes = o;  // ctrl + params + both look-back state arrays are cleared per call
     L.partials = o;
     o += align_up((uint64_t)kRangeGridMax * F * sizeof(float2), kAlign);
+    L.bext = o;  // each block's extremes from the range pass (relative bound)
+    o += align_up(nb * F * 8ull, kAlign);
     L.sizes = o;
     o += align_up(nb * 4, kAlign);
     L.list = o;
@@ -227,7 +229,8 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
             ra.partials = reinterpret_cast<float2*>(ws + L.partials);
             ra.done_counter = range_counter;
             ra.d_params = d_params;
-            uint64_t want = (n / 4 + kRangeThreads - 1) / kRangeThreads;
+            ra.bext = reinterpret_cast<uint2*>(ws + L.bext);
+            uint64_t want = (nb * F + kRangeThreads / 32 - 1) / (kRangeThreads / 32);  // a warp per (block, field)
             const int grid = (int)(want < 1 ? 1 : (want > (uint64_t)kRangeGridMax ? kRangeGridMax : want));
             if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
             rec.mark("range");
@@ -244,6 +247,7 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         qa.G = p->seg_bits;
         qa.bulk_ok = vec_ok ? 1 : 0;
         qa.d_params = rel ? d_params : nullptr;
+        qa.bext = rel ? reinterpret_cast<const uint2*>(ws + L.bext) : nullptr;
         qa.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
         qa.slot_words = slot_words_of(F);
         qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);

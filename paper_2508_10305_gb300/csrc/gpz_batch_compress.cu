@@ -37,6 +37,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.G = ch->G;
         A.bulk_ok = ch->bulk_ok;
         A.d_params = nullptr;
+        A.bext = nullptr;  // the fused kernel finds each block's extremes itself
         A.temp = g.temp + ch->temp_base;
         A.slot_words = batch_slot_words(ch->F);
         A.sizes = g.sizes + base;

@@ -48,6 +48,7 @@ struct RangeArgs {
     float2* partials;           // [gridDim.x][F] (min, max)
     uint32_t* done_counter;
     FieldParams* d_params;      // out
+    uint2* bext;                // out, [nblocks][F]: each block's extremes (order keys), (0, 0) if non-finite
 };
 
 struct QseArgs {
@@ -59,6 +60,7 @@ struct QseArgs {
     int bulk_ok;                // every field pointer 16-byte aligned: stage tiles with bulk copies
     FieldParams params[kMaxFields];
     const FieldParams* d_params; // device constants (relative bound) or nullptr
+    const uint2* bext;          // each block's extremes from the range pass, or nullptr
     uint32_t* temp;             // [nblocks][slot_words]
     uint32_t slot_words;
     uint32_t* sizes;            // [nblocks] words per block
@@ -289,6 +291,7 @@ cudaError_t launch_range(const RangeArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);         // fast kernel, then the general list
 cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s);  // the same with blocks placed directly
 cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
+cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);

@@ -7,7 +7,9 @@
 // Thread (warp w, lane l) owns elements 128w + 32r + l, r = 0..3, so that each
 // warp covers 128 consecutive particles in storage order.  Per CTA:
 //   1. coalesced streaming loads; per-field exact fp32 minimum (Section 4.1:
-//      per-thread, then warp reduction, then a shared atomic per warp);
+//      per-thread, then warp reduction, then a shared atomic per warp), or,
+//      with a relative bound, the block's extremes the range pass already
+//      found (gpz_qse_pre.cu);
 //   2. quantisation q = floor(fma(x - min, 1/s, 1/2)) with the stream
 //      format's fp32 verification (skipped for blocks where it provably
 //      passes); blocks that need a fallback candidate, codes >= 2^23 or
@@ -22,11 +24,10 @@
 //      histogram; a CTA-wide scan over (bin, warp) gives every element its
 //      sorted position.  The non-empty bins are the run-length code (unique
 //      ids and counts, Section 4.3);
-//   5. fixed-length coding (Section 4.3): the sorted records are scattered
-//      to shared memory, and each thread packs its run of deltas, counts and
-//      records into zeroed staging words with a thread-serial bit appender
-//      (words shared with a neighbour are merged with atomicOr); the
-//      encoded block is copied out with 16-byte stores;
+//   5. fixed-length coding (Section 4.3) into staging words cleared at the
+//      start: the deltas and counts by thread-serial bit appenders, each
+//      record ORed in by its own thread at its sorted position; the encoded
+//      block is copied out with 16-byte stores;
 //   6. the block goes to its temporary slot with its word count (step 1 of
 //      the three-step compaction, Section 4.4).
 #include "gpz_qse_block.cuh"
@@ -35,55 +36,71 @@ namespace gpz {
 
 // ------------------------------------------------------------------ range pass (relative bound)
 
-__global__ void __launch_bounds__(kRangeThreads) gpz_range_kernel(RangeArgs a) {
+// One warp per (block, field) item, field-major, so that consecutive warps
+// stream consecutive blocks of a field.  Each item yields the block's
+// extremes for the fused kernel (order keys; (0, 0) when the block holds a
+// NaN or an infinity in that field) and feeds the CTA's running extremes of
+// the field over its non-NaN values.
+__global__ void __launch_bounds__(kRangeThreads, 8) gpz_range_kernel(RangeArgs a) {
     __shared__ float2 red[kRangeThreads / 32];
+    __shared__ uint32_t s_lo[kMaxFields], s_hi[kMaxFields];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int f = 0; f < a.F; ++f) {
-        const float* x = a.fields[f];
-        float lo = INFINITY, hi = -INFINITY;
-        if (a.vec_ok) {
+    if (tid < kMaxFields) {
+        s_lo[tid] = 0xffffffffu;
+        s_hi[tid] = 0u;
+    }
+    __syncthreads();
+    const uint64_t nb = (a.n + kBlock - 1) / kBlock;
+    const uint64_t items = nb * (uint64_t)a.F;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kRangeThreads / 32);
+    for (uint64_t it = (uint64_t)blockIdx.x * (kRangeThreads / 32) + warp; it < items; it += nwarps) {
+        const int f = (int)(it / nb);
+        const uint64_t b = it - (uint64_t)f * nb;
+        const float* x = a.fields[f] + b * kBlock;
+        const int n_b = (int)min((uint64_t)kBlock, a.n - b * kBlock);
+        float lo = INFINITY, hi = -INFINITY, probe = 0.0f;  // probe: NaN if any value is NaN or infinite
+        if (a.vec_ok && n_b == kBlock) {  // 256 16-byte words: two rounds of four loads in flight per lane
             const float4* x4 = reinterpret_cast<const float4*>(x);
-            const uint64_t n4 = a.n >> 2;
-            const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-            uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid;
-            for (; i + 3 * stride < n4; i += 4 * stride) {  // four 16-byte loads in flight per thread
-                const float4 v0 = __ldcs(x4 + i), v1 = __ldcs(x4 + i + stride), v2 = __ldcs(x4 + i + 2 * stride),
-                             v3 = __ldcs(x4 + i + 3 * stride);
-                lo = fminf(lo, fminf(fminf(fminf(v0.x, v0.y), fminf(v0.z, v0.w)), fminf(fminf(v1.x, v1.y), fminf(v1.z, v1.w))));
-                lo = fminf(lo, fminf(fminf(fminf(v2.x, v2.y), fminf(v2.z, v2.w)), fminf(fminf(v3.x, v3.y), fminf(v3.z, v3.w))));
-                hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v0.x, v0.y), fmaxf(v0.z, v0.w)), fmaxf(fmaxf(v1.x, v1.y), fmaxf(v1.z, v1.w))));
-                hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v2.x, v2.y), fmaxf(v2.z, v2.w)), fmaxf(fmaxf(v3.x, v3.y), fmaxf(v3.z, v3.w))));
-            }
-            for (; i < n4; i += stride) {
-                const float4 v = __ldcs(x4 + i);
-                lo = fminf(fminf(lo, v.x), fminf(v.y, fminf(v.z, v.w)));
-                hi = fmaxf(fmaxf(hi, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
-            }
-            for (uint64_t i = (n4 << 2) + (uint64_t)blockIdx.x * blockDim.x + tid; i < a.n;
-                 i += (uint64_t)gridDim.x * blockDim.x) {
-                float v = x[i];
-                lo = fminf(lo, v);
-                hi = fmaxf(hi, v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float4 v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = __ldcs(x4 + lane + 32 * (4 * h + k));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    lo = fminf(lo, fminf(fminf(v[k].x, v[k].y), fminf(v[k].z, v[k].w)));
+                    hi = fmaxf(hi, fmaxf(fmaxf(v[k].x, v[k].y), fmaxf(v[k].z, v[k].w)));
+                    probe = __fmaf_rn(v[k].x, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].y, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].z, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].w, 0.0f, probe);
+                }
             }
         } else {
-            for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
-                float v = x[i];
+            for (int i = lane; i < n_b; i += 32) {
+                const float v = __ldcs(x + i);
                 lo = fminf(lo, v);
                 hi = fmaxf(hi, v);
+                probe = __fmaf_rn(v, 0.0f, probe);
             }
         }
         lo = warp_min_f32(lo);
         hi = warp_max_f32(hi);
-        if (lane == 0) red[warp] = make_float2(lo, hi);
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < kRangeThreads / 32; ++w) {
-                lo = fminf(lo, red[w].x);
-                hi = fmaxf(hi, red[w].y);
+        const bool nonfinite = __any_sync(0xffffffffu, probe != probe);
+        if (lane == 0) {
+            a.bext[b * (uint64_t)a.F + f] = nonfinite ? make_uint2(0u, 0u) : make_uint2(order_key(lo), order_key(hi));
+            if (lo <= hi) {  // some value is not NaN
+                atomicMin(&s_lo[f], order_key(lo));
+                atomicMax(&s_hi[f], order_key(hi));
             }
-            a.partials[(size_t)blockIdx.x * a.F + f] = make_float2(lo, hi);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (tid < a.F) {
+        const uint32_t kl = s_lo[tid], kh = s_hi[tid];
+        const bool any = kl != 0xffffffffu || kh != 0u;
+        a.partials[(size_t)blockIdx.x * a.F + tid] =
+            any ? make_float2(from_order_key(kl), from_order_key(kh)) : make_float2(INFINITY, -INFINITY);
     }
     // The last CTA to finish folds the partials and finalises the constants.
     __shared__ bool last;
@@ -179,6 +196,7 @@ cudaError_t launch_qse_general_f(const QseArgs& a, cudaStream_t s) {
 
 cudaError_t launch_qse(const QseArgs& a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
+    if (a.bext) return launch_qse_pre(a, s);
     switch (a.F) {
         case 1: return launch_qse_f<1>(a, s);
         case 2: return launch_qse_f<2>(a, s);

@@ -652,7 +652,9 @@ __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool 
 
 // Block b of the array described by a; a block the fast path cannot take is
 // appended to a.general_list as list_id.
-template <int F, bool FULL, class Idx, bool DIRECT = false>
+// PRE: the range pass has already found each block's extremes (a.bext);
+// otherwise the block finds them itself.
+template <int F, bool FULL, class Idx, bool DIRECT = false, bool PRE = false>
 __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, Idx idx) {
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -663,7 +665,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     uint16_t* sperm = cnt + kMaxBins;                                        // [1024]
     uint32_t* stage = reinterpret_cast<uint32_t*>(dsm + kFastStage);        // [kStageWords] the encoded block
 
-    if (t < F) {
+    if (!PRE && t < F) {
         S.minkey[t] = 0xffffffffu;
         S.maxkey[t] = 0u;
     }
@@ -692,31 +694,54 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
 #pragma unroll
         for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
     }
-    __syncthreads();  // shared reduction slots initialised (the loads are in flight)
-    float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+    uint32_t kmin[F], kmax[F];  // the block's extremes, as order keys
+    if constexpr (PRE) {  // from the range pass; (0, 0) marks a non-finite value
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-        float lo = INFINITY, hi = -INFINITY;
+        for (int f = 0; f < F; ++f) {
+            const uint2 e = __ldg(a.bext + (size_t)idx.b() * F + f);
+            kmin[f] = e.x;
+            kmax[f] = e.y;
+        }
+        __syncthreads();  // shared counters initialised (the loads are in flight)
+        bool nonfinite = false;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            if (valid[r]) {
-                probe = __fmaf_rn(x[f][r], 0.0f, probe);
-                lo = fminf(lo, x[f][r]);
-                hi = fmaxf(hi, x[f][r]);
+        for (int f = 0; f < F; ++f) nonfinite |= kmin[f] == 0u;
+        if (nonfinite) {  // uniform: every thread read the same extremes
+            raw_block<F, DIRECT>(a, idx.b(), n_b, t);
+            return;
+        }
+    } else {
+        __syncthreads();  // shared reduction slots initialised (the loads are in flight)
+        float probe = 0.0f;  // becomes NaN if any value is NaN or infinite (x * 0)
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (valid[r]) {
+                    probe = __fmaf_rn(x[f][r], 0.0f, probe);
+                    lo = fminf(lo, x[f][r]);
+                    hi = fmaxf(hi, x[f][r]);
+                }
+            }
+            const uint32_t lk = __reduce_min_sync(0xffffffffu, lo == INFINITY ? 0xffffffffu : order_key(lo));
+            const uint32_t hk = __reduce_max_sync(0xffffffffu, hi == -INFINITY ? 0u : order_key(hi));
+            if (lane == 0) {
+                atomicMin(&S.minkey[f], lk);
+                atomicMax(&S.maxkey[f], hk);
             }
         }
-        const uint32_t lk = __reduce_min_sync(0xffffffffu, lo == INFINITY ? 0xffffffffu : order_key(lo));
-        const uint32_t hk = __reduce_max_sync(0xffffffffu, hi == -INFINITY ? 0u : order_key(hi));
-        if (lane == 0) {
-            atomicMin(&S.minkey[f], lk);
-            atomicMax(&S.maxkey[f], hk);
+        if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
+        __syncthreads();  // A
+        if (S.flags & 1u) {
+            raw_block<F, DIRECT>(a, idx.b(), n_b, t);
+            return;
         }
-    }
-    if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
-    __syncthreads();  // A
-    if (S.flags & 1u) {
-        raw_block<F, DIRECT>(a, idx.b(), n_b, t);
-        return;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            kmin[f] = S.minkey[f];
+            kmax[f] = S.maxkey[f];
+        }
     }
 
     // ---- 2. widths from the block maxima: q0 = floor(fma(x - min, 1/s, 1/2))
@@ -730,8 +755,8 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
-            const float m = from_order_key(S.minkey[f]);
-            const float mx = from_order_key(S.maxkey[f]);
+            const float m = from_order_key(kmin[f]);
+            const float mx = from_order_key(kmax[f]);
             mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
             const float tq = __fmaf_rn(__fsub_rn(mx, mn[f]), p.inv, 0.5f);
             big |= !(tq < 8388608.0f);

@@ -8,28 +8,33 @@
 
 namespace gpz {
 
-template <int F>
+template <int F, bool PRE>
 __global__ void __launch_bounds__(kThreads, 5) gpz_qse_direct_kernel(QseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
-        qse_block_fast<F, true, GridBlock, true>(a, dsm, S, GridBlock{});
+        qse_block_fast<F, true, GridBlock, true, PRE>(a, dsm, S, GridBlock{});
     else
-        qse_block_fast<F, false, GridBlock, true>(a, dsm, S, GridBlock{});
+        qse_block_fast<F, false, GridBlock, true, PRE>(a, dsm, S, GridBlock{});
+}
+
+template <int F, bool PRE>
+cudaError_t launch_qse_direct_fp(const QseArgs& a, cudaStream_t s) {
+    const size_t smem = qse_fast_smem_bytes();
+    cudaError_t e =
+        cudaFuncSetAttribute(gpz_qse_direct_kernel<F, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gpz_qse_direct_kernel<F, PRE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    gpz_qse_direct_kernel<F, PRE><<<a.nblocks, kThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_qse_general(a, s);
 }
 
 template <int F>
 cudaError_t launch_qse_direct_f(const QseArgs& a, cudaStream_t s) {
-    const size_t smem = qse_fast_smem_bytes();
-    cudaError_t e =
-        cudaFuncSetAttribute(gpz_qse_direct_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gpz_qse_direct_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    gpz_qse_direct_kernel<F><<<a.nblocks, kThreads, smem, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_qse_general(a, s);
+    return a.bext ? launch_qse_direct_fp<F, true>(a, s) : launch_qse_direct_fp<F, false>(a, s);
 }
 
 cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s) {
