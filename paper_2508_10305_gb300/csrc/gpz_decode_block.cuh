@@ -208,18 +208,26 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         header_fits && payload_start + payload_words <= a.total_words && off <= end && end <= payload_words;
     const uint32_t* blk = Sw + payload_start + off;
     const uint32_t nw = end - off;
-    // round trip 2: the block's words after its header, staged in shared
-    // memory (all of them when they fit; the deltas and counts always fit)
+    // round trip 2: warp 0 fetches the stream header, the block header and the
+    // steps (all in bounds once the block is inside the stream), and every
+    // warp stages the block's words after its header in shared memory (all of
+    // them when they fit; the deltas and counts always fit)
+    uint32_t hv = 0, bw = 0;
+    float step = 0.0f;
+    if (w == 0) {
+        if (lane < kHeaderWords) hv = __ldg(Sw + lane);  // the host checked total_words >= kHeaderWords
+        if (inside && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
+        if (header_fits && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
+    }
     if (inside && nw > hdr) {
         const uint32_t nst = min(nw - hdr, kDecStageWords);
         for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
     }
 
-    // ---- the format checks and the block's constants: warp 0 alone, into
-    // shared memory (the other warps go straight on to the barrier)
+    // ---- the format checks and the block's constants: warp 0 alone, from the
+    // words it fetched above, into shared memory (the other warps go straight
+    // on to the barrier)
     if (w == 0) {
-        uint32_t hv = 0;
-        if (lane < kHeaderWords) hv = __ldg(Sw + lane);  // the host checked total_words >= kHeaderWords
         bool ok = true;
         switch (lane) {
             case 0: ok = hv == kMagic; break;
@@ -237,11 +245,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         const uint32_t G = __shfl_sync(0xffffffffu, hv, 3);
         ok = __all_sync(0xffffffffu, ok) && inside && !(b == 0 && off != 0) &&
              !(b + 1 == a.nblocks && end != payload_words) && end != off;
-        // the block header (mode word, minima, width bytes) and the steps
-        uint32_t bw = 0;
-        if (ok && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
-        float step = 0.0f;
-        if (ok && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
+        // the block header: mode word, minima, width bytes
         const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
         const bool raw = ok && (mode & 1u);
         if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
