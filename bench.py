@@ -52,6 +52,7 @@ N_FIELDS = 6
 REL_EB = 1e-4
 SEG_BITS = 3
 SEED = 2
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
 WORKLOAD = "cosmology-like snapshot: 2^26 particles x 6 fp32 (x,y,z,vx,vy,vz), 20,000 halos + 30% background, relative eb 1e-4"
 
 
@@ -242,6 +243,39 @@ def cpu_oracle_sample(x_host_blocks, n_fields):
     return x_host_blocks.nbytes / (t2 - t0) / 1e9, t1 - t0, t2 - t1
 
 
+def cpu_oracle_threads(x_host, n_fields, threads):
+    """The oracle, unchanged, over `threads` host threads: each compresses and
+    then decompresses a contiguous range of whole blocks (blocks are
+    independent).  The relative bound is first turned into each field's
+    absolute bound over the whole array, as the oracle itself computes it, so
+    every block is encoded as in one call on the whole array.  ctypes releases
+    the interpreter lock during the C calls.  Returns (GB/s of input per round
+    trip, wall seconds, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import gpz_oracle
+    gpz_oracle.lib()
+    F, n = x_host.shape
+    ebs = []
+    for f in range(F):
+        v = x_host[f][~np.isnan(x_host[f])]
+        rng = float(v.max()) - float(v.min()) if v.size else 0.0
+        e = REL_EB * rng
+        ebs.append(e if (0.0 < rng < float("inf") and 0.0 < e < float("inf")) else REL_EB)
+    nb = (n + 1023) // 1024
+    cuts = [min(n, (nb * k // threads) * 1024) for k in range(threads + 1)]
+    parts = [np.ascontiguousarray(x_host[:, cuts[k]:cuts[k + 1]]) for k in range(threads) if cuts[k + 1] > cuts[k]]
+
+    def work(part):
+        stream, _ = gpz_oracle.compress(part, ebs, 0, SEG_BITS, want_perm=False)
+        gpz_oracle.decompress(stream, n_fields, part.shape[1])
+
+    with ThreadPoolExecutor(len(parts)) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(work, parts))
+        dt = time.perf_counter() - t0
+    return x_host.nbytes / dt / 1e9, dt, len(parts)
+
+
 def host_sample(x_dev, every=4):
     """Every `every`-th 1024-particle block of the device workload, on the host."""
     import torch
@@ -255,10 +289,11 @@ def host_sample(x_dev, every=4):
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
-    """The CPU oracle as it stands, single-threaded on the host, on the same
-    workload, metric and unit.  Each step is a bounded sample of whole
-    1024-particle blocks spread over the snapshot (rotating offset), sized so
-    that all steps together take about 90 s."""
+    """The CPU oracle as it stands, on the host's cores (one thread per core,
+    each on a contiguous range of whole blocks), on the same workload, metric
+    and unit.  Each step is a bounded sample of whole 1024-particle blocks
+    spread over the snapshot (rotating offset), sized so that all steps
+    together take about 90 s of single-core work per core."""
     if rank != 0:
         return
     import torch
@@ -266,7 +301,8 @@ def run_reference(args, rank, world):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     x = synth.cosmology(args.n, seed=SEED, device=dev)
     nb = args.n // 1024
-    per_step = int(max(8, min(nb, 90.0 * 1.4e6 / max(1, args.steps) / 1024)))
+    nthreads = os.cpu_count() or 1
+    per_step = int(max(8 * nthreads, min(nb, nthreads * 90.0 * 1.4e6 / max(1, args.steps) / 1024)))
     stride = max(1, nb // per_step)
 
     def sample(i):
@@ -275,12 +311,12 @@ def run_reference(args, rank, world):
         return x[:, sel].cpu().numpy()
 
     for i in range(args.warmup):
-        cpu_oracle_sample(sample(i)[:, :1 << 14], N_FIELDS)
-    total, nbytes = 0.0, 0
+        cpu_oracle_threads(sample(i)[:, :nthreads << 14], N_FIELDS, nthreads)
+    total, nbytes, used = 0.0, 0, 1
     for i in range(args.steps):
         s = sample(i)
-        _, tc, td = cpu_oracle_sample(s, N_FIELDS)
-        total += tc + td
+        _, dt, used = cpu_oracle_threads(s, N_FIELDS, nthreads)
+        total += dt
         nbytes += s.nbytes
     value = nbytes / total / 1e9
     line = {
@@ -290,10 +326,10 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": args.n, "fields": N_FIELDS, "eb_mode": "rel", "eb": REL_EB,
                    "seg_bits": SEG_BITS},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": used, "kind": "oracle",
                          "sample": "per step %d whole 1024-particle blocks (every %dth, rotating offset) x 6 "
-                                   "fields; single-threaded C++ oracle compress + decompress; relative eb over "
-                                   "the sample" % (per_step, stride)},
+                                   "fields; C++ oracle compress + decompress over %d host threads by block "
+                                   "range; relative eb over the sample" % (per_step, stride, used)},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -401,7 +437,8 @@ def run_gpz(args, rank, world, local):
     roofline = {"bound": "hbm", "kernel": "gpz_%s_kernel" % dom, "achieved": kernels[dom]["achieved_gbs"],
                 "peak": peak, "unit": "GB/s", "frac": kernels[dom]["frac"],
                 "traffic": recorded_traffic(dom), "peak_source": peak_kind,
-                "note": "frac of %s copy bandwidth" % peak_kind}
+                "note": "frac of %s copy bandwidth" % peak_kind,
+                "frac_of_nominal": kernels[dom]["achieved_gbs"] / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS}
 
     result = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -562,11 +599,18 @@ def run_gpz(args, rank, world, local):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, npart = host_sample(x, every=4)
-        gbs, tc, td = cpu_oracle_sample(sample, F)
-        result["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                  "sample": "every 4th 1024-particle block (%d particles x 6 fields), one "
-                                            "compress + decompress, single-threaded C++ oracle, relative eb "
-                                            "over the sample; %.1f s" % (npart, tc + td)}
+        gbs1, tc, td = cpu_oracle_sample(sample, F)
+        nthreads = os.cpu_count() or 1
+        whole, _ = host_sample(x, every=1)
+        gbs, dt, used = cpu_oracle_threads(whole, F, nthreads)
+        result["cpu_baseline"] = {
+            "value": gbs, "unit": "GB/s", "cores": used, "kind": "oracle",
+            "sample": "the whole snapshot (%d particles x 6 fields), one compress + decompress, the C++ oracle "
+                      "over %d host threads by contiguous block ranges, relative eb over the snapshot; %.1f s"
+                      % (whole.shape[1], used, dt),
+            "single_thread": {"value": gbs1, "cores": 1,
+                              "sample": "every 4th 1024-particle block (%d particles x 6 fields), relative eb "
+                                        "over the sample; %.1f s" % (npart, tc + td)}}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
