@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-compaction comparison")
+    ap.add_argument("--no-aos", action="store_true", help="skip the interleaved-records round trip")
     ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served", "sweep"])
     ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
@@ -485,6 +486,57 @@ def run_gpz(args, rank, world, local):
             "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st_f.items()},
             "blocks_not_placed": deferred, "blocks": (n + 1023) // 1024, "same_stream": same}
         del ref_stream
+
+    # interleaved records (gpz_compress_aos / gpz_decompress_aos: a transpose
+    # around the same kernels) on the same snapshot, particle-major
+    if not args.no_aos:
+        import ctypes as C
+        x_aos = x.t().contiguous()
+        params = gpz.make_params(F, REL_EB, gpz.EB_REL, SEG_BITS)
+        cap = gpz.gpz_bound_size(n, F)
+        a_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        a_size = torch.zeros(1, dtype=torch.int64, device=dev)
+        cws = gpz.gpz_compress_aos_workspace_size(n, F)
+        dws = gpz.gpz_decompress_aos_workspace_size(n, F)
+        a_cws = torch.empty(cws, dtype=torch.uint8, device=dev)
+        a_dws = torch.zeros(dws, dtype=torch.uint8, device=dev)
+        a_rec = torch.empty((n, F), dtype=torch.float32, device=dev)
+        hs = gpz._stream_handle(stream)
+
+        def aos_step():
+            st1 = gpz.lib.gpz_compress_aos(x_aos.data_ptr(), n, C.byref(params), a_out.data_ptr(), cap,
+                                           a_size.data_ptr(), None, None, a_cws.data_ptr(), cws, hs)
+            st2 = gpz.lib.gpz_decompress_aos(a_out.data_ptr(), size, a_rec.data_ptr(), F, n, a_dws.data_ptr(), dws,
+                                             hs)
+            if st1 != gpz.OK or st2 != gpz.OK:
+                raise gpz.GpzError(st1 or st2, "aos round trip")
+
+        for _ in range(args.warmup):
+            aos_step()
+        torch.cuda.synchronize()
+        same_aos = int(a_size.item()) == size and bool(torch.equal(a_out[:size], comp.out[:size]))
+        ka = min(args.steps, 60)
+        gpz.gpz_set_stage_timing(True)
+        gpz.gpz_stage_times()
+        ev0.record(stream)
+        for _ in range(ka):
+            aos_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        st_a = gpz.gpz_stage_times()
+        gpz.gpz_set_stage_timing(False)
+        for wsb in (a_cws, a_dws):
+            stc = gpz.gpz_sync_status(wsb)
+            if stc != gpz.OK:
+                raise gpz.GpzError(stc, "aos round trip (device)")
+        ms_a = ranks_max([ev0.elapsed_time(ev1) / ka], dev)[0]
+        tr = st_a.get("aos", (0.0, 1))
+        result["aos"] = {"value": job_gbs(world, in_bytes, 1, ms_a / 1e3), "unit": "GB/s", "ms_per_step": ms_a,
+                         "steps": ka, "transpose_ms": tr[0] / max(tr[1], 1),
+                         "transpose_gbs": 2 * in_bytes / (tr[0] / max(tr[1], 1)) / 1e6 if tr[0] else None,
+                         "same_stream": same_aos,
+                         "records_checked": bool(torch.equal(a_rec.t(), dec(comp.out, size)))}
+        del x_aos, a_out, a_cws, a_dws, a_rec
 
     # end to end through the public API with host buffers: H2D input ->
     # compress -> D2H stream -> H2D stream -> decompress -> D2H output, every

@@ -156,6 +156,29 @@ gpz_status gpz_sync_status(void* d_ws, void* stream);
 gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_fields,
                        int* seg_bits, int* mode);
 
+/* Interleaved (array-of-structures) input and output: particle i's fields at
+ * d_aos[i*F .. i*F+F-1], the layout of LAS-style point records (4-byte
+ * aligned).  A transpose kernel moves the records to structure-of-arrays
+ * form in the workspace before compression (and back after decompression),
+ * around gpz_compress / gpz_decompress, so the stream is the one gpz_compress
+ * writes for the same values, and decompressed particle j (block-sorted
+ * order) is d_aos[j*F ..].
+ *   d_ws/ws_size: workspace (256-byte aligned) of at least
+ *       gpz_compress_aos_workspace_size(n, F) / gpz_decompress_aos_workspace_size(n, F)
+ *       bytes (4*n*F more than the ordinary calls), or NULL to let the library
+ *       allocate and free it (the call then synchronises and returns the
+ *       device-side status).  With a workspace, gpz_sync_status(d_ws) reads the
+ *       device-side status as for the ordinary calls.
+ * Other arguments, errors and ordering as gpz_compress / gpz_decompress.
+ * The workspace sizes are 0 for n_fields outside 1..8. */
+uint64_t gpz_compress_aos_workspace_size(uint64_t n, int n_fields);
+uint64_t gpz_decompress_aos_workspace_size(uint64_t n, int n_fields);
+gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p, void* d_out,
+                            uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size,
+                            uint32_t* d_perm, void* d_ws, uint64_t ws_size, void* stream);
+gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, int n_fields,
+                              uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
+
 /* Static text for a status code. */
 const char* gpz_status_str(gpz_status s);
 

@@ -1,0 +1,188 @@
+// gpz_aos.cu -- interleaved (array-of-structures) input and output: particle
+// i's fields at aos[i*F .. i*F+F-1], the layout of LAS-style point records.
+// A transpose kernel moves the records to structure-of-arrays form in the
+// workspace before compression (and back after decompression), around the
+// ordinary entry points, so the stream is the one gpz_compress writes for the
+// same values.  Both transposes are HBM-bound copies staged through shared
+// memory: one CTA per tile of 1024 particles, contiguous reads of the tile's
+// records and contiguous writes of each field's run (or the reverse).
+#include "gpz.h"
+#include "gpz_host.hpp"
+#include "gpz_internal.cuh"
+
+using namespace gpz;
+using namespace gpz::host;
+
+namespace gpz {
+
+constexpr int kAosTile = 1024;     // particles per tile
+constexpr int kAosThreads = 256;
+
+// soa[f * ld + i] = aos[i * F + f] for i < n
+__global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float* __restrict__ aos,
+                                                                     float* __restrict__ soa, uint64_t n, int F,
+                                                                     uint64_t ld) {
+    __shared__ float tile[kAosTile * kMaxFields + kMaxFields];
+    const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
+    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const uint64_t first = tl * kAosTile;
+        const int cnt = (int)min((uint64_t)kAosTile, n - first);
+        const int words = cnt * F;
+        const float* src = aos + first * (uint64_t)F;
+        for (int k = threadIdx.x; k < words; k += kAosThreads) {
+            const int i = k / F, f = k - i * F;
+            tile[f * (kAosTile + 1) + i] = __ldcs(src + k);  // field-major in shared memory, padded rows
+        }
+        __syncthreads();
+        for (int f = 0; f < F; ++f)
+            for (int i = threadIdx.x; i < cnt; i += kAosThreads) soa[(uint64_t)f * ld + first + i] = tile[f * (kAosTile + 1) + i];
+        __syncthreads();
+    }
+}
+
+// aos[i * F + f] = soa[f * ld + i] for i < n
+__global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float* __restrict__ soa,
+                                                                     float* __restrict__ aos, uint64_t n, int F,
+                                                                     uint64_t ld) {
+    __shared__ float tile[kAosTile * kMaxFields + kMaxFields];
+    const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
+    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const uint64_t first = tl * kAosTile;
+        const int cnt = (int)min((uint64_t)kAosTile, n - first);
+        for (int f = 0; f < F; ++f)
+            for (int i = threadIdx.x; i < cnt; i += kAosThreads)
+                tile[f * (kAosTile + 1) + i] = __ldcs(soa + (uint64_t)f * ld + first + i);
+        __syncthreads();
+        const int words = cnt * F;
+        float* dst = aos + first * (uint64_t)F;
+        for (int k = threadIdx.x; k < words; k += kAosThreads) {
+            const int i = k / F, f = k - i * F;
+            dst[k] = tile[f * (kAosTile + 1) + i];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace gpz
+
+namespace {
+
+constexpr uint64_t kAosAlign = 256;
+
+// Leading dimension of the structure-of-arrays copy: every field 16-byte aligned.
+uint64_t soa_ld(uint64_t n) { return align_up(n, 4); }
+
+uint64_t soa_bytes(uint64_t n, int F) { return align_up(4ull * soa_ld(n) * (uint64_t)F, kAosAlign); }
+
+unsigned transpose_grid(uint64_t n) {
+    const uint64_t tiles = (n + kAosTile - 1) / kAosTile;
+    const uint64_t cap = 152ull * 8ull;  // eight CTAs per SM of a GB300
+    return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t gpz_compress_aos_workspace_size(uint64_t n, int n_fields) {
+    const uint64_t c = gpz_compress_workspace_size(n, n_fields);
+    if (c == 0) return 0;
+    return align_up(c, kAosAlign) + soa_bytes(n, n_fields);
+}
+
+uint64_t gpz_decompress_aos_workspace_size(uint64_t n, int n_fields) {
+    if (n_fields < 1 || n_fields > kMaxFields) return 0;
+    return align_up(gpz_decompress_workspace_size(), kAosAlign) + soa_bytes(n, n_fields);
+}
+
+gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p, void* d_out,
+                            uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                            void* d_ws, uint64_t ws_size, void* stream) {
+    if (!p || p->n_fields < 1 || p->n_fields > kMaxFields) return GPZ_ERR_INVALID_ARG;
+    const int F = p->n_fields;
+    if (n > 0 && (!d_aos || (reinterpret_cast<uintptr_t>(d_aos) & 3u))) return GPZ_ERR_INVALID_ARG;
+    const uint64_t need = gpz_compress_aos_workspace_size(n, F);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own = false;
+    if (d_ws) {
+        if (ws_size < need) return GPZ_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(d_ws) % kAosAlign) return GPZ_ERR_INVALID_ARG;
+    } else {
+        if (cudaMallocAsync(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
+        own = true;
+    }
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    const uint64_t cws = align_up(gpz_compress_workspace_size(n, F), kAosAlign);
+    float* soa = reinterpret_cast<float*>(ws + cws);
+    const uint64_t ld = soa_ld(n);
+    gpz_status rc = GPZ_OK;
+    if (n > 0) {
+        Recorder rec(s);
+        rec.begin(1);
+        gpz_aos_to_soa_kernel<<<transpose_grid(n), kAosThreads, 0, s>>>(d_aos, soa, n, F, ld);
+        rc = cuda_status(cudaGetLastError());
+        if (rc == GPZ_OK) rec.mark("aos");
+    }
+    if (rc == GPZ_OK) {
+        const float* fields[kMaxFields];
+        for (int f = 0; f < F; ++f) fields[f] = soa + (uint64_t)f * ld;
+        // the compression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
+        rc = gpz_compress(fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream);
+    }
+    if (own) {
+        cudaFreeAsync(d_ws, s);
+        if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
+    }
+    return rc;
+}
+
+gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, int n_fields, uint64_t n,
+                              void* d_ws, uint64_t ws_size, void* stream) {
+    if (n_fields < 1 || n_fields > kMaxFields) return GPZ_ERR_INVALID_ARG;
+    const int F = n_fields;
+    if (n > 0 && (!d_aos || (reinterpret_cast<uintptr_t>(d_aos) & 3u))) return GPZ_ERR_INVALID_ARG;
+    const uint64_t need = gpz_decompress_aos_workspace_size(n, F);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own = false;
+    if (d_ws) {
+        if (ws_size < need) return GPZ_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(d_ws) % kAosAlign) return GPZ_ERR_INVALID_ARG;
+    } else {
+        if (cudaMallocAsync(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
+        if (cudaMemsetAsync(d_ws, 0, 4, s) != cudaSuccess) {
+            cudaFreeAsync(d_ws, s);
+            return GPZ_ERR_CUDA;
+        }
+        own = true;
+    }
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    const uint64_t dws = align_up(gpz_decompress_workspace_size(), kAosAlign);
+    float* soa = reinterpret_cast<float*>(ws + dws);
+    const uint64_t ld = soa_ld(n);
+    float* fields[kMaxFields];
+    for (int f = 0; f < F; ++f) fields[f] = soa + (uint64_t)f * ld;
+    // the decompression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
+    gpz_status rc = gpz_decompress(d_in, in_size, fields, F, n, ws, dws, stream);
+    if (rc == GPZ_OK && n > 0) {
+        Recorder rec(s);
+        rec.begin(1);
+        gpz_soa_to_aos_kernel<<<transpose_grid(n), kAosThreads, 0, s>>>(soa, d_aos, n, F, ld);
+        rc = cuda_status(cudaGetLastError());
+        if (rc == GPZ_OK) rec.mark("aos");
+    }
+    if (own) {
+        if (rc == GPZ_OK) {
+            uint32_t st = 0;
+            if (cudaMemcpyAsync(&st, d_ws, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                rc = GPZ_ERR_CUDA;
+            else if (st != 0)
+                rc = (gpz_status)st;
+        }
+        cudaFreeAsync(d_ws, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess && rc == GPZ_OK) rc = GPZ_ERR_CUDA;
+    }
+    return rc;
+}
+
+}  // extern "C"

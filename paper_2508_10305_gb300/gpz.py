@@ -95,6 +95,14 @@ def _load():
     L.gpz_set_stage_timing.restype = None
     L.gpz_set_fused_compaction.argtypes = [C.c_int]
     L.gpz_set_fused_compaction.restype = C.c_int
+    L.gpz_compress_aos_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_compress_aos_workspace_size.restype = u64
+    L.gpz_decompress_aos_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_decompress_aos_workspace_size.restype = u64
+    L.gpz_compress_aos.argtypes = [vp, u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp, u64, vp]
+    L.gpz_compress_aos.restype = C.c_int
+    L.gpz_decompress_aos.argtypes = [vp, u64, vp, C.c_int, u64, vp, u64, vp]
+    L.gpz_decompress_aos.restype = C.c_int
     L.gpz_stage_times.argtypes = [P(C.c_char_p), P(C.c_float), P(C.c_int), C.c_int]
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
@@ -168,6 +176,51 @@ def gpz_set_stage_timing(enable):
 def gpz_set_fused_compaction(enable):
     """Select the compaction form of later gpz_compress calls; returns the previous one."""
     return bool(lib.gpz_set_fused_compaction(1 if enable else 0))
+
+
+def gpz_compress_aos_workspace_size(n, n_fields):
+    return int(lib.gpz_compress_aos_workspace_size(n, n_fields))
+
+
+def gpz_decompress_aos_workspace_size(n, n_fields):
+    return int(lib.gpz_decompress_aos_workspace_size(n, n_fields))
+
+
+def compress_aos(x_aos, n_fields, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
+    """x_aos: CUDA float32 tensor of n * n_fields values, particle-major.
+    Returns (stream bytes as a CUDA uint8 tensor of the exact size, perm or None)."""
+    n = x_aos.numel() // n_fields
+    dev = x_aos.device
+    params = make_params(n_fields, eb, mode, seg_bits)
+    cap = gpz_bound_size(n, n_fields)
+    out = torch.empty(max(cap, 16), dtype=torch.uint8, device=dev)
+    ws_size = gpz_compress_aos_workspace_size(n, n_fields)
+    ws = torch.empty(max(ws_size, 256), dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if want_perm else None
+    h = C.c_uint64(0)
+    st = lib.gpz_compress_aos(x_aos.data_ptr() if n else None, n, C.byref(params), out.data_ptr(), cap, None,
+                              C.byref(h), perm.data_ptr() if want_perm else None, ws.data_ptr(), ws_size,
+                              _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_compress_aos")
+    return out[:h.value], (perm[:n] if want_perm else None)
+
+
+def decompress_aos(stream_buf, n_fields, n, size=None, stream=None):
+    """The inverse: a CUDA float32 tensor [n, n_fields] in block-sorted order."""
+    size = stream_buf.numel() if size is None else size
+    dev = stream_buf.device
+    out = torch.empty((max(n, 1), n_fields), dtype=torch.float32, device=dev)
+    ws_size = gpz_decompress_aos_workspace_size(n, n_fields)
+    ws = torch.zeros(max(ws_size, 256), dtype=torch.uint8, device=dev)
+    st = lib.gpz_decompress_aos(stream_buf.data_ptr(), size, out.data_ptr(), n_fields, n, ws.data_ptr(), ws_size,
+                                _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_aos")
+    st = gpz_sync_status(ws, stream)
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_aos (device)")
+    return out[:n]
 
 
 def compress_deferred_blocks(ws):
