@@ -19,10 +19,11 @@ constexpr int kAosTile = 1024;     // particles per tile
 constexpr int kAosThreads = 256;
 
 // soa[f * ld + i] = aos[i * F + f] for i < n
+template <int F>
 __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float* __restrict__ aos,
-                                                                     float* __restrict__ soa, uint64_t n, int F,
+                                                                     float* __restrict__ soa, uint64_t n,
                                                                      uint64_t ld) {
-    __shared__ float tile[kAosTile * kMaxFields + kMaxFields];
+    __shared__ float tile[(kAosTile + 1) * F];
     const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
     for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         const uint64_t first = tl * kAosTile;
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float
             tile[f * (kAosTile + 1) + i] = __ldcs(src + k);  // field-major in shared memory, padded rows
         }
         __syncthreads();
+#pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = threadIdx.x; i < cnt; i += kAosThreads) soa[(uint64_t)f * ld + first + i] = tile[f * (kAosTile + 1) + i];
         __syncthreads();
@@ -41,14 +43,16 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float
 }
 
 // aos[i * F + f] = soa[f * ld + i] for i < n
+template <int F>
 __global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float* __restrict__ soa,
-                                                                     float* __restrict__ aos, uint64_t n, int F,
+                                                                     float* __restrict__ aos, uint64_t n,
                                                                      uint64_t ld) {
-    __shared__ float tile[kAosTile * kMaxFields + kMaxFields];
+    __shared__ float tile[(kAosTile + 1) * F];
     const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
     for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         const uint64_t first = tl * kAosTile;
         const int cnt = (int)min((uint64_t)kAosTile, n - first);
+#pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = threadIdx.x; i < cnt; i += kAosThreads)
                 tile[f * (kAosTile + 1) + i] = __ldcs(soa + (uint64_t)f * ld + first + i);
@@ -61,6 +65,31 @@ __global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float
         }
         __syncthreads();
     }
+}
+
+template <int F>
+cudaError_t launch_transpose_f(bool to_soa, const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
+                               cudaStream_t s) {
+    if (to_soa)
+        gpz_aos_to_soa_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld);
+    else
+        gpz_soa_to_aos_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(bool to_soa, const float* src, float* dst, uint64_t n, int F, uint64_t ld,
+                             unsigned grid, cudaStream_t s) {
+    switch (F) {
+        case 1: return launch_transpose_f<1>(to_soa, src, dst, n, ld, grid, s);
+        case 2: return launch_transpose_f<2>(to_soa, src, dst, n, ld, grid, s);
+        case 3: return launch_transpose_f<3>(to_soa, src, dst, n, ld, grid, s);
+        case 4: return launch_transpose_f<4>(to_soa, src, dst, n, ld, grid, s);
+        case 5: return launch_transpose_f<5>(to_soa, src, dst, n, ld, grid, s);
+        case 6: return launch_transpose_f<6>(to_soa, src, dst, n, ld, grid, s);
+        case 7: return launch_transpose_f<7>(to_soa, src, dst, n, ld, grid, s);
+        case 8: return launch_transpose_f<8>(to_soa, src, dst, n, ld, grid, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gpz
@@ -119,8 +148,7 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
     if (n > 0) {
         Recorder rec(s);
         rec.begin(1);
-        gpz_aos_to_soa_kernel<<<transpose_grid(n), kAosThreads, 0, s>>>(d_aos, soa, n, F, ld);
-        rc = cuda_status(cudaGetLastError());
+        rc = cuda_status(launch_transpose(true, d_aos, soa, n, F, ld, transpose_grid(n), s));
         if (rc == GPZ_OK) rec.mark("aos");
     }
     if (rc == GPZ_OK) {
@@ -129,9 +157,17 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
         // the compression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
         rc = gpz_compress(fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream);
     }
-    if (own) {
+    if (own) {  // as gpz_compress without a workspace: synchronise and return the device-side status
+        if (rc == GPZ_OK) {
+            uint32_t st = 0;
+            if (cudaMemcpyAsync(&st, d_ws, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                rc = GPZ_ERR_CUDA;
+            else if (st != 0)
+                rc = (gpz_status)st;
+        }
         cudaFreeAsync(d_ws, s);
-        if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess && rc == GPZ_OK) rc = GPZ_ERR_CUDA;
     }
     return rc;
 }
@@ -166,8 +202,7 @@ gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, 
     if (rc == GPZ_OK && n > 0) {
         Recorder rec(s);
         rec.begin(1);
-        gpz_soa_to_aos_kernel<<<transpose_grid(n), kAosThreads, 0, s>>>(soa, d_aos, n, F, ld);
-        rc = cuda_status(cudaGetLastError());
+        rc = cuda_status(launch_transpose(false, soa, d_aos, n, F, ld, transpose_grid(n), s));
         if (rc == GPZ_OK) rec.mark("aos");
     }
     if (own) {

@@ -59,3 +59,31 @@ def test_aos_workspace_checks(gpz):
                                   ws.data_ptr(), need, None)
     assert st == gpz.ERR_INVALID_ARG  # records must be 4-byte aligned
     assert gpz.gpz_decompress_aos_workspace_size(n, 9) == 0
+
+
+def test_aos_without_workspace(gpz, oracle):
+    """d_ws = NULL: the library allocates, synchronises and returns the status."""
+    import ctypes as C
+    rng = np.random.default_rng(5)
+    F, n = 3, 20_000
+    x = gen("clustered", F, n, rng)
+    xa = torch.from_numpy(np.ascontiguousarray(x.T).reshape(-1)).cuda()
+    params = gpz.make_params(F, 1e-3)
+    cap = gpz.gpz_bound_size(n, F)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    h = C.c_uint64(0)
+    st = gpz.lib.gpz_compress_aos(xa.data_ptr(), n, C.byref(params), out.data_ptr(), cap, None, C.byref(h), None,
+                                  None, 0, None)
+    assert st == gpz.OK
+    rs, _ = oracle.compress(x, 1e-3, 0, 3)
+    assert h.value == rs.size and np.array_equal(out[:h.value].cpu().numpy(), rs)
+    rec = torch.empty(n * F, dtype=torch.float32, device="cuda")
+    st = gpz.lib.gpz_decompress_aos(out.data_ptr(), h.value, rec.data_ptr(), F, n, None, 0, None)
+    assert st == gpz.OK
+    ro = oracle.decompress(rs, F, n)
+    assert np.array_equal(rec.cpu().numpy().view(np.uint32), np.ascontiguousarray(ro.T).reshape(-1).view(np.uint32))
+    # a damaged stream: the status comes back from the call itself
+    bad = out[:h.value].clone()
+    bad[0] ^= 1
+    st = gpz.lib.gpz_decompress_aos(bad.data_ptr(), h.value, rec.data_ptr(), F, n, None, 0, None)
+    assert st == gpz.ERR_CORRUPT
