@@ -597,6 +597,54 @@ int gpzo_compress(const float* const* fields, uint64_t n, int F, int mode, const
     return GPZO_OK;
 }
 
+int gpzo_compress_f64(const double* const* fields, uint64_t n, int F, int mode, const double* eb,
+                      int G, uint8_t* out, uint64_t cap, uint64_t* out_size, uint32_t* perm,
+                      double* eb_used) {
+    if (F < 1 || F > MAX_FIELDS || (mode != 0 && mode != 1) || !eb) return GPZO_ERR_INVALID_ARG;
+    if (n > 0 && !fields) return GPZO_ERR_INVALID_ARG;
+    for (int f = 0; f < F && n > 0; ++f)
+        if (!fields[f]) return GPZO_ERR_INVALID_ARG;
+    std::vector<std::vector<float>> x32(F, std::vector<float>(n));
+    std::vector<const float*> ptrs(F);
+    std::vector<double> ebp(F);
+    for (int f = 0; f < F; ++f) {
+        if (!(eb[f] > 0.0) || !std::isfinite(eb[f])) return GPZO_ERR_INVALID_ARG;
+        /* Round every value to fp32; the largest rounding error over the finite
+           values, and the fp64 range of the non-NaN values. */
+        double delta = 0.0, lo = 0.0, hi = 0.0;
+        bool any = false;
+        for (uint64_t i = 0; i < n; ++i) {
+            const double v = fields[f][i];
+            const float r = (float)v;
+            x32[f][i] = r;
+            if (std::isfinite(v)) delta = std::max(delta, std::fabs(v - (double)r));
+            if (std::isnan(v)) continue;
+            if (!any) {
+                lo = hi = v;
+                any = true;
+            } else {
+                lo = std::min(lo, v);
+                hi = std::max(hi, v);
+            }
+        }
+        double e = eb[f];
+        if (mode == 1 && any) {
+            const double range = hi - lo;
+            if (range > 0.0 && std::isfinite(range)) {
+                const double t = eb[f] * range;
+                if (t > 0.0 && std::isfinite(t)) e = t;
+            }
+        }
+        const double reduced = e - delta;
+        if (!(reduced > 0.0) || !std::isfinite(reduced)) return GPZO_ERR_UNSUPPORTED;
+        ebp[f] = reduced;
+        ptrs[f] = x32[f].data();
+    }
+    if (eb_used)
+        for (int f = 0; f < F; ++f) eb_used[f] = ebp[f];
+    return gpzo_compress(ptrs.data(), n, F, 0, ebp.data(), G, out, cap, out_size, perm);
+}
+
 int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int F, uint64_t n) {
     if (!in || F < 1 || F > MAX_FIELDS || (n > 0 && !out)) return GPZO_ERR_INVALID_ARG;
     if (in_size % 4 != 0 || in_size < 4ull * STREAM_HEADER_WORDS) return GPZO_ERR_CORRUPT;

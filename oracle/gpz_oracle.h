@@ -88,6 +88,22 @@ int gpzo_compress(const float* const* fields, uint64_t n, int n_fields, int mode
                   const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
                   uint64_t* out_size, uint32_t* perm);
 
+/* fp64 input (the paper's note on double-precision data, Section 5): each
+ * value is rounded to fp32 (round to nearest), and the fp32 values are
+ * compressed with an absolute bound per field reduced by the largest rounding
+ * error over the field's finite values:
+ *     eb'_f = eb_f - max_i |x_i - RN32(x_i)|,
+ * where eb_f is eb[f] (mode 0) or rel = eb[f] times the fp64 range of the
+ * non-NaN values (mode 1; rel itself when that range or the product is not a
+ * finite positive number).  The stream is an ordinary absolute-bound stream
+ * of the fp32 values, so every decompressed value lies within eb_f of its
+ * fp64 input.  GPZO_ERR_UNSUPPORTED when some eb'_f is not positive (also when
+ * a finite value rounds beyond the fp32 range).  eb_used (nullable) receives
+ * the F values eb'_f. */
+int gpzo_compress_f64(const double* const* fields, uint64_t n, int n_fields, int mode,
+                      const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
+                      uint64_t* out_size, uint32_t* perm, double* eb_used);
+
 /* Inverse.  Writes n values per field, in the stream's (block-sorted) order. */
 int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int n_fields,
                     uint64_t n);

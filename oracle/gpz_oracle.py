@@ -48,6 +48,8 @@ def lib():
         L.gpzo_compress.argtypes = [P(f32p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
                                     u8p, C.c_uint64, P(C.c_uint64), u32p]
         L.gpzo_decompress.argtypes = [u8p, C.c_uint64, P(f32p), C.c_int, C.c_uint64]
+        L.gpzo_compress_f64.argtypes = [P(C.c_void_p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
+                                        u8p, C.c_uint64, P(C.c_uint64), u32p, P(C.c_double)]
         _lib = L
     return _lib
 
@@ -197,6 +199,42 @@ def compress_status(fields, eb, mode=0, seg_bits=3, cap=None):
     size = C.c_uint64(0)
     return lib().gpzo_compress(_field_ptrs(x), n, F, mode, _ptr(ebs, C.c_double), seg_bits,
                                _ptr(out, C.c_uint8), cap, C.byref(size), None)
+
+
+def compress_f64(fields, eb, mode=0, seg_bits=3, want_perm=True):
+    """fp64 [F, n] -> (stream bytes, perm or None, the reduced absolute bounds eb'_f)."""
+    x = np.ascontiguousarray(fields, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[None, :]
+    F, n = x.shape
+    ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
+    cap = bound_size(n, F)
+    out = np.zeros(max(cap, 4), dtype=np.uint8)
+    size = C.c_uint64(0)
+    perm = np.zeros(n, dtype=np.uint32) if want_perm else None
+    used = np.zeros(F, dtype=np.float64)
+    ptrs = (C.c_void_p * F)(*[x[f].ctypes.data for f in range(F)])
+    rc = lib().gpzo_compress_f64(ptrs, n, F, mode, _ptr(ebs, C.c_double), seg_bits, _ptr(out, C.c_uint8), cap,
+                                 C.byref(size), _ptr(perm, C.c_uint32) if want_perm else None,
+                                 _ptr(used, C.c_double))
+    if rc != OK:
+        raise RuntimeError("gpzo_compress_f64 failed: %d" % rc)
+    return out[:size.value].copy(), perm, used
+
+
+def compress_f64_status(fields, eb, mode=0, seg_bits=3):
+    """Only the status code of gpzo_compress_f64."""
+    x = np.ascontiguousarray(fields, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[None, :]
+    F, n = x.shape
+    ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
+    cap = bound_size(n, F)
+    out = np.zeros(max(cap, 4), dtype=np.uint8)
+    size = C.c_uint64(0)
+    ptrs = (C.c_void_p * F)(*[x[f].ctypes.data for f in range(F)])
+    return lib().gpzo_compress_f64(ptrs, n, F, mode, _ptr(ebs, C.c_double), seg_bits, _ptr(out, C.c_uint8), cap,
+                                   C.byref(size), None, None)
 
 
 def decompress(stream, n_fields, n):

@@ -453,3 +453,45 @@ def test_width_and_count_rules(oracle):
     counts[0] = 0
     st, _ = decode(se.replace_block(w, 3, b, se.rebuild_block(p, counts=counts, wc=11)))
     assert st == oracle.ERR_CORRUPT
+
+
+def test_f64_input_bound_and_definition(oracle):
+    """fp64 input: every decompressed value is within eb of its fp64 input
+    (checked in double), the reduced bound is eb minus the largest fp32
+    rounding error (computed here independently), and the stream is the
+    fp32 compression of the rounded values with that bound."""
+    rng = np.random.default_rng(31)
+    F, n = 3, 5000
+    x = rng.random((F, n)) * np.array([1e4, 3.0, 250.0])[:, None] + np.array([-5e3, 0.0, 7.0])[:, None]
+    x[1, 17] = np.nan
+    x[2, 4000] = np.inf
+    for mode, eb in [(0, 1e-3), (1, 1e-4)]:
+        s, perm, used = oracle.compress_f64(x, eb, mode)
+        r = x.astype(np.float32)
+        fin = np.isfinite(x)
+        delta = np.array([np.max(np.abs(x[f][fin[f]] - r[f][fin[f]].astype(np.float64))) for f in range(F)])
+        if mode == 0:
+            ebf = np.full(F, eb)
+        else:
+            ebf = []
+            for f in range(F):
+                v = x[f][~np.isnan(x[f])]
+                rngf = float(v.max()) - float(v.min())
+                t = eb * rngf
+                ebf.append(t if (0 < rngf < np.inf and 0 < t < np.inf) else eb)
+            ebf = np.array(ebf)
+        assert np.array_equal(used, ebf - delta)
+        ref, rperm = oracle.compress(r, used, 0, 3)
+        assert np.array_equal(s, ref) and np.array_equal(perm, rperm)
+        out = oracle.decompress(s, F, n).astype(np.float64)
+        xs = x[:, perm]
+        with np.errstate(invalid="ignore"):
+            ok = np.isnan(xs) & np.isnan(out) | (xs == out) | (np.abs(xs - out) <= ebf[:, None])
+        assert ok.all()
+
+
+def test_f64_bound_finer_than_fp32_is_refused(oracle):
+    x = np.array([[12345.678901234, 1.0, 2.0]])
+    assert oracle.compress_f64_status(x, 1e-9, 0) == oracle.ERR_UNSUPPORTED  # ulp/2 of 12345.68 in fp32 is ~4.9e-4
+    assert oracle.compress_f64_status(np.array([[1e300, 0.0]]), 1.0, 0) == oracle.ERR_UNSUPPORTED  # beyond fp32
+    assert oracle.compress_f64_status(x, 1e-3, 0) == oracle.OK
