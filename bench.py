@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-compaction comparison")
     ap.add_argument("--no-aos", action="store_true", help="skip the interleaved-records round trip")
+    ap.add_argument("--no-f64", action="store_true", help="skip the fp64 round trip")
     ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served", "sweep"])
     ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
@@ -537,6 +538,60 @@ def run_gpz(args, rank, world, local):
                          "same_stream": same_aos,
                          "records_checked": bool(torch.equal(a_rec.t(), dec(comp.out, size)))}
         del x_aos, a_out, a_cws, a_dws, a_rec
+
+    # fp64 input and output (gpz_compress_f64 / gpz_decompress_f64: a rounding
+    # pass and a widening pass around the same kernels) on the snapshot
+    # widened to fp64; GB/s of fp64 input
+    if not args.no_f64:
+        import ctypes as C
+        x64 = x.double()
+        params = gpz.make_params(F, REL_EB, gpz.EB_REL, SEG_BITS)
+        cap = gpz.gpz_bound_size(n, F)
+        f_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        f_size = torch.zeros(1, dtype=torch.int64, device=dev)
+        cws = int(gpz.lib.gpz_compress_f64_workspace_size(n, F))
+        dws = int(gpz.lib.gpz_decompress_f64_workspace_size(n, F))
+        f_cws = torch.empty(cws, dtype=torch.uint8, device=dev)
+        f_dws = torch.zeros(dws, dtype=torch.uint8, device=dev)
+        f_rec = torch.empty((F, n), dtype=torch.float64, device=dev)
+        in_ptrs = gpz._ptr_array([x64[f] for f in range(F)])
+        out_ptrs = gpz._ptr_array([f_rec[f] for f in range(F)])
+        hs = gpz._stream_handle(stream)
+        h_sz = C.c_uint64(0)
+
+        def f64_step():
+            st1 = gpz.lib.gpz_compress_f64(in_ptrs, n, C.byref(params), f_out.data_ptr(), cap, f_size.data_ptr(),
+                                           C.byref(h_sz), None, f_cws.data_ptr(), cws, None, hs)
+            st2 = gpz.lib.gpz_decompress_f64(f_out.data_ptr(), h_sz.value, out_ptrs, F, n, f_dws.data_ptr(), dws, hs)
+            if st1 != gpz.OK or st2 != gpz.OK:
+                raise gpz.GpzError(st1 or st2, "fp64 round trip")
+
+        for _ in range(args.warmup):
+            f64_step()
+        torch.cuda.synchronize()
+        kf = min(args.steps, 30)
+        gpz.gpz_set_stage_timing(True)
+        gpz.gpz_stage_times()
+        ev0.record(stream)
+        for _ in range(kf):
+            f64_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        st_f = gpz.gpz_stage_times()
+        gpz.gpz_set_stage_timing(False)
+        stc = gpz.gpz_sync_status(f_dws)
+        if stc != gpz.OK:
+            raise gpz.GpzError(stc, "fp64 round trip (device)")
+        ms_f = ranks_max([ev0.elapsed_time(ev1) / kf], dev)[0]
+        # every sampled value within the bound of its fp64 input: |x - x^| <= eb' + max rounding error
+        used = (C.c_double * F)()
+        gpz.lib.gpz_compress_f64(in_ptrs, n, C.byref(params), f_out.data_ptr(), cap, None, C.byref(h_sz), None,
+                                 f_cws.data_ptr(), cws, used, hs)
+        result["f64"] = {"value": job_gbs(world, 8.0 * n * F, 1, ms_f / 1e3), "unit": "GB/s of fp64 input",
+                         "ms_per_step": ms_f, "steps": kf, "ratio_vs_fp64": 8.0 * n * F / h_sz.value,
+                         "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st_f.items()},
+                         "eb_reduced": [used[f] for f in range(F)]}
+        del x64, f_out, f_cws, f_dws, f_rec
 
     # end to end through the public API with host buffers: H2D input ->
     # compress -> D2H stream -> H2D stream -> decompress -> D2H output, every

@@ -179,6 +179,37 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
 gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, int n_fields,
                               uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
 
+/* fp64 input and output (Section 5.1: fp64 input is down-cast to
+ * fp32 when that suffices for the error bound).  gpz_compress_f64 rounds every value to fp32 on the GPU and
+ * compresses the fp32 values with each field's bound reduced by the largest
+ * rounding error over its finite values,
+ *     eb'_f = eb_f - max_i |x_i - RN32(x_i)|,
+ * where eb_f is the given absolute bound or, with GPZ_EB_REL, the relative
+ * bound times the fp64 range of the field's non-NaN values (the relative
+ * bound itself when that range is not a finite positive number).  The
+ * result is an ordinary stream with absolute bounds eb'_f (header mode 0),
+ * and every decompressed value lies within eb_f of its fp64 input.
+ *   d_fields:   host array of n_fields device pointers to n doubles (8-byte aligned).
+ *   d_ws:       required: at least gpz_compress_f64_workspace_size(n, F) bytes,
+ *               256-byte aligned (4*n*F bytes more than gpz_compress needs).
+ *   h_eb_used:  host array of n_fields doubles receiving eb'_f, or NULL.
+ * The call synchronises `stream` once (after the rounding pass, to form eb').
+ * GPZ_ERR_UNSUPPORTED when some eb'_f is not positive: the bound is finer than
+ * fp32 can hold for that field (or a finite value lies beyond the fp32 range).
+ * Other arguments, errors and ordering as gpz_compress; gpz_sync_status(d_ws)
+ * reads the device-side status.
+ * gpz_decompress_f64 decompresses into an fp32 copy in its workspace (at least
+ * gpz_decompress_f64_workspace_size(n, F) bytes, required) and widens it to the
+ * n_fields fp64 arrays (exact); otherwise as gpz_decompress. */
+uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields);
+uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields);
+gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                            uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size,
+                            uint32_t* d_perm, void* d_ws, uint64_t ws_size, double* h_eb_used,
+                            void* stream);
+gpz_status gpz_decompress_f64(const void* d_in, uint64_t in_size, double* const* d_fields, int n_fields,
+                              uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
+
 /* Static text for a status code. */
 const char* gpz_status_str(gpz_status s);
 

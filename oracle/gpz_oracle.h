@@ -88,7 +88,8 @@ int gpzo_compress(const float* const* fields, uint64_t n, int n_fields, int mode
                   const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
                   uint64_t* out_size, uint32_t* perm);
 
-/* fp64 input (the paper's note on double-precision data, Section 5): each
+/* fp64 input (Section 5.1: fp64 input is lowered to fp32 when that is enough
+ * for the bound; the test used here is the following): each
  * value is rounded to fp32 (round to nearest), and the fp32 values are
  * compressed with an absolute bound per field reduced by the largest rounding
  * error over the field's finite values:

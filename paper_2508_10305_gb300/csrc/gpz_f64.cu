@@ -1,0 +1,249 @@
+// gpz_f64.cu -- fp64 input and output (Section 5.1: the paper down-casts fp64
+// input to fp32 when that suffices for the error bound).  Compression rounds every value to fp32 on the GPU and
+// compresses the fp32 values with each field's bound reduced by the largest
+// rounding error over its finite values, eb' = eb - max |x - RN32(x)|, so
+// that every decompressed value lies within eb of its fp64 input.  One
+// prepass kernel writes the fp32 copy (in the workspace) and finds, per
+// field, the fp64 extremes of the non-NaN values and the largest rounding
+// error; the host reads those (the call synchronises once), forms eb' (a
+// relative bound is taken over the fp64 range) and calls gpz_compress with
+// absolute bounds on the copy.  Decompression runs gpz_decompress into an
+// fp32 copy and widens it to fp64 (exact).
+#include <cmath>
+#include <cstring>
+
+#include "gpz.h"
+#include "gpz_host.hpp"
+#include "gpz_internal.cuh"
+
+using namespace gpz;
+using namespace gpz::host;
+
+namespace gpz {
+
+constexpr int kF64Threads = 256;
+
+// Order key of a double: unsigned order equals numeric order (NaN excluded).
+__device__ __forceinline__ unsigned long long order_key64(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// res[3f] = order key of the field's minimum, res[3f+1] of its maximum (over
+// the non-NaN values), res[3f+2] = bits of the largest |x - RN32(x)| over
+// the finite values (non-negative, so its bits order as the value).
+// res must start as {~0, 0, 0} per field.
+__global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a) {
+    __shared__ unsigned long long s_res[kF64Threads / 32][3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t stride = (uint64_t)gridDim.x * kF64Threads;
+    for (int f = 0; f < a.F; ++f) {
+        const double* x = a.in[f];
+        float* y = a.out32[f];
+        unsigned long long kmin = ~0ull, kmax = 0ull, dmax = 0ull;
+        for (uint64_t i = (uint64_t)blockIdx.x * kF64Threads + tid; i < a.n; i += stride) {
+            const double v = __ldcs(x + i);
+            const float r = __double2float_rn(v);
+            y[i] = r;
+            if (v == v) {  // not NaN
+                const unsigned long long k = order_key64(v);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+                if (fabs(v) <= 1.7976931348623157e308) {  // finite: the rounding error is exact in double
+                    const double d = fabs(v - (double)r);
+                    dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+            dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        }
+        if (lane == 0) {
+            s_res[warp][0] = kmin;
+            s_res[warp][1] = kmax;
+            s_res[warp][2] = dmax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kF64Threads / 32; ++w) {
+                kmin = min(kmin, s_res[w][0]);
+                kmax = max(kmax, s_res[w][1]);
+                dmax = max(dmax, s_res[w][2]);
+            }
+            atomicMin(a.res + 3 * f, kmin);
+            atomicMax(a.res + 3 * f + 1, kmax);
+            atomicMax(a.res + 3 * f + 2, dmax);
+        }
+        __syncthreads();
+    }
+}
+
+// out64[f][i] = (double)in32[f][i]
+__global__ void __launch_bounds__(kF64Threads) gpz_f64_widen_kernel(F64Args a) {
+    const uint64_t stride = (uint64_t)gridDim.x * kF64Threads;
+    for (int f = 0; f < a.F; ++f)
+        for (uint64_t i = (uint64_t)blockIdx.x * kF64Threads + threadIdx.x; i < a.n; i += stride)
+            a.out64[f][i] = (double)__ldcs(a.in32[f] + i);
+}
+
+}  // namespace gpz
+
+namespace {
+
+constexpr uint64_t kF64Align = 256;
+constexpr uint64_t kResBytes = 256;  // 3 x 8 fields x 8 bytes
+
+uint64_t f32_ld(uint64_t n) { return align_up(n, 4); }
+uint64_t f32_bytes(uint64_t n, int F) { return align_up(4ull * f32_ld(n) * (uint64_t)F, kF64Align); }
+unsigned f64_grid(uint64_t n) {
+    const uint64_t want = (n + kF64Threads - 1) / kF64Threads;
+    const uint64_t cap = 152ull * 8ull;
+    return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+double from_key64(unsigned long long k) {
+    const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields) {
+    const uint64_t c = gpz_compress_workspace_size(n, n_fields);
+    if (c == 0) return 0;
+    return align_up(c, kF64Align) + kResBytes + f32_bytes(n, n_fields);
+}
+
+uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields) {
+    if (n_fields < 1 || n_fields > kMaxFields) return 0;
+    return align_up(gpz_decompress_workspace_size(), kF64Align) + f32_bytes(n, n_fields);
+}
+
+gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                            uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                            void* d_ws, uint64_t ws_size, double* h_eb_used, void* stream) {
+    if (!p || p->n_fields < 1 || p->n_fields > kMaxFields || (p->mode != GPZ_EB_ABS && p->mode != GPZ_EB_REL))
+        return GPZ_ERR_INVALID_ARG;
+    const int F = p->n_fields;
+    for (int f = 0; f < F; ++f)
+        if (!(p->eb[f] > 0.0) || !std::isfinite(p->eb[f])) return GPZ_ERR_INVALID_ARG;
+    if (n > 0) {
+        if (!d_fields) return GPZ_ERR_INVALID_ARG;
+        for (int f = 0; f < F; ++f)
+            if (!d_fields[f] || (reinterpret_cast<uintptr_t>(d_fields[f]) & 7u)) return GPZ_ERR_INVALID_ARG;
+    }
+    const uint64_t need = gpz_compress_f64_workspace_size(n, F);
+    if (need == 0) return GPZ_ERR_INVALID_ARG;
+    if (!d_ws || ws_size < need) return d_ws ? GPZ_ERR_CAPACITY : GPZ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_ws) % kF64Align) return GPZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    const uint64_t cws = align_up(gpz_compress_workspace_size(n, F), kF64Align);
+    unsigned long long* res = reinterpret_cast<unsigned long long*>(ws + cws);
+    float* y = reinterpret_cast<float*>(ws + cws + kResBytes);
+    const uint64_t ld = f32_ld(n);
+
+    // the prepass: the fp32 copy, the fp64 extremes and the largest rounding error
+    unsigned long long init[3 * kMaxFields];
+    for (int f = 0; f < F; ++f) {
+        init[3 * f] = ~0ull;
+        init[3 * f + 1] = 0ull;
+        init[3 * f + 2] = 0ull;
+    }
+    if (cudaMemcpyAsync(res, init, 24ull * F, cudaMemcpyHostToDevice, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    F64Args fa{};
+    fa.F = F;
+    fa.n = n;
+    fa.res = res;
+    for (int f = 0; f < F; ++f) {
+        fa.in[f] = n ? d_fields[f] : nullptr;
+        fa.out32[f] = y + (uint64_t)f * ld;
+    }
+    if (n > 0) {
+        Recorder rec(s);
+        rec.begin(1);
+        gpz_f64_prepass_kernel<<<f64_grid(n), kF64Threads, 0, s>>>(fa);
+        if (cudaGetLastError() != cudaSuccess) return GPZ_ERR_CUDA;
+        rec.mark("f64");
+    }
+    unsigned long long got[3 * kMaxFields];
+    if (cudaMemcpyAsync(got, res, 24ull * F, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GPZ_ERR_CUDA;
+
+    // the reduced absolute bounds (each step one IEEE double operation)
+    double ebp[kMaxFields];
+    for (int f = 0; f < F; ++f) {
+        double e = p->eb[f];
+        const bool any = got[3 * f] != ~0ull;  // some value is not NaN
+        if (p->mode == GPZ_EB_REL && any) {
+            const volatile double range = from_key64(got[3 * f + 1]) - from_key64(got[3 * f]);
+            if (range > 0.0 && std::isfinite(range)) {
+                const volatile double t = p->eb[f] * range;
+                if (t > 0.0 && std::isfinite(t)) e = t;
+            }
+        }
+        double delta;
+        std::memcpy(&delta, &got[3 * f + 2], 8);
+        const volatile double reduced = e - delta;
+        if (!(reduced > 0.0) || !std::isfinite(reduced)) return GPZ_ERR_UNSUPPORTED;
+        ebp[f] = reduced;
+    }
+    if (h_eb_used)
+        for (int f = 0; f < F; ++f) h_eb_used[f] = ebp[f];
+    gpz_params q{};
+    q.mode = GPZ_EB_ABS;
+    q.n_fields = F;
+    q.seg_bits = p->seg_bits;
+    for (int f = 0; f < F; ++f) q.eb[f] = ebp[f];
+    const float* fields[kMaxFields];
+    for (int f = 0; f < F; ++f) fields[f] = y + (uint64_t)f * ld;
+    // the compression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
+    return gpz_compress(fields, n, &q, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream);
+}
+
+gpz_status gpz_decompress_f64(const void* d_in, uint64_t in_size, double* const* d_fields, int n_fields, uint64_t n,
+                              void* d_ws, uint64_t ws_size, void* stream) {
+    if (n_fields < 1 || n_fields > kMaxFields) return GPZ_ERR_INVALID_ARG;
+    const int F = n_fields;
+    if (n > 0) {
+        if (!d_fields) return GPZ_ERR_INVALID_ARG;
+        for (int f = 0; f < F; ++f)
+            if (!d_fields[f] || (reinterpret_cast<uintptr_t>(d_fields[f]) & 7u)) return GPZ_ERR_INVALID_ARG;
+    }
+    const uint64_t need = gpz_decompress_f64_workspace_size(n, F);
+    if (!d_ws || ws_size < need) return d_ws ? GPZ_ERR_CAPACITY : GPZ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_ws) % kF64Align) return GPZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    const uint64_t dws = align_up(gpz_decompress_workspace_size(), kF64Align);
+    float* y = reinterpret_cast<float*>(ws + dws);
+    const uint64_t ld = f32_ld(n);
+    float* fields[kMaxFields];
+    for (int f = 0; f < F; ++f) fields[f] = y + (uint64_t)f * ld;
+    // the decompression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
+    gpz_status rc = gpz_decompress(d_in, in_size, fields, F, n, ws, dws, stream);
+    if (rc != GPZ_OK || n == 0) return rc;
+    F64Args fa{};
+    fa.F = F;
+    fa.n = n;
+    for (int f = 0; f < F; ++f) {
+        fa.in32[f] = y + (uint64_t)f * ld;
+        fa.out64[f] = d_fields[f];
+    }
+    Recorder rec(s);
+    rec.begin(1);
+    gpz_f64_widen_kernel<<<f64_grid(n), kF64Threads, 0, s>>>(fa);
+    if (cudaGetLastError() != cudaSuccess) return GPZ_ERR_CUDA;
+    rec.mark("f64");
+    return GPZ_OK;
+}
+
+}  // extern "C"

@@ -79,6 +79,16 @@ struct QseArgs {
 
 constexpr uint32_t kPlaced = 0x80000000u;  // in a block's word count: already in the stream
 
+struct F64Args {                // fp64 input and output (gpz_f64.cu)
+    const double* in[kMaxFields];
+    float* out32[kMaxFields];
+    const float* in32[kMaxFields];
+    double* out64[kMaxFields];
+    uint64_t n;
+    int F;
+    unsigned long long* res;    // [F][3]: min key, max key, largest rounding error (bits)
+};
+
 struct ScanArgs {
     const uint32_t* sizes;      // [nblocks]
     uint32_t nblocks;

@@ -95,6 +95,14 @@ def _load():
     L.gpz_set_stage_timing.restype = None
     L.gpz_set_fused_compaction.argtypes = [C.c_int]
     L.gpz_set_fused_compaction.restype = C.c_int
+    L.gpz_compress_f64_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_compress_f64_workspace_size.restype = u64
+    L.gpz_decompress_f64_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_decompress_f64_workspace_size.restype = u64
+    L.gpz_compress_f64.argtypes = [vp, u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp, u64, P(C.c_double), vp]
+    L.gpz_compress_f64.restype = C.c_int
+    L.gpz_decompress_f64.argtypes = [vp, u64, vp, C.c_int, u64, vp, u64, vp]
+    L.gpz_decompress_f64.restype = C.c_int
     L.gpz_compress_aos_workspace_size.argtypes = [u64, C.c_int]
     L.gpz_compress_aos_workspace_size.restype = u64
     L.gpz_decompress_aos_workspace_size.argtypes = [u64, C.c_int]
@@ -221,6 +229,44 @@ def decompress_aos(stream_buf, n_fields, n, size=None, stream=None):
     if st != OK:
         raise GpzError(st, "gpz_decompress_aos (device)")
     return out[:n]
+
+
+def compress_f64(x, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
+    """x: CUDA float64 tensor [F, n].  Returns (stream bytes as a CUDA uint8
+    tensor of the exact size, perm or None, the reduced bounds eb'_f)."""
+    F, n = x.shape
+    dev = x.device
+    params = make_params(F, eb, mode, seg_bits)
+    cap = gpz_bound_size(n, F)
+    out = torch.empty(max(cap, 16), dtype=torch.uint8, device=dev)
+    ws_size = int(lib.gpz_compress_f64_workspace_size(n, F))
+    ws = torch.empty(max(ws_size, 256), dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if want_perm else None
+    used = (C.c_double * F)()
+    h = C.c_uint64(0)
+    st = lib.gpz_compress_f64(_ptr_array([x[f] for f in range(F)]), n, C.byref(params), out.data_ptr(), cap, None,
+                              C.byref(h), perm.data_ptr() if want_perm else None, ws.data_ptr(), ws_size, used,
+                              _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_compress_f64")
+    return out[:h.value], (perm[:n] if want_perm else None), [used[f] for f in range(F)]
+
+
+def decompress_f64(stream_buf, n_fields, n, size=None, stream=None):
+    """The inverse: a CUDA float64 tensor [F, n] in block-sorted order."""
+    size = stream_buf.numel() if size is None else size
+    dev = stream_buf.device
+    out = torch.empty((n_fields, max(n, 1)), dtype=torch.float64, device=dev)
+    ws_size = int(lib.gpz_decompress_f64_workspace_size(n, n_fields))
+    ws = torch.zeros(max(ws_size, 256), dtype=torch.uint8, device=dev)
+    st = lib.gpz_decompress_f64(stream_buf.data_ptr(), size, _ptr_array([out[f] for f in range(n_fields)]),
+                                n_fields, n, ws.data_ptr(), ws_size, _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_f64")
+    st = gpz_sync_status(ws, stream)
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_f64 (device)")
+    return out[:, :n]
 
 
 def compress_deferred_blocks(ws):
