@@ -55,6 +55,9 @@ struct BatchCompressArgs {
     uint32_t* rkeys;             // [chunks][kMaxFields][2]: ~order key of the min, order key of the max; zeroed
     uint32_t* rdone;             // [chunks] range items finished; zeroed
     FieldParams* rparams;        // [chunks][kMaxFields]
+    uint2* bext;                 // [all blocks][kMaxFields]: each block's extremes from the range items
+                                 // (a chunk's blocks from block_base * kMaxFields, b * F + f), or nullptr
+    int pre;                     // the group's blocks read their extremes from bext (relative bounds)
     uint32_t* temp;
     uint32_t* sizes;             // [all blocks] words per block
     uint32_t* general_list;      // [the group's blocks] global block ids left to the general kernel

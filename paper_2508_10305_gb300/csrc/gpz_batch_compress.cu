@@ -37,7 +37,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.G = ch->G;
         A.bulk_ok = ch->bulk_ok;
         A.d_params = nullptr;
-        A.bext = nullptr;  // the fused kernel finds each block's extremes itself
+        A.bext = g.pre ? g.bext + (size_t)ch->block_base * kMaxFields : nullptr;
         A.temp = g.temp + ch->temp_base;
         A.slot_words = batch_slot_words(ch->F);
         A.sizes = g.sizes + base;
@@ -61,35 +61,52 @@ __device__ __forceinline__ void range_item(const BatchCompressArgs& g, uint32_t 
     const uint32_t slices = ch->range_slices;
     const uint32_t f = local / slices, sl = local - f * slices;
     const uint64_t n = ch->n;
-    const uint64_t start = (uint64_t)sl * g.slice;
+    const uint64_t start = (uint64_t)sl * g.slice;  // a multiple of 1024: the slice holds whole blocks
     const uint64_t end = start + g.slice < n ? start + g.slice : n;
     const float* x = ch->in[f];
+    const int F = ch->F;
+    uint2* bext = g.bext + (size_t)ch->block_base * kMaxFields;
+    // a warp per block: the block's extremes (order keys, or (0, 0) when it
+    // holds a NaN or an infinity), and the warp's running extremes of the
+    // slice over its non-NaN values
     float lo = INFINITY, hi = -INFINITY;
-    uint64_t tail = start + t;
-    if (ch->bulk_ok && start < end) {
-        // start is a multiple of the slice (itself a multiple of 1024): aligned
-        const float4* x4 = reinterpret_cast<const float4*>(x);
-        const uint64_t e4 = end >> 2;
-        uint64_t i = (start >> 2) + t;
-        for (; i + 3 * kThreads < e4; i += 4 * kThreads) {
-            const float4 v0 = __ldcs(x4 + i), v1 = __ldcs(x4 + i + kThreads), v2 = __ldcs(x4 + i + 2 * kThreads),
-                         v3 = __ldcs(x4 + i + 3 * kThreads);
-            lo = fminf(lo, fminf(fminf(fminf(v0.x, v0.y), fminf(v0.z, v0.w)), fminf(fminf(v1.x, v1.y), fminf(v1.z, v1.w))));
-            lo = fminf(lo, fminf(fminf(fminf(v2.x, v2.y), fminf(v2.z, v2.w)), fminf(fminf(v3.x, v3.y), fminf(v3.z, v3.w))));
-            hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v0.x, v0.y), fmaxf(v0.z, v0.w)), fmaxf(fmaxf(v1.x, v1.y), fmaxf(v1.z, v1.w))));
-            hi = fmaxf(hi, fmaxf(fmaxf(fmaxf(v2.x, v2.y), fmaxf(v2.z, v2.w)), fmaxf(fmaxf(v3.x, v3.y), fmaxf(v3.z, v3.w))));
+    const uint64_t b_first = start / kBlock, b_end = (end + kBlock - 1) / kBlock;
+    for (uint64_t b = b_first + warp; b < b_end; b += kWarps) {
+        const float* xb = x + b * kBlock;
+        const int n_b = (int)min((uint64_t)kBlock, n - b * kBlock);
+        float blo = INFINITY, bhi = -INFINITY, probe = 0.0f;
+        if (ch->bulk_ok && n_b == kBlock) {  // two rounds of four 16-byte loads per lane
+            const float4* x4 = reinterpret_cast<const float4*>(xb);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float4 v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = __ldcs(x4 + lane + 32 * (4 * h + k));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    blo = fminf(blo, fminf(fminf(v[k].x, v[k].y), fminf(v[k].z, v[k].w)));
+                    bhi = fmaxf(bhi, fmaxf(fmaxf(v[k].x, v[k].y), fmaxf(v[k].z, v[k].w)));
+                    probe = __fmaf_rn(v[k].x, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].y, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].z, 0.0f, probe);
+                    probe = __fmaf_rn(v[k].w, 0.0f, probe);
+                }
+            }
+        } else {
+            for (int i = lane; i < n_b; i += 32) {
+                const float v = __ldcs(xb + i);
+                blo = fminf(blo, v);
+                bhi = fmaxf(bhi, v);
+                probe = __fmaf_rn(v, 0.0f, probe);
+            }
         }
-        for (; i < e4; i += kThreads) {
-            const float4 v = __ldcs(x4 + i);
-            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
-            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-        }
-        tail = (e4 << 2) + t;
-    }
-    for (uint64_t i = tail; i < end; i += kThreads) {
-        const float v = x[i];
-        lo = fminf(lo, v);
-        hi = fmaxf(hi, v);
+        blo = warp_min_f32(blo);
+        bhi = warp_max_f32(bhi);
+        const bool nonfinite = __any_sync(0xffffffffu, probe != probe);
+        if (lane == 0 && bext)
+            bext[b * (uint64_t)F + f] = nonfinite ? make_uint2(0u, 0u) : make_uint2(order_key(blo), order_key(bhi));
+        lo = fminf(lo, blo);
+        hi = fmaxf(hi, bhi);
     }
     lo = warp_min_f32(lo);
     hi = warp_max_f32(hi);
@@ -139,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) gpz_batch_range_kernel(BatchCompress
 
 // One CTA per block of the group: the single-array fused kernel's code, with
 // the chunk's arguments in shared memory.
-template <int F>
+template <int F, bool PRE>
 __global__ void __launch_bounds__(kThreads, 5) gpz_batch_compress_kernel(BatchCompressArgs g) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
@@ -150,9 +167,9 @@ __global__ void __launch_bounds__(kThreads, 5) gpz_batch_compress_kernel(BatchCo
     __syncthreads();
     const SlotBlock idx{slot};
     if ((uint64_t)(idx.b() + 1) * kBlock <= A.n)
-        qse_block_fast<F, true>(A, dsm, S, idx);
+        qse_block_fast<F, true, SlotBlock, false, PRE>(A, dsm, S, idx);
     else
-        qse_block_fast<F, false>(A, dsm, S, idx);
+        qse_block_fast<F, false, SlotBlock, false, PRE>(A, dsm, S, idx);
 }
 
 // Blocks the fast path left to the general one (rare); the grid walks the
@@ -345,10 +362,14 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
 
 template <int F>
 bool prepare_f() {
-    return cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(gpz_batch_compress_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)qse_fast_smem_bytes()) == cudaSuccess &&
-           cudaFuncSetAttribute(gpz_batch_compress_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
-               cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_compress_kernel<F, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                100) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_compress_kernel<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)qse_fast_smem_bytes()) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_compress_kernel<F, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                100) == cudaSuccess &&
            cudaFuncSetAttribute(gpz_batch_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)qse_smem_bytes(F)) == cudaSuccess;
 }
@@ -371,8 +392,10 @@ template <int F>
 void launch_f(const BatchCompressArgs& a, int grid, cudaStream_t s, bool general) {
     if (general)
         gpz_batch_general_kernel<F><<<grid, kThreads, qse_smem_bytes(F), s>>>(a);
+    else if (a.pre)
+        gpz_batch_compress_kernel<F, true><<<grid, kThreads, qse_fast_smem_bytes(), s>>>(a);
     else
-        gpz_batch_compress_kernel<F><<<grid, kThreads, qse_fast_smem_bytes(), s>>>(a);
+        gpz_batch_compress_kernel<F, false><<<grid, kThreads, qse_fast_smem_bytes(), s>>>(a);
 }
 
 cudaError_t launch_group(const BatchCompressArgs& a, int F, int grid, cudaStream_t s, bool general) {

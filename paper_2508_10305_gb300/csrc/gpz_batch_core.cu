@@ -150,15 +150,22 @@ gpz_status core_add_decompress(BatchCore& c, const gpz_decompress_chunk& d) {
 
 gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
     if (c.chunks.empty()) return GPZ_ERR_INVALID_ARG;
-    // group by field count, keeping the caller's order within a group
-    std::stable_sort(c.chunks.begin(), c.chunks.end(), [](const BatchChunk& a, const BatchChunk& b) { return a.F < b.F; });
+    // group by field count and (compression) bound mode, keeping the caller's
+    // order within a group: relative-bound groups read each block's extremes
+    // from their range items
+    const bool bymode = c.kind == 0;
+    std::stable_sort(c.chunks.begin(), c.chunks.end(), [bymode](const BatchChunk& a, const BatchChunk& b) {
+        return a.F != b.F ? a.F < b.F : (bymode && a.mode < b.mode);
+    });
     c.groups.clear();
     uint64_t blocks = 0, temp = 0;
     for (uint32_t k = 0; k < c.count(); ++k) {
         BatchChunk& ch = c.chunks[k];
-        if (c.groups.empty() || c.groups.back().F != ch.F) {
+        const int pre = bymode && ch.mode == GPZ_EB_REL;
+        if (c.groups.empty() || c.groups.back().F != ch.F || c.groups.back().pre != pre) {
             BatchGroup g{};
             g.F = ch.F;
+            g.pre = pre;
             g.first = k;
             g.block_first = (uint32_t)blocks;
             c.groups.push_back(g);
@@ -199,6 +206,7 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
         L.zero_bytes = o;
         L.map = take(4 * blocks);
         L.rparams = take(sizeof(FieldParams) * kMaxFields * n);
+        L.bext = c.any_rel ? take(8ull * kMaxFields * blocks) : 0;
         L.offsets = take(8 * (blocks + 1));
         L.sizes = take(4 * blocks);
         L.list = take(4 * blocks);
@@ -280,6 +288,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
     a.rkeys = reinterpret_cast<uint32_t*>(ws + L.rkeys);
     a.rdone = reinterpret_cast<uint32_t*>(ws + L.rdone);
     a.rparams = reinterpret_cast<FieldParams*>(ws + L.rparams);
+    a.bext = c.any_rel ? reinterpret_cast<uint2*>(ws + L.bext) : nullptr;
     a.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
     a.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
     a.chunk_status = status;
@@ -293,6 +302,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
         a.total_blocks = g.blocks;
         a.general_list = reinterpret_cast<uint32_t*>(ws + L.list) + g.block_first;
         a.general_count = ctrl + k;
+        a.pre = g.pre && a.bext != nullptr;
         if (g.range_items > 0) {
             if (launch_batch_range(a, s) != cudaSuccess) return GPZ_ERR_CUDA;
             rec.mark("batch_range");

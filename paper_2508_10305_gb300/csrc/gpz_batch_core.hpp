@@ -20,6 +20,7 @@ namespace host {
 
 struct BatchGroup {
     int F;
+    int pre;                            // relative-bound chunks: block extremes from the range items
     uint32_t first, count;              // plan positions of the group's chunks
     uint32_t range_first, range_items;  // the group's range items
     uint32_t block_first, blocks;       // the group's blocks
@@ -27,7 +28,7 @@ struct BatchGroup {
 
 struct BatchLayout {  // byte offsets into the workspace
     uint64_t ctrl, status, rkeys, rdone, states, zero_bytes;
-    uint64_t map, rparams, offsets, sizes, list, out_sizes, temp, total;
+    uint64_t map, rparams, bext, offsets, sizes, list, out_sizes, temp, total;
 };
 
 struct BatchDevice {  // the device copy of the descriptors

@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
         const double* x = a.in[f];
         float* y = a.out32[f];
         unsigned long long kmin = ~0ull, kmax = 0ull, dmax = 0ull;
-        for (uint64_t i = (uint64_t)blockIdx.x * kF64Threads + tid; i < a.n; i += stride) {
-            const double v = __ldcs(x + i);
+        auto visit = [&](double v, uint64_t i) {
             const float r = __double2float_rn(v);
             y[i] = r;
             if (v == v) {  // not NaN
@@ -54,7 +53,17 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
                     dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
                 }
             }
+        };
+        uint64_t i = (uint64_t)blockIdx.x * kF64Threads + tid;
+        for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
+            const double v0 = __ldcs(x + i), v1 = __ldcs(x + i + stride), v2 = __ldcs(x + i + 2 * stride),
+                         v3 = __ldcs(x + i + 3 * stride);
+            visit(v0, i);
+            visit(v1, i + stride);
+            visit(v2, i + 2 * stride);
+            visit(v3, i + 3 * stride);
         }
+        for (; i < a.n; i += stride) visit(__ldcs(x + i), i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -84,9 +93,20 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
 // out64[f][i] = (double)in32[f][i]
 __global__ void __launch_bounds__(kF64Threads) gpz_f64_widen_kernel(F64Args a) {
     const uint64_t stride = (uint64_t)gridDim.x * kF64Threads;
-    for (int f = 0; f < a.F; ++f)
-        for (uint64_t i = (uint64_t)blockIdx.x * kF64Threads + threadIdx.x; i < a.n; i += stride)
-            a.out64[f][i] = (double)__ldcs(a.in32[f] + i);
+    for (int f = 0; f < a.F; ++f) {
+        const float* src = a.in32[f];
+        double* dst = a.out64[f];
+        uint64_t i = (uint64_t)blockIdx.x * kF64Threads + threadIdx.x;
+        for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
+            const float v0 = __ldcs(src + i), v1 = __ldcs(src + i + stride), v2 = __ldcs(src + i + 2 * stride),
+                        v3 = __ldcs(src + i + 3 * stride);
+            dst[i] = (double)v0;
+            dst[i + stride] = (double)v1;
+            dst[i + 2 * stride] = (double)v2;
+            dst[i + 3 * stride] = (double)v3;
+        }
+        for (; i < a.n; i += stride) dst[i] = (double)__ldcs(src + i);
+    }
 }
 
 }  // namespace gpz
