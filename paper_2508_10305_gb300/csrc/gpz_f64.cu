@@ -42,7 +42,33 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
         float* y = a.out32[f];
         unsigned long long kmin = ~0ull, kmax = 0ull, dmax = 0ull;
         auto visit = [&](double v, uint64_t i) {
-            const float r = __double2float_rn(v);
+            const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+            const int e = (int)((u >> 52) & 0x7ffu);
+            const int e32 = e - 1023 + 127;
+            if (e32 >= 1 && e32 <= 254) {
+                // fp32-normal magnitude: round to nearest even on the bits, and
+                // the rounding error |v - r| = |rem - (up ? 2^29 : 0)| * 2^(e-1075)
+                // (exact in double) as its bit pattern, with integer operations
+                const unsigned long long m = u & 0xfffffffffffffull;
+                const uint32_t m24 = (uint32_t)(m >> 29), rem = (uint32_t)(m & 0x1fffffffu);
+                const bool up = rem > 0x10000000u || (rem == 0x10000000u && (m24 & 1u));
+                const uint32_t rb = (((uint32_t)(u >> 63)) << 31) | (((uint32_t)e32 << 23) + m24 + (up ? 1u : 0u));
+                y[i] = __uint_as_float(rb);  // a carry into exponent 255 is the correct +-Inf
+                const uint32_t res = up ? 0x20000000u - rem : rem;  // < 2^29
+                unsigned long long d = 0ull;
+                if (res) {
+                    const int p = 31 - __clz(res);  // position of the leading bit
+                    d = ((unsigned long long)(e - 52 + p) << 52) |
+                        (((unsigned long long)res << (52 - p)) & 0xfffffffffffffull);
+                }
+                if (((rb >> 23) & 0xffu) == 0xffu) d = 0x7ff0000000000000ull;  // rounded past the fp32 range: |v - r| is infinite
+                dmax = max(dmax, d);
+                const unsigned long long k = order_key64(v);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+                return;
+            }
+            const float r = __double2float_rn(v);  // zero, fp32-subnormal, beyond fp32, infinite or NaN
             y[i] = r;
             if (v == v) {  // not NaN
                 const unsigned long long k = order_key64(v);
@@ -90,6 +116,16 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
     }
 }
 
+// (double)x: exact; normal values re-biased with integer operations
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (double)x;  // zero, subnormal, infinite or NaN
+    const unsigned long long u = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)u);
+}
+
 // out64[f][i] = (double)in32[f][i]
 __global__ void __launch_bounds__(kF64Threads) gpz_f64_widen_kernel(F64Args a) {
     const uint64_t stride = (uint64_t)gridDim.x * kF64Threads;
@@ -100,12 +136,12 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_widen_kernel(F64Args a) {
         for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
             const float v0 = __ldcs(src + i), v1 = __ldcs(src + i + stride), v2 = __ldcs(src + i + 2 * stride),
                         v3 = __ldcs(src + i + 3 * stride);
-            dst[i] = (double)v0;
-            dst[i + stride] = (double)v1;
-            dst[i + 2 * stride] = (double)v2;
-            dst[i + 3 * stride] = (double)v3;
+            dst[i] = widen(v0);
+            dst[i + stride] = widen(v1);
+            dst[i + 2 * stride] = widen(v2);
+            dst[i + 3 * stride] = widen(v3);
         }
-        for (; i < a.n; i += stride) dst[i] = (double)__ldcs(src + i);
+        for (; i < a.n; i += stride) dst[i] = widen(__ldcs(src + i));
     }
 }
 

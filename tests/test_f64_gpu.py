@@ -55,6 +55,28 @@ def test_f64_matches_oracle(gpz, oracle, F, n, mode, eb, special):
     assert np.all(err[fin] <= ((ebf + delta) * (1 + 1e-12))[np.nonzero(fin)[0]])
 
 
+def test_f64_rounding_edges(gpz, oracle):
+    """Values on the fp32 rounding ties, at the top of the fp32 range (one
+    rounds to infinity: refused), fp32-subnormal magnitudes and zeros take
+    the same path as the oracle."""
+    import struct
+    rng = np.random.default_rng(12)
+    f32 = rng.standard_normal(4096).astype(np.float32)
+    ties = np.array([struct.unpack("<d", struct.pack("<Q", struct.unpack("<Q", struct.pack("<d", float(v)))[0]
+                                                    | 0x10000000))[0] for v in f32])
+    x = np.stack([ties, np.concatenate([rng.standard_normal(4000) * 1e-40, np.zeros(96)]),
+                  rng.uniform(-1.0, 1.0, 4096) * 3.3e38])
+    s, p, used = gpz.compress_f64(torch.from_numpy(x).cuda(), 1e32)
+    rs, rp, rused = oracle.compress_f64(x, 1e32)
+    assert np.array_equal(np.array(used), rused) and np.array_equal(s.cpu().numpy(), rs)
+    y = x.copy()
+    y[2, 7] = 3.4028235677973366e38  # rounds to +inf in fp32
+    assert oracle.compress_f64_status(y, 1e32) == oracle.ERR_UNSUPPORTED
+    with pytest.raises(gpz.GpzError) as e:
+        gpz.compress_f64(torch.from_numpy(y).cuda(), 1e32)
+    assert e.value.status == gpz.ERR_UNSUPPORTED
+
+
 def test_f64_refuses_bounds_finer_than_fp32(gpz, oracle):
     x = np.full((1, 2048), 12345.678901234)
     x[0, 1::2] = 1.0
