@@ -302,15 +302,19 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
             const uint32_t* src = a.temp + ch->temp_base + (uint64_t)b * batch_slot_words((int)F);
             uint32_t* out = dst + payload_start + rel;
             const uint32_t L = (uint32_t)len;
-            uint32_t k = lane;
-            for (; k + 224 < L; k += 256) {  // eight words in flight per lane
+            for (uint32_t k0 = lane; k0 < L; k0 += 256) {  // eight words in flight per lane, the tail too
                 uint32_t v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldcs(src + k + 32 * u);
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t k = k0 + 32 * u;
+                    v[u] = k < L ? __ldcs(src + k) : 0u;
+                }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) out[k + 32 * u] = v[u];
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t k = k0 + 32 * u;
+                    if (k < L) out[k] = v[u];
+                }
             }
-            for (; k < L; k += 32) out[k] = __ldcs(src + k);
         } else {
             // the chunk's stream header, constants, closing table entry and size
             const uint32_t c = q - a.total_blocks;

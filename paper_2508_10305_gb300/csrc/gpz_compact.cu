@@ -156,15 +156,19 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
         const uint32_t len = __ldcg(a.table + b + 1) - __ldcg(a.table + b);  // clamped by the scan
         const uint32_t* src = a.temp + (size_t)b * a.slot_words;
         uint32_t* dst = payload + __ldcg(a.table + b);
-        uint32_t k = lane;
-        for (; k + 224 < len; k += 256) {  // eight words in flight per lane
+        for (uint32_t k0 = lane; k0 < len; k0 += 256) {  // eight words in flight per lane, the tail too
             uint32_t v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcs(src + k + 32 * u);
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t k = k0 + 32 * u;
+                v[u] = k < len ? __ldcs(src + k) : 0u;
+            }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) dst[k + 32 * u] = v[u];
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t k = k0 + 32 * u;
+                if (k < len) dst[k] = v[u];
+            }
         }
-        for (; k < len; k += 32) dst[k] = __ldcs(src + k);
     }
 }
 

@@ -535,7 +535,8 @@ struct QseFastShared {
     uint32_t maxkey[kMaxFields];
     uint32_t flags;                 // bit 0: non-finite value, bit 1: a value needs a fallback candidate
     uint32_t maxcnt, maxdelta;
-    uint32_t warp_tot[kWarps], warp_nz[kWarps], warp_last[kWarps];
+    uint32_t warp_tot[kWarps];      // per warp: count sum | non-empty bins << 16
+    uint32_t warp_last[kWarps];
     uint32_t offset;                // fused compaction: the block's offset in the payload, or kNotPlaced
 };
 
@@ -859,8 +860,10 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     }
     const uint32_t tot = c0 + c1;
     const uint32_t nz = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
-    const uint32_t incl_tot = warp_incl_sum(tot);
-    const uint32_t incl_nz = warp_incl_sum(nz);
+    // one scan of both: the counts sum to at most 1024 and the non-empty bins
+    // to at most 512, so they share a word
+    const uint32_t incl_tn = warp_incl_sum(tot | (nz << 16));
+    const uint32_t incl_tot = incl_tn & 0xffffu, incl_nz = incl_tn >> 16;
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, max(c0, c1));
     // the last non-empty bin up to this thread's (0 when none: a first id's
     // delta is the id itself), for the deltas of the unique ids
@@ -868,8 +871,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) last = max(last, __shfl_up_sync(0xffffffffu, last, o));
     if (lane == 31) {
-        S.warp_tot[w] = incl_tot;
-        S.warp_nz[w] = incl_nz;
+        S.warp_tot[w] = incl_tn;
         S.warp_last[w] = last;
     }
     if (lane == 0) atomicMax(&S.maxcnt, cmax);
@@ -877,13 +879,13 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     uint32_t base_tot = 0, base_nz = 0, U = 0, prev = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
-        const uint32_t vt = S.warp_tot[ww], vn = S.warp_nz[ww], vl = S.warp_last[ww];
+        const uint32_t vtn = S.warp_tot[ww], vl = S.warp_last[ww];
         if (ww < w) {
-            base_tot += vt;
-            base_nz += vn;
+            base_tot += vtn & 0xffffu;
+            base_nz += vtn >> 16;
             prev = max(prev, vl);
         }
-        U += vn;
+        U += vtn >> 16;
     }
     {
         const uint32_t up = __shfl_up_sync(0xffffffffu, last, 1);
