@@ -413,7 +413,7 @@ def run_gpz(args, rank, world, local):
     in_bytes = 4.0 * n * F
     value = job_gbs(world, in_bytes, args.steps, elapsed_ms / 1e3)
 
-    comp_ms = sum(stages[k][0] for k in ("range", "qse", "scan", "compact") if k in stages) / args.steps
+    comp_ms = sum(stages[k][0] for k in ("range", "info", "qse", "scan", "compact") if k in stages) / args.steps
     dec_ms = stages.get("decompress", (0.0, 1))[0] / args.steps
 
     # roofline of each kernel: algorithmic bytes per launch / mean launch time
@@ -421,6 +421,7 @@ def run_gpz(args, rank, world, local):
     payload_bytes = size - 4 * (16 + 2 * F + (n + 1023) // 1024 + 1)
     algo = {
         "range": in_bytes,                       # one read of every field
+        "info": 8.0 * (F + 1) * ((n + 1023) // 1024),  # read each block's extremes, write its widths
         "qse": in_bytes + payload_bytes,         # read the input, write the encoded blocks
         "scan": 8.0 * ((n + 1023) // 1024),      # read sizes, write offsets
         "compact": 2.0 * payload_bytes,          # read temporary blocks, write the stream
@@ -1113,7 +1114,7 @@ def run_sweep(args):
                 torch.cuda.synchronize()
                 st = gpz.gpz_stage_times()
                 gpz.gpz_set_stage_timing(False)
-                c_ms = sum(st[k][0] for k in ("range", "qse", "scan", "compact") if k in st) / reps
+                c_ms = sum(st[k][0] for k in ("range", "info", "qse", "scan", "compact") if k in st) / reps
                 d_ms = st.get("decompress", (0.0, 1))[0] / reps
                 points.append({"workload": name, "eb": eb, "G": G, "ratio": in_bytes / size,
                                "bits_per_value": 8.0 * size / (n * F), "psnr_db": psnr, "max_err_over_eb": worst,

@@ -36,7 +36,7 @@ uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * k
 uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kScanTile; }
 
 struct WsLayout {
-    uint64_t ctrl, params, states, bstates, partials, bext, sizes, list, temp, total, zero_bytes;
+    uint64_t ctrl, params, states, bstates, partials, bext, binfo, sizes, list, temp, total, zero_bytes;
 };
 
 std::atomic<int> g_fused{0};  // gpz_set_fused_compaction
@@ -58,6 +58,8 @@ WsLayout layout_of(uint64_t n, int F) {
     o += align_up((uint64_t)kRangeGridMax * F * sizeof(float2), kAlign);
     L.bext = o;  // each block's extremes from the range pass (relative bound)
     o += align_up(nb * F * 8ull, kAlign);
+    L.binfo = o;  // each block's widths and flags, derived from them
+    o += align_up(nb * 8ull, kAlign);
     L.sizes = o;
     o += align_up(nb * 4, kAlign);
     L.list = o;
@@ -234,6 +236,13 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
             const int grid = (int)(want < 1 ? 1 : (want > (uint64_t)kRangeGridMax ? kRangeGridMax : want));
             if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
             rec.mark("range");
+            if (nb > 0) {
+                if ((rc = cuda_status(launch_block_info(ra.bext, d_params, (uint32_t)nb, F,
+                                                        reinterpret_cast<unsigned long long*>(ws + L.binfo), s))) !=
+                    GPZ_OK)
+                    break;
+                rec.mark("info");
+            }
         }
 
         QseArgs qa{};
@@ -248,6 +257,7 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         qa.bulk_ok = vec_ok ? 1 : 0;
         qa.d_params = rel ? d_params : nullptr;
         qa.bext = rel ? reinterpret_cast<const uint2*>(ws + L.bext) : nullptr;
+        qa.binfo = rel ? reinterpret_cast<const unsigned long long*>(ws + L.binfo) : nullptr;
         qa.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
         qa.slot_words = slot_words_of(F);
         qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);

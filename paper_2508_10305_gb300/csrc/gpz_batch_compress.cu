@@ -38,6 +38,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.bulk_ok = ch->bulk_ok;
         A.d_params = nullptr;
         A.bext = g.pre ? g.bext + (size_t)ch->block_base * kMaxFields : nullptr;
+        A.binfo = nullptr;  // the fused kernel derives the widths from the extremes
         A.temp = g.temp + ch->temp_base;
         A.slot_words = batch_slot_words(ch->F);
         A.sizes = g.sizes + base;

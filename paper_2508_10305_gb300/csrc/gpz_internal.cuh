@@ -61,6 +61,7 @@ struct QseArgs {
     FieldParams params[kMaxFields];
     const FieldParams* d_params; // device constants (relative bound) or nullptr
     const uint2* bext;          // each block's extremes from the range pass, or nullptr
+    const unsigned long long* binfo; // each block's widths and flags (gpz_block_info_kernel), or nullptr
     uint32_t* temp;             // [nblocks][slot_words]
     uint32_t slot_words;
     uint32_t* sizes;            // [nblocks] words per block
@@ -302,6 +303,8 @@ cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);         // fast kernel
 cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s);  // the same with blocks placed directly
 cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
+cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
+                              unsigned long long* binfo, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);

@@ -653,6 +653,27 @@ __device__ __forceinline__ void quantise_append(const float (&x)[4], const bool 
 
 // Block b of the array described by a; a block the fast path cannot take is
 // appended to a.general_list as list_id.
+// The code width of one field of a block from its extremes (step 2 of the
+// fused kernel): q0 = floor(fma(x - min, 1/s, 1/2)) is monotone in x, so when
+// every value keeps its first candidate the largest code is q0 of the block
+// maximum.  big: that code reaches 2^23; exact: no first candidate of the
+// field can fail its check (first_candidate_exact).
+__device__ __forceinline__ void block_field_width(uint32_t kmin, uint32_t kmax, const FieldParams& p, uint32_t& bits,
+                                                  bool& big, bool& exact) {
+    const float m0 = from_order_key(kmin);
+    const float m = m0 == 0.0f ? 0.0f : m0;  // a zero minimum is stored as +0
+    const float mx = from_order_key(kmax);
+    const float tq = __fmaf_rn(__fsub_rn(mx, m), p.inv, 0.5f);
+    big = !(tq < 8388608.0f);
+    bits = bit_width(__float_as_uint(__fadd_rd(tq, 8388608.0f)) - kMagic23);
+    exact = first_candidate_exact(bits, m, mx, p.eb);
+}
+
+// A block's widths and flags, precomputed once per block after the range
+// pass (gpz_block_info_kernel): the width of field f in bits 5f..5f+4, and:
+constexpr int kInfoBig = 61;      // some field's largest code reaches 2^23
+constexpr int kInfoExact = 62;    // no first candidate of the block can fail its check
+
 // PRE: the range pass has already found each block's extremes (a.bext);
 // otherwise the block finds them itself.
 template <int F, bool FULL, class Idx, bool DIRECT = false, bool PRE = false>
@@ -696,6 +717,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
     }
     uint32_t kmin[F], kmax[F];  // the block's extremes, as order keys
+    unsigned long long info = 0ull;  // the block's widths and flags, when precomputed (a.binfo)
     if constexpr (PRE) {  // from the range pass; (0, 0) marks a non-finite value
 #pragma unroll
         for (int f = 0; f < F; ++f) {
@@ -703,6 +725,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
             kmin[f] = e.x;
             kmax[f] = e.y;
         }
+        if (a.binfo) info = __ldg(a.binfo + idx.b());
         __syncthreads();  // shared counters initialised (the loads are in flight)
         bool nonfinite = false;
 #pragma unroll
@@ -753,16 +776,23 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     bool big = false, exact = true;
     {
         uint32_t g[F];
+        const bool have_info = PRE && a.binfo != nullptr;  // uniform
+        if (have_info) {
+            big = (info >> kInfoBig) & 1ull;
+            exact = (info >> kInfoExact) & 1ull;
+        }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-            FieldParams p = a.d_params ? a.d_params[f] : a.params[f];
             const float m = from_order_key(kmin[f]);
-            const float mx = from_order_key(kmax[f]);
             mn[f] = m == 0.0f ? 0.0f : m;  // a zero minimum is stored as +0
-            const float tq = __fmaf_rn(__fsub_rn(mx, mn[f]), p.inv, 0.5f);
-            big |= !(tq < 8388608.0f);
-            bits[f] = bit_width(__float_as_uint(__fadd_rd(tq, 8388608.0f)) - kMagic23);
-            exact = exact && first_candidate_exact(bits[f], mn[f], mx, p.eb);
+            if (have_info) {
+                bits[f] = (uint32_t)(info >> (5 * f)) & 31u;
+            } else {
+                bool bg, ex;
+                block_field_width(kmin[f], kmax[f], a.d_params ? a.d_params[f] : a.params[f], bits[f], bg, ex);
+                big |= bg;
+                exact = exact && ex;
+            }
             g[f] = f < P ? min((uint32_t)a.G, bits[f]) : 0u;
             o[f] = f < P ? bits[f] - g[f] : 0u;
             wf[f] = f < P ? o[f] : bits[f];

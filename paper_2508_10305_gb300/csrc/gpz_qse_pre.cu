@@ -17,6 +17,50 @@ __global__ void __launch_bounds__(kThreads, 5) gpz_qse_pre_kernel(QseArgs a) {
         qse_block_fast<F, false, GridBlock, false, true>(a, dsm, S, GridBlock{});
 }
 
+// After the range pass, one thread per block: the widths and flags the fused
+// kernel's step 2 would find (block_field_width, the same arithmetic), from
+// the block's extremes and the field constants, packed as described at
+// kInfoBig.  A block with a non-finite mark is stored raw before its widths
+// are read, so those are left at 0.
+template <int F>
+__global__ void __launch_bounds__(256) gpz_block_info_kernel(const uint2* bext, const FieldParams* params,
+                                                             uint32_t nblocks, unsigned long long* info) {
+    const uint32_t b = blockIdx.x * 256u + threadIdx.x;
+    if (b >= nblocks) return;
+    unsigned long long v = 0ull;
+    bool big = false, exact = true;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const uint2 e = __ldg(bext + (size_t)b * F + f);
+        if (e.x == 0u) continue;  // non-finite
+        uint32_t bits;
+        bool bg, ex;
+        block_field_width(e.x, e.y, params[f], bits, bg, ex);
+        v |= (unsigned long long)(bits & 31u) << (5 * f);
+        big |= bg;
+        exact = exact && ex;
+    }
+    info[b] = v | ((unsigned long long)big << kInfoBig) | ((unsigned long long)exact << kInfoExact);
+}
+
+cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
+                              unsigned long long* binfo, cudaStream_t s) {
+    if (nblocks == 0) return cudaSuccess;
+    const unsigned grid = (nblocks + 255u) / 256u;
+    switch (F) {
+        case 1: gpz_block_info_kernel<1><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 2: gpz_block_info_kernel<2><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 3: gpz_block_info_kernel<3><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 4: gpz_block_info_kernel<4><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 5: gpz_block_info_kernel<5><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 6: gpz_block_info_kernel<6><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 7: gpz_block_info_kernel<7><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        case 8: gpz_block_info_kernel<8><<<grid, 256, 0, s>>>(bext, d_params, nblocks, binfo); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int F>
 cudaError_t launch_qse_pre_f(const QseArgs& a, cudaStream_t s) {
     const size_t smem = qse_fast_smem_bytes();
