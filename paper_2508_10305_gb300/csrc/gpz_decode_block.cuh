@@ -112,7 +112,7 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
     }
 }
 
-struct DecShared {
+struct DecCore {  // everything a block's decoding keeps in shared memory but its staged words
     uint16_t uniq[kMaxBins];
     uint32_t mask[32], mpre[32];
     uint32_t warp_uc[kDecWarps];  // per warp: id sum | count sum << 15
@@ -122,7 +122,10 @@ struct DecShared {
     uint4 lay[kMaxFields];      // per field: bits in the record, segId bits of a position axis,
                                 // segId mask shifted above the segOffset bits, code width
     float2 ms[kMaxFields];      // per field: block minimum, step
-    alignas(16) uint32_t stage[kDecStageWords + kDecStagePad];
+};
+
+struct DecShared : DecCore {
+    alignas(16) uint32_t stage[kDecStageWords + kDecStagePad];  // the block's words after its header
 };
 
 // Codes of fields F-1 .. 0 of four records, consumed from the least
@@ -133,7 +136,7 @@ struct DecShared {
 // a position axis, the whole code otherwise.
 template <int F, bool WIDE>
 __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4][4], uint32_t (&key)[4],
-                                              const DecShared& L, uint64_t first, int left) {
+                                              const DecCore& L, uint64_t first, int left) {
     constexpr int P = F < 3 ? F : 3;
 #pragma unroll
     for (int f = F - 1; f >= 0; --f) {
@@ -177,120 +180,93 @@ struct DecSlotBlock {
 };
 
 // Decode block idx.b() of the stream described by a (every thread of the CTA).
-template <int F, class Idx>
-__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx idx) {
+// The format checks and the block's constants (warp 0 alone; every lane
+// calls): from the stream header words hv (lane k holds word k), the block's
+// first words bw (lane k holds word k, up to the block header's end) and the
+// steps (lane f holds field f's), and the block's table entries; into S.
+template <int F>
+__device__ __forceinline__ void decode_checks(const DecArgs& a, DecCore& S, uint32_t hv, uint32_t bw, float step,
+                                              bool inside, uint32_t b, uint32_t off, uint32_t end,
+                                              uint32_t payload_words, int n_b) {
+    constexpr int P = F < 3 ? F : 3;
+    const int lane = threadIdx.x & 31;
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    const uint32_t nw = end - off;
+        bool ok = true;
+    switch (lane) {
+        case 0: ok = hv == kMagic; break;
+        case 1: ok = hv == kVersion; break;
+        case 2: ok = hv == (uint32_t)F; break;
+        case 3: ok = hv <= (uint32_t)kMaxSegBits; break;
+        case 4: ok = hv == (uint32_t)kBlock; break;
+        case 5: ok = hv <= 1u; break;
+        case 6: ok = hv == (uint32_t)(a.n & 0xffffffffull); break;
+        case 7: ok = hv == (uint32_t)(a.n >> 32); break;
+        case 8: ok = hv == a.nblocks; break;
+        case 9: break;
+        default: ok = lane >= 10 + 6 || hv == 0u; break;
+    }
+    const uint32_t G = __shfl_sync(0xffffffffu, hv, 3);
+    ok = __all_sync(0xffffffffu, ok) && inside && !(b == 0 && off != 0) &&
+         !(b + 1 == a.nblocks && end != payload_words) && end != off;
+    // the block header: mode word, minima, width bytes
+    const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
+    const bool raw = ok && (mode & 1u);
+    if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
+    // lane f holds field f: its code width, minimum and step, and its
+    // layout -- bits in the record, segId bits and mask
+    const bool fl = lane < F;
+    const uint32_t wword = __shfl_sync(0xffffffffu, bw, (1 + F + (lane >> 2)) & 31);
+    const uint32_t bits = fl ? (wword >> (8 * (lane & 3))) & 0xffu : 0u;
+    const float mn = __uint_as_float(__shfl_sync(0xffffffffu, bw, (1 + lane) & 31));
+    const uint32_t bf = bits <= 31u ? bits : 0u;
+    const uint32_t g = lane < P ? min(G, bf) : 0u;
+    const uint32_t wf = fl ? bf - g : 0u;
+    uint32_t U = 0, wd = 0, wc = 0, W = 0, keybits = 0;
+    if (ok && !raw) {
+        U = (mode >> 1) & 0x7ffu;
+        wd = (mode >> 12) & 31u;
+        wc = (mode >> 17) & 31u;
+        ok = (mode >> 22) == 0u && nw >= hdr && !__any_sync(0xffffffffu, bits > 31u);
+        // padding bytes of the last width word are zero
+        const uint32_t lastw = __shfl_sync(0xffffffffu, bw, hdr - 1);
+        if ((F & 3) != 0) ok = ok && (lastw >> (8 * (F & 3))) == 0u;
+        keybits = __reduce_add_sync(0xffffffffu, g);
+        W = __reduce_add_sync(0xffffffffu, wf);
+        // ids are below 2^keybits and counts at most 1024, so their widths
+        // are at most keybits and 11 bits: the deltas and counts then fit
+        // the words reserved for them in the staging area
+        ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) && wd <= keybits && wc <= 11u &&
+             nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
+    }
+    if (lane == 0) {
+        S.ok = ok;
+        S.raw = raw;
+        S.U = U;
+        S.wd = wd;
+        S.wc = wc;
+        S.W = W;
+        S.keybits = keybits;
+        S.G = G;
+    }
+    if (fl) {
+        S.lay[lane] = make_uint4(wf, g, mask_bits(g) << wf, bf);  // g + wf = bits <= 31
+        S.ms[lane] = make_float2(mn, step);
+    }
+}
+
+// Decode a block whose constants warp 0 has published in S (after a
+// barrier): stage holds the block's words after its header, blk the block in
+// the stream (read directly for raw blocks and records wider than 128 bits).
+template <int F>
+__device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const uint32_t* stage,
+                                            const uint32_t* blk, uint32_t b, int n_b) {
     uint16_t* uniq = S.uniq;
     uint32_t* mask = S.mask;
     uint32_t* mpre = S.mpre;
     uint32_t& s_bad = S.bad;
-    uint32_t* stage = S.stage;
-    constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const uint32_t* Sw = a.stream;
-    const uint32_t b = idx.b();
-    const int n_b = (int)((a.n - (uint64_t)b * kBlock) < (uint64_t)kBlock ? (a.n - (uint64_t)b * kBlock) : (uint64_t)kBlock);
-    const uint64_t table_start = kHeaderWords + 2ull * F;
-    const uint64_t payload_start = table_start + a.nblocks + 1;
     const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
-    if (t < 32) mask[t] = 0u;
-    if (t == 0) s_bad = 0u;
-
-    // ---- 1. where the block is (every warp, one round trip): the payload
-    // size and the block's two table entries, checked only as far as staging
-    // the block safely needs
-    const bool header_fits = payload_start <= a.total_words;
-    uint32_t hw = 0;
-    if (header_fits && lane < 3) hw = __ldg(lane == 0 ? Sw + 9 : Sw + table_start + b + (uint32_t)(lane - 1));
-    const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 0);
-    const uint32_t off = __shfl_sync(0xffffffffu, hw, 1);
-    const uint32_t end = __shfl_sync(0xffffffffu, hw, 2);
-    const bool inside =
-        header_fits && payload_start + payload_words <= a.total_words && off <= end && end <= payload_words;
-    const uint32_t* blk = Sw + payload_start + off;
-    const uint32_t nw = end - off;
-    // round trip 2: warp 0 fetches the stream header, the block header and the
-    // steps (all in bounds once the block is inside the stream), and every
-    // warp stages the block's words after its header in shared memory (all of
-    // them when they fit; the deltas and counts always fit)
-    uint32_t hv = 0, bw = 0;
-    float step = 0.0f;
-    if (w == 0) {
-        if (lane < kHeaderWords) hv = __ldg(Sw + lane);  // the host checked total_words >= kHeaderWords
-        if (inside && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
-        if (header_fits && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
-    }
-    if (inside && nw > hdr) {
-        const uint32_t nst = min(nw - hdr, kDecStageWords);
-        for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
-    }
-
-    // ---- the format checks and the block's constants: warp 0 alone, from the
-    // words it fetched above, into shared memory (the other warps go straight
-    // on to the barrier)
-    if (w == 0) {
-        bool ok = true;
-        switch (lane) {
-            case 0: ok = hv == kMagic; break;
-            case 1: ok = hv == kVersion; break;
-            case 2: ok = hv == (uint32_t)F; break;
-            case 3: ok = hv <= (uint32_t)kMaxSegBits; break;
-            case 4: ok = hv == (uint32_t)kBlock; break;
-            case 5: ok = hv <= 1u; break;
-            case 6: ok = hv == (uint32_t)(a.n & 0xffffffffull); break;
-            case 7: ok = hv == (uint32_t)(a.n >> 32); break;
-            case 8: ok = hv == a.nblocks; break;
-            case 9: break;
-            default: ok = lane >= 10 + 6 || hv == 0u; break;
-        }
-        const uint32_t G = __shfl_sync(0xffffffffu, hv, 3);
-        ok = __all_sync(0xffffffffu, ok) && inside && !(b == 0 && off != 0) &&
-             !(b + 1 == a.nblocks && end != payload_words) && end != off;
-        // the block header: mode word, minima, width bytes
-        const uint32_t mode = __shfl_sync(0xffffffffu, bw, 0);
-        const bool raw = ok && (mode & 1u);
-        if (raw) ok = mode == 1u && nw == 1u + (uint32_t)F * (uint32_t)n_b;
-        // lane f holds field f: its code width, minimum and step, and its
-        // layout -- bits in the record, segId bits and mask
-        const bool fl = lane < F;
-        const uint32_t wword = __shfl_sync(0xffffffffu, bw, (1 + F + (lane >> 2)) & 31);
-        const uint32_t bits = fl ? (wword >> (8 * (lane & 3))) & 0xffu : 0u;
-        const float mn = __uint_as_float(__shfl_sync(0xffffffffu, bw, (1 + lane) & 31));
-        const uint32_t bf = bits <= 31u ? bits : 0u;
-        const uint32_t g = lane < P ? min(G, bf) : 0u;
-        const uint32_t wf = fl ? bf - g : 0u;
-        uint32_t U = 0, wd = 0, wc = 0, W = 0, keybits = 0;
-        if (ok && !raw) {
-            U = (mode >> 1) & 0x7ffu;
-            wd = (mode >> 12) & 31u;
-            wc = (mode >> 17) & 31u;
-            ok = (mode >> 22) == 0u && nw >= hdr && !__any_sync(0xffffffffu, bits > 31u);
-            // padding bytes of the last width word are zero
-            const uint32_t lastw = __shfl_sync(0xffffffffu, bw, hdr - 1);
-            if ((F & 3) != 0) ok = ok && (lastw >> (8 * (F & 3))) == 0u;
-            keybits = __reduce_add_sync(0xffffffffu, g);
-            W = __reduce_add_sync(0xffffffffu, wf);
-            // ids are below 2^keybits and counts at most 1024, so their widths
-            // are at most keybits and 11 bits: the deltas and counts then fit
-            // the words reserved for them in the staging area
-            ok = ok && U >= 1u && U <= (uint32_t)n_b && U <= (1u << keybits) && wd <= keybits && wc <= 11u &&
-                 nw == hdr + ceil_words(U * wd) + ceil_words(U * wc) + ceil_words((uint32_t)n_b * W);
-        }
-        if (lane == 0) {
-            S.ok = ok;
-            S.raw = raw;
-            S.U = U;
-            S.wd = wd;
-            S.wc = wc;
-            S.W = W;
-            S.keybits = keybits;
-            S.G = G;
-        }
-        if (fl) {
-            S.lay[lane] = make_uint4(wf, g, mask_bits(g) << wf, bf);  // g + wf = bits <= 31
-            S.ms[lane] = make_float2(mn, step);
-        }
-    }
-    __syncthreads();
     if (!S.ok) {
         if (t == 0) set_status(a.status, kStCorrupt);
         return;  // uniform across the CTA
@@ -301,7 +277,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
 #pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = t; i < n_b; i += kDecThreads)
-                a.out[f][(uint64_t)idx.b() * kBlock + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
+                a.out[f][(uint64_t)b * kBlock + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
         return;
     }
 
@@ -388,7 +364,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         key[e] = uniq[run];
     }
     if (!fast) {
-        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)idx.b() * kBlock, key[0],
+        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)b * kBlock, key[0],
                        key[1], key[2], key[3]);
         return;
     }
@@ -411,11 +387,59 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
             rr[e][2] = rr[e][3] = 0u;
         }
     }
-    const uint64_t first = (uint64_t)idx.b() * kBlock + j0;
+    const uint64_t first = (uint64_t)b * kBlock + j0;
     if (wide)
         decode_fields<F, true>(a, rr, key, S, first, n_b - j0);
     else
         decode_fields<F, false>(a, rr, key, S, first, n_b - j0);
+}
+
+
+template <int F, class Idx>
+__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx idx) {
+    uint32_t* stage = S.stage;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const uint32_t* Sw = a.stream;
+    const uint32_t b = idx.b();
+    const int n_b = (int)((a.n - (uint64_t)b * kBlock) < (uint64_t)kBlock ? (a.n - (uint64_t)b * kBlock) : (uint64_t)kBlock);
+    const uint64_t table_start = kHeaderWords + 2ull * F;
+    const uint64_t payload_start = table_start + a.nblocks + 1;
+    const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
+    if (t < 32) S.mask[t] = 0u;
+    if (t == 0) S.bad = 0u;
+
+    // ---- 1. where the block is (every warp, one round trip): the payload
+    // size and the block's two table entries, checked only as far as staging
+    // the block safely needs
+    const bool header_fits = payload_start <= a.total_words;
+    uint32_t hw = 0;
+    if (header_fits && lane < 3) hw = __ldg(lane == 0 ? Sw + 9 : Sw + table_start + b + (uint32_t)(lane - 1));
+    const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 0);
+    const uint32_t off = __shfl_sync(0xffffffffu, hw, 1);
+    const uint32_t end = __shfl_sync(0xffffffffu, hw, 2);
+    const bool inside =
+        header_fits && payload_start + payload_words <= a.total_words && off <= end && end <= payload_words;
+    const uint32_t* blk = Sw + payload_start + off;
+    const uint32_t nw = end - off;
+    // round trip 2: warp 0 fetches the stream header, the block header and the
+    // steps (all in bounds once the block is inside the stream), and every
+    // warp stages the block's words after its header in shared memory (all of
+    // them when they fit; the deltas and counts always fit)
+    uint32_t hv = 0, bw = 0;
+    float step = 0.0f;
+    if (w == 0) {
+        if (lane < kHeaderWords) hv = __ldg(Sw + lane);  // the host checked total_words >= kHeaderWords
+        if (inside && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
+        if (header_fits && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
+    }
+    if (inside && nw > hdr) {
+        const uint32_t nst = min(nw - hdr, kDecStageWords);
+        for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
+    }
+
+    if (w == 0) decode_checks<F>(a, S, hv, bw, step, inside, b, off, end, payload_words, n_b);
+    __syncthreads();
+    decode_tail<F>(a, S, stage, blk, b, n_b);
 }
 
 }  // namespace gpz
