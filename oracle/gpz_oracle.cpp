@@ -681,3 +681,444 @@ int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int 
 }
 
 } /* extern "C" */
+
+/* ================= 64-bit intermediates (stream version 2) =================
+ *
+ * Section 5.2 (shared memory usage) keeps 32-bit intermediates by default and
+ * falls back to 64-bit ones when the value range or the precision needs
+ * them.  Reading of the paper: the 64-bit form quantises fp64 values in fp64
+ * to codes below 2^53, with the same four stages as above; what changes is
+ * the arithmetic (double instead of float, 64-bit codes), the stored minima
+ * and constants (doubles, two words each, low word first) and the version
+ * word of the stream (2).  Everything else -- block size, segment bits, key,
+ * sort, run-length + delta code, record order, offset table -- is the
+ * 32-bit form's. */
+namespace {
+
+const uint32_t STREAM_VERSION_WIDE = 2;
+/* Codes stay below 2^53, so every code converts to double exactly. */
+const double Q_LIMIT_WIDE = 9007199254740992.0;
+const uint32_t MAX_CODE_BITS_WIDE = 53;
+
+struct WideParams {
+    double eb, s, inv, ebchk;
+};
+
+/* The constants in double: the step 2 eb shrunk by 1/64 (as in the 32-bit
+ * form), its reciprocal, and the check threshold eb less two ulps, so that a
+ * rounded difference at most ebchk implies an exact difference at most eb
+ * (the rounding of x - x^ is below 2^-53 of its size). */
+void finalise_wide(double eb, WideParams* p) {
+    p->eb = eb;
+    p->s = eb * STEP_PER_EB;
+    p->inv = 1.0 / p->s;
+    p->ebchk = std::nextafter(std::nextafter(eb, 0.0), 0.0);
+}
+
+uint32_t bit_width64(uint64_t v) {
+    uint32_t w = 0;
+    while (v != 0) {
+        ++w;
+        v >>= 1;
+    }
+    return w;
+}
+
+void words_of_double(double d, uint32_t* lo, uint32_t* hi) {
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    *lo = (uint32_t)(u & 0xFFFFFFFFull);
+    *hi = (uint32_t)(u >> 32);
+}
+
+double double_of_words(uint32_t lo, uint32_t hi) {
+    const uint64_t u = (uint64_t)lo | ((uint64_t)hi << 32);
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+}
+
+double reconstruct_wide(uint64_t q, double s, double boundary_min) {
+    return std::fma((double)q, s, boundary_min);
+}
+
+bool within_bound_wide(double p, uint64_t q, const WideParams& fp, double boundary_min) {
+    return std::fabs(p - reconstruct_wide(q, fp.s, boundary_min)) <= fp.ebchk;
+}
+
+/* q = floor((p - min) / (2 eb) + 1/2) with one fused multiply-add, verified;
+ * then q - 1, then q + 1 (each only while it is a code below 2^53). */
+bool quantise_wide(double p, double boundary_min, const WideParams& fp, uint64_t* q_out) {
+    const double t = std::fma(p - boundary_min, fp.inv, 0.5);
+    if (!(t < Q_LIMIT_WIDE)) return false;
+    const uint64_t q = (uint64_t)std::floor(t);
+    if (within_bound_wide(p, q, fp, boundary_min)) {
+        *q_out = q;
+        return true;
+    }
+    if (q > 0 && within_bound_wide(p, q - 1, fp, boundary_min)) {
+        *q_out = q - 1;
+        return true;
+    }
+    if ((double)(q + 1) < Q_LIMIT_WIDE && within_bound_wide(p, q + 1, fp, boundary_min)) {
+        *q_out = q + 1;
+        return true;
+    }
+    return false;
+}
+
+/* Append / read the low w (<= 64) bits of v, LSB first. */
+void put_bits64(std::vector<uint32_t>& words, uint64_t& bitpos, uint64_t v, uint32_t w) {
+    for (uint32_t b = 0; b < w; ++b) {
+        const uint64_t t = bitpos + b;
+        if (t / 32 >= words.size()) words.resize(t / 32 + 1, 0);
+        if ((v >> b) & 1ull) words[t / 32] |= 1u << (t % 32);
+    }
+    bitpos += w;
+}
+
+uint64_t get_bits64(const uint32_t* words, uint64_t bitpos, uint32_t w) {
+    uint64_t v = 0;
+    for (uint32_t b = 0; b < w; ++b) {
+        const uint64_t t = bitpos + b;
+        v |= (uint64_t)((words[t / 32] >> (t % 32)) & 1u) << b;
+    }
+    return v;
+}
+
+/* The words of one block in the 64-bit form (see encode_block for the
+ * 32-bit form, which this follows step by step). */
+std::vector<uint32_t> encode_block_wide(const double* const* fields, int F, int n_b, int G,
+                                        const WideParams* params, std::vector<uint32_t>* perm_b) {
+    const int P = position_fields(F);
+    const uint32_t raw_words = 1 + 2 * (uint32_t)F * (uint32_t)n_b;
+    bool raw = false;
+    /* Reading of the paper: a block holding any NaN or infinity is stored raw. */
+    for (int f = 0; f < F && !raw; ++f)
+        for (int i = 0; i < n_b; ++i)
+            if (!std::isfinite(fields[f][i])) raw = true;
+
+    std::vector<double> boundary_min(F, 0.0);
+    std::vector<std::vector<uint64_t>> q(F, std::vector<uint64_t>(n_b, 0));
+    std::vector<uint32_t> bits(F, 0), g(F, 0), o(F, 0);
+    if (!raw) {
+        /* Stage 1 (Section 4.1): block minimum, codes, their widths. */
+        for (int f = 0; f < F && !raw; ++f) {
+            double mn = fields[f][0];
+            for (int i = 1; i < n_b; ++i) mn = std::min(mn, fields[f][i]);
+            if (mn == 0.0) mn = 0.0; /* a zero minimum is stored as +0 */
+            boundary_min[f] = mn;
+            uint64_t qmax = 0;
+            for (int i = 0; i < n_b; ++i) {
+                if (!quantise_wide(fields[f][i], mn, params[f], &q[f][i])) {
+                    raw = true;
+                    break;
+                }
+                qmax = std::max(qmax, q[f][i]);
+            }
+            bits[f] = bit_width64(qmax);
+        }
+    }
+    std::vector<uint32_t> key(n_b, 0), perm(n_b);
+    std::vector<uint32_t> uniq, counts, delta;
+    uint32_t w_delta = 0, w_count = 0, W = 0;
+    if (!raw) {
+        /* segId / segOffset with m = 2^o, o = bits - min(G, bits) */
+        for (int f = 0; f < P; ++f) {
+            g[f] = std::min<uint32_t>((uint32_t)G, bits[f]);
+            o[f] = bits[f] - g[f];
+        }
+        for (int i = 0; i < n_b; ++i) {
+            uint32_t k = 0;
+            for (int f = 0; f < P; ++f) k = k * (1u << g[f]) + (uint32_t)(q[f][i] >> o[f]);
+            key[i] = k;
+        }
+        /* Stage 2 (Section 4.2): stable sort by the linearised segId. */
+        for (int i = 0; i < n_b; ++i) perm[i] = (uint32_t)i;
+        std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+        /* Stage 3 (Section 4.3): runs, deltas, widths. */
+        for (int j = 0; j < n_b; ++j) {
+            const uint32_t id = key[perm[j]];
+            if (j == 0 || id != key[perm[j - 1]]) {
+                uniq.push_back(id);
+                counts.push_back(1);
+            } else {
+                counts.back() += 1;
+            }
+        }
+        uint32_t dmax = 0, cmax = 0;
+        for (size_t k = 0; k < uniq.size(); ++k) {
+            delta.push_back(k == 0 ? uniq[0] : uniq[k] - uniq[k - 1]);
+            dmax = std::max(dmax, delta.back());
+            cmax = std::max(cmax, counts[k]);
+        }
+        w_delta = bit_width(dmax);
+        w_count = bit_width(cmax);
+        for (int f = 0; f < F; ++f) W += f < P ? o[f] : bits[f];
+        const uint32_t U = (uint32_t)uniq.size();
+        const uint32_t enc = 1 + 2 * (uint32_t)F + ceil_div(F, 4) + ceil_div((uint64_t)U * w_delta, 32) +
+                             ceil_div((uint64_t)U * w_count, 32) + ceil_div((uint64_t)n_b * W, 32);
+        if (enc >= raw_words) raw = true; /* never larger than the raw block */
+    }
+
+    std::vector<uint32_t> out;
+    if (raw) {
+        out.push_back(1u);
+        for (int f = 0; f < F; ++f)
+            for (int i = 0; i < n_b; ++i) {
+                uint32_t lo, hi;
+                words_of_double(fields[f][i], &lo, &hi);
+                out.push_back(lo);
+                out.push_back(hi);
+            }
+        if (perm_b) {
+            perm_b->resize(n_b);
+            for (int i = 0; i < n_b; ++i) (*perm_b)[i] = (uint32_t)i;
+        }
+        return out;
+    }
+    const uint32_t U = (uint32_t)uniq.size();
+    out.push_back((U << 1) | (w_delta << 12) | (w_count << 17));
+    for (int f = 0; f < F; ++f) {
+        uint32_t lo, hi;
+        words_of_double(boundary_min[f], &lo, &hi);
+        out.push_back(lo);
+        out.push_back(hi);
+    }
+    std::vector<uint32_t> widths(ceil_div(F, 4), 0);
+    for (int f = 0; f < F; ++f) widths[f / 4] |= bits[f] << (8 * (f % 4));
+    out.insert(out.end(), widths.begin(), widths.end());
+    std::vector<uint32_t> d_words = pack_fixed(delta, w_delta);
+    std::vector<uint32_t> c_words = pack_fixed(counts, w_count);
+    std::vector<uint32_t> r_words(ceil_div((uint64_t)n_b * W, 32), 0);
+    uint64_t bitpos = 0;
+    for (int j = 0; j < n_b; ++j) {
+        const uint32_t i = perm[j];
+        for (int f = F - 1; f >= 0; --f) {
+            const uint32_t wf = f < P ? o[f] : bits[f];
+            const uint64_t part = f < P ? (q[f][i] & ((1ull << o[f]) - 1ull)) : q[f][i];
+            put_bits64(r_words, bitpos, part, wf);
+        }
+    }
+    out.insert(out.end(), d_words.begin(), d_words.end());
+    out.insert(out.end(), c_words.begin(), c_words.end());
+    out.insert(out.end(), r_words.begin(), r_words.end());
+    if (perm_b) *perm_b = perm;
+    return out;
+}
+
+bool decode_block_wide(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, const double* s,
+                       double* const* out) {
+    if (nwords < 1) return false;
+    if (w[0] & 1u) {
+        if (w[0] != 1u || nwords != 1 + 2 * (uint32_t)F * (uint32_t)n_b) return false;
+        for (int f = 0; f < F; ++f)
+            for (int i = 0; i < n_b; ++i) {
+                const uint32_t k = 1 + 2 * ((uint32_t)f * n_b + i);
+                out[f][i] = double_of_words(w[k], w[k + 1]);
+            }
+        return true;
+    }
+    const int P = position_fields(F);
+    const uint32_t hdr = 1 + 2 * (uint32_t)F + ceil_div(F, 4);
+    if (nwords < hdr) return false;
+    const uint32_t mode = w[0];
+    const uint32_t U = (mode >> 1) & 0x7FFu, w_delta = (mode >> 12) & 31u, w_count = (mode >> 17) & 31u;
+    if ((mode >> 22) != 0) return false;
+    std::vector<double> boundary_min(F);
+    for (int f = 0; f < F; ++f) boundary_min[f] = double_of_words(w[1 + 2 * f], w[2 + 2 * f]);
+    const uint32_t* wb = w + 1 + 2 * F;
+    std::vector<uint32_t> bits(F), g(F, 0), o(F, 0);
+    for (int f = 0; f < F; ++f) {
+        bits[f] = (wb[f / 4] >> (8 * (f % 4))) & 0xFFu;
+        if (bits[f] > MAX_CODE_BITS_WIDE) return false;
+    }
+    for (int f = F; f < 4 * (int)ceil_div(F, 4); ++f)
+        if ((wb[f / 4] >> (8 * (f % 4))) & 0xFFu) return false;
+    uint32_t key_bits = 0, W = 0;
+    for (int f = 0; f < F; ++f) {
+        if (f < P) {
+            g[f] = std::min<uint32_t>((uint32_t)G, bits[f]);
+            o[f] = bits[f] - g[f];
+            key_bits += g[f];
+        }
+        W += f < P ? o[f] : bits[f];
+    }
+    if (U < 1 || U > (uint32_t)n_b || U > (1u << key_bits)) return false;
+    if (w_delta > key_bits || w_count > bit_width(BLOCK)) return false;
+    const uint32_t d_len = ceil_div((uint64_t)U * w_delta, 32);
+    const uint32_t c_len = ceil_div((uint64_t)U * w_count, 32);
+    const uint32_t r_len = ceil_div((uint64_t)n_b * W, 32);
+    if (nwords != hdr + d_len + c_len + r_len) return false;
+    const uint32_t* d_words = w + hdr;
+    const uint32_t* c_words = d_words + d_len;
+    const uint32_t* r_words = c_words + c_len;
+    std::vector<uint32_t> uniq(U), counts(U);
+    uint64_t total = 0;
+    for (uint32_t k = 0; k < U; ++k) {
+        const uint32_t d = get_bits(d_words, (uint64_t)k * w_delta, w_delta);
+        if (k > 0 && d == 0) return false;
+        const uint64_t id = (k == 0) ? d : (uint64_t)uniq[k - 1] + d;
+        if (id >= (1ull << key_bits)) return false;
+        uniq[k] = (uint32_t)id;
+        counts[k] = get_bits(c_words, (uint64_t)k * w_count, w_count);
+        if (counts[k] == 0) return false;
+        total += counts[k];
+    }
+    if (total != (uint64_t)n_b) return false;
+    int j = 0;
+    uint64_t bitpos = 0;
+    for (uint32_t k = 0; k < U; ++k) {
+        for (uint32_t c = 0; c < counts[k]; ++c, ++j) {
+            std::vector<uint64_t> part(F, 0);
+            for (int f = F - 1; f >= 0; --f) {
+                const uint32_t wf = f < P ? o[f] : bits[f];
+                part[f] = get_bits64(r_words, bitpos, wf);
+                bitpos += wf;
+            }
+            uint32_t rest = uniq[k];
+            std::vector<uint64_t> seg_id(P, 0);
+            for (int f = P - 1; f >= 0; --f) {
+                seg_id[f] = rest % (1u << g[f]);
+                rest /= (1u << g[f]);
+            }
+            for (int f = 0; f < F; ++f) {
+                const uint64_t qv = f < P ? (seg_id[f] << o[f]) + part[f] : part[f];
+                out[f][j] = reconstruct_wide(qv, s[f], boundary_min[f]);
+            }
+        }
+    }
+    return true;
+}
+
+/* The bound of field f: eb (mode 0), or rel times the fp64 range of the
+ * non-NaN values (mode 1; rel itself when that is not a finite positive
+ * number) -- the rule of gpzo_compress_f64. */
+double field_bound_f64(const double* x, uint64_t n, int mode, double eb) {
+    if (mode == 0) return eb;
+    bool any = false;
+    double lo = 0.0, hi = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (std::isnan(x[i])) continue;
+        if (!any) {
+            lo = hi = x[i];
+            any = true;
+        } else {
+            lo = std::min(lo, x[i]);
+            hi = std::max(hi, x[i]);
+        }
+    }
+    if (!any) return eb;
+    const double range = hi - lo;
+    if (!(range > 0.0) || !std::isfinite(range)) return eb;
+    const double t = eb * range;
+    return (t > 0.0 && std::isfinite(t)) ? t : eb;
+}
+
+} /* namespace */
+
+extern "C" {
+
+int gpzo_params_wide(double eb, double* s, double* inv, double* ebchk) {
+    if (!(eb > 0.0) || !std::isfinite(eb) || !s || !inv || !ebchk) return GPZO_ERR_INVALID_ARG;
+    WideParams p;
+    finalise_wide(eb, &p);
+    *s = p.s;
+    *inv = p.inv;
+    *ebchk = p.ebchk;
+    return GPZO_OK;
+}
+
+uint64_t gpzo_bound_size_wide(uint64_t n, int F) {
+    if (F < 1 || F > MAX_FIELDS) return 0;
+    const uint64_t nb = n_blocks_of(n);
+    return 4ull * (STREAM_HEADER_WORDS + 4ull * F + (nb + 1) + nb + 2ull * F * n);
+}
+
+int gpzo_compress_wide(const double* const* fields, uint64_t n, int F, int mode, const double* eb, int G,
+                       uint8_t* out, uint64_t cap, uint64_t* out_size, uint32_t* perm, double* eb_used) {
+    if (!valid_shape(F, G) || (mode != 0 && mode != 1) || !eb || !out || !out_size)
+        return GPZO_ERR_INVALID_ARG;
+    if (n > 0 && !fields) return GPZO_ERR_INVALID_ARG;
+    for (int f = 0; f < F && n > 0; ++f)
+        if (!fields[f]) return GPZO_ERR_INVALID_ARG;
+    const uint64_t nb = n_blocks_of(n);
+    if (nb + 2ull * F * n > 0xFFFFFFFFull) return GPZO_ERR_UNSUPPORTED;
+    if (cap < gpzo_bound_size_wide(n, F)) return GPZO_ERR_CAPACITY;
+    std::vector<WideParams> params(F);
+    for (int f = 0; f < F; ++f) {
+        if (!(eb[f] > 0.0) || !std::isfinite(eb[f])) return GPZO_ERR_INVALID_ARG;
+        finalise_wide(field_bound_f64(n ? fields[f] : nullptr, n, mode, eb[f]), &params[f]);
+        if (eb_used) eb_used[f] = params[f].eb;
+    }
+    /* Stages 1-3 per block, then the three-step compaction (Section 4.4). */
+    std::vector<std::vector<uint32_t>> temp(nb);
+    std::vector<uint32_t> offsets(nb + 1, 0);
+    std::vector<const double*> block_fields(F);
+    for (uint64_t b = 0; b < nb; ++b) {
+        const uint64_t first = b * BLOCK;
+        const int n_b = (int)std::min<uint64_t>(BLOCK, n - first);
+        for (int f = 0; f < F; ++f) block_fields[f] = fields[f] + first;
+        std::vector<uint32_t> perm_b;
+        temp[b] = encode_block_wide(block_fields.data(), F, n_b, G, params.data(), perm ? &perm_b : nullptr);
+        offsets[b + 1] = offsets[b] + (uint32_t)temp[b].size();
+        if (perm)
+            for (int j = 0; j < n_b; ++j) perm[first + j] = (uint32_t)(first + perm_b[j]);
+    }
+    std::vector<uint32_t> words = {STREAM_MAGIC, STREAM_VERSION_WIDE, (uint32_t)F, (uint32_t)G, BLOCK,
+                                   (uint32_t)mode, (uint32_t)(n & 0xFFFFFFFFull), (uint32_t)(n >> 32),
+                                   (uint32_t)nb, offsets[nb]};
+    while (words.size() < STREAM_HEADER_WORDS) words.push_back(0);
+    for (int f = 0; f < F; ++f) {
+        uint32_t lo, hi;
+        words_of_double(params[f].eb, &lo, &hi);
+        words.push_back(lo);
+        words.push_back(hi);
+        words_of_double(params[f].s, &lo, &hi);
+        words.push_back(lo);
+        words.push_back(hi);
+    }
+    words.insert(words.end(), offsets.begin(), offsets.end());
+    for (uint64_t b = 0; b < nb; ++b) words.insert(words.end(), temp[b].begin(), temp[b].end());
+    const uint64_t bytes = 4ull * words.size();
+    if (bytes > cap) return GPZO_ERR_CAPACITY;
+    std::memcpy(out, words.data(), bytes);
+    *out_size = bytes;
+    return GPZO_OK;
+}
+
+int gpzo_decompress_wide(const uint8_t* in, uint64_t in_size, double* const* out, int F, uint64_t n) {
+    if (!in || F < 1 || F > MAX_FIELDS || (n > 0 && !out)) return GPZO_ERR_INVALID_ARG;
+    if (in_size % 4 != 0 || in_size < 4ull * STREAM_HEADER_WORDS) return GPZO_ERR_CORRUPT;
+    const uint64_t total_words = in_size / 4;
+    std::vector<uint32_t> w(total_words);
+    std::memcpy(w.data(), in, in_size);
+    const uint64_t nb = n_blocks_of(n);
+    const uint64_t stream_n = (uint64_t)w[6] | ((uint64_t)w[7] << 32);
+    if (w[0] != STREAM_MAGIC || w[1] != STREAM_VERSION_WIDE || w[2] != (uint32_t)F ||
+        w[3] > (uint32_t)MAX_SEG_BITS || w[4] != BLOCK || w[5] > 1 || stream_n != n || w[8] != nb)
+        return GPZO_ERR_CORRUPT;
+    for (uint32_t k = 10; k < STREAM_HEADER_WORDS; ++k)
+        if (w[k] != 0) return GPZO_ERR_CORRUPT;
+    const int G = (int)w[3];
+    const uint64_t table = STREAM_HEADER_WORDS + 4ull * F;
+    const uint64_t payload = table + nb + 1;
+    if (payload > total_words) return GPZO_ERR_CORRUPT;
+    std::vector<double> s(F);
+    for (int f = 0; f < F; ++f) s[f] = double_of_words(w[STREAM_HEADER_WORDS + 4 * f + 2], w[STREAM_HEADER_WORDS + 4 * f + 3]);
+    const uint32_t* offsets = w.data() + table;
+    if (offsets[0] != 0 || offsets[nb] != w[9] || payload + offsets[nb] > total_words) return GPZO_ERR_CORRUPT;
+    std::vector<double*> block_out(F);
+    for (uint64_t b = 0; b < nb; ++b) {
+        if (offsets[b + 1] < offsets[b]) return GPZO_ERR_CORRUPT;
+        const uint64_t first = b * BLOCK;
+        const int n_b = (int)std::min<uint64_t>(BLOCK, n - first);
+        for (int f = 0; f < F; ++f) block_out[f] = out[f] + first;
+        if (!decode_block_wide(w.data() + payload + offsets[b], offsets[b + 1] - offsets[b], F, n_b, G, s.data(),
+                               block_out.data()))
+            return GPZO_ERR_CORRUPT;
+    }
+    return GPZO_OK;
+}
+
+} /* extern "C" */

@@ -109,6 +109,25 @@ int gpzo_compress_f64(const double* const* fields, uint64_t n, int n_fields, int
 int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int n_fields,
                     uint64_t n);
 
+/* 64-bit intermediates (Section 5.2: 32-bit intermediates unless the value
+ * range or the precision needs 64-bit ones).  fp64 values are quantised in
+ * fp64 to codes below 2^53 and coded with the same four stages; the stream
+ * has version 2, its per-field constants and block minima are doubles (two
+ * words, low first), a raw block holds the fp64 values (two words each).
+ *   gpzo_params_wide:   the step s = eb * 63/32, inv = 1/s and the check
+ *                       threshold (eb less two ulps) of a bound eb.
+ *   gpzo_compress_wide: eb[f] absolute (mode 0) or relative to the field's
+ *                       fp64 range (mode 1, the rule of gpzo_compress_f64);
+ *                       eb_used (nullable) receives the absolute bounds.
+ *   gpzo_decompress_wide: the inverse, fp64 output in block-sorted order. */
+int gpzo_params_wide(double eb, double* s, double* inv, double* ebchk);
+uint64_t gpzo_bound_size_wide(uint64_t n, int n_fields);
+int gpzo_compress_wide(const double* const* fields, uint64_t n, int n_fields, int mode,
+                       const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
+                       uint64_t* out_size, uint32_t* perm, double* eb_used);
+int gpzo_decompress_wide(const uint8_t* in, uint64_t in_size, double* const* out, int n_fields,
+                         uint64_t n);
+
 #ifdef __cplusplus
 }
 #endif

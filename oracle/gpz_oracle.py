@@ -50,6 +50,13 @@ def lib():
         L.gpzo_decompress.argtypes = [u8p, C.c_uint64, P(f32p), C.c_int, C.c_uint64]
         L.gpzo_compress_f64.argtypes = [P(C.c_void_p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
                                         u8p, C.c_uint64, P(C.c_uint64), u32p, P(C.c_double)]
+        dp = P(C.c_double)
+        L.gpzo_params_wide.argtypes = [C.c_double, dp, dp, dp]
+        L.gpzo_bound_size_wide.argtypes = [C.c_uint64, C.c_int]
+        L.gpzo_bound_size_wide.restype = C.c_uint64
+        L.gpzo_compress_wide.argtypes = [P(C.c_void_p), C.c_uint64, C.c_int, C.c_int, dp, C.c_int, u8p, C.c_uint64,
+                                         P(C.c_uint64), u32p, dp]
+        L.gpzo_decompress_wide.argtypes = [u8p, C.c_uint64, P(C.c_void_p), C.c_int, C.c_uint64]
         _lib = L
     return _lib
 
@@ -251,3 +258,65 @@ def decompress_status(stream, n_fields, n):
     s = np.ascontiguousarray(stream, dtype=np.uint8)
     out = np.zeros((n_fields, n), dtype=np.float32)
     return lib().gpzo_decompress(_ptr(s, C.c_uint8), s.size, _field_ptrs(out), n_fields, n)
+
+
+# ---------------------------------------------------------------- 64-bit intermediates
+
+def params_wide(eb):
+    """(s, inv, ebchk) of the 64-bit form for an absolute bound eb."""
+    s, inv, chk = C.c_double(0), C.c_double(0), C.c_double(0)
+    rc = lib().gpzo_params_wide(float(eb), C.byref(s), C.byref(inv), C.byref(chk))
+    if rc != OK:
+        raise ValueError("gpzo_params_wide failed: %d" % rc)
+    return s.value, inv.value, chk.value
+
+
+def bound_size_wide(n, n_fields):
+    return int(lib().gpzo_bound_size_wide(n, n_fields))
+
+
+def _f64_fields(fields):
+    x = np.ascontiguousarray(fields, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[None, :]
+    return x
+
+
+def compress_wide_status(fields, eb, mode=0, seg_bits=3, want_perm=True):
+    """fp64 [F, n] -> (status, stream bytes, perm or None, absolute bounds used)."""
+    x = _f64_fields(fields)
+    F, n = x.shape
+    ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
+    cap = bound_size_wide(n, F)
+    out = np.zeros(max(cap, 4), dtype=np.uint8)
+    size = C.c_uint64(0)
+    perm = np.zeros(n, dtype=np.uint32) if want_perm else None
+    used = np.zeros(F, dtype=np.float64)
+    ptrs = (C.c_void_p * F)(*[x[f].ctypes.data for f in range(F)])
+    rc = lib().gpzo_compress_wide(ptrs, n, F, mode, _ptr(ebs, C.c_double), seg_bits, _ptr(out, C.c_uint8), cap,
+                                  C.byref(size), _ptr(perm, C.c_uint32) if want_perm else None,
+                                  _ptr(used, C.c_double))
+    return rc, out[:size.value].copy(), perm, used
+
+
+def compress_wide(fields, eb, mode=0, seg_bits=3, want_perm=True):
+    rc, s, perm, used = compress_wide_status(fields, eb, mode, seg_bits, want_perm)
+    if rc != OK:
+        raise RuntimeError("gpzo_compress_wide failed: %d" % rc)
+    return s, perm, used
+
+
+def decompress_wide_status(stream, n_fields, n):
+    """Stream bytes -> (status, [F, n] float64 in block-sorted order)."""
+    s = np.ascontiguousarray(stream, dtype=np.uint8)
+    out = np.zeros((n_fields, n), dtype=np.float64)
+    ptrs = (C.c_void_p * n_fields)(*[out[f].ctypes.data for f in range(n_fields)])
+    rc = lib().gpzo_decompress_wide(_ptr(s, C.c_uint8), s.size, ptrs, n_fields, n)
+    return rc, out
+
+
+def decompress_wide(stream, n_fields, n):
+    rc, out = decompress_wide_status(stream, n_fields, n)
+    if rc != OK:
+        raise RuntimeError("gpzo_decompress_wide failed: %d" % rc)
+    return out
