@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-compaction comparison")
     ap.add_argument("--no-aos", action="store_true", help="skip the interleaved-records round trip")
     ap.add_argument("--no-f64", action="store_true", help="skip the fp64 round trip")
+    ap.add_argument("--no-wide", action="store_true", help="skip the 64-bit-intermediate round trip")
     ap.add_argument("--workload", default="cosmology", choices=["cosmology", "batched", "served", "sweep"])
     ap.add_argument("--requests", type=int, default=4000, help="served workload: requests per arm")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served workload: admission budget")
@@ -595,6 +596,72 @@ def run_gpz(args, rank, world, local):
                          "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st_f.items()},
                          "eb_reduced": [used[f] for f in range(F)]}
         del x64, f_out, f_cws, f_dws, f_rec
+
+    # 64-bit intermediates (gpz_compress_wide / gpz_decompress_wide) on the
+    # snapshot widened to fp64 with a relative bound of 1e-12, which fp32
+    # cannot hold; the absolute bounds come from one relative call, then every
+    # timed step runs without a host synchronisation; GB/s of fp64 input
+    if not args.no_wide:
+        import ctypes as C
+        x64 = x.double()
+        wide_rel = 1e-12
+        cap = gpz.gpz_bound_size_wide(n, F)
+        w_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        w_size = torch.zeros(1, dtype=torch.int64, device=dev)
+        cws = int(gpz.lib.gpz_compress_wide_workspace_size(n, F))
+        w_cws = torch.empty(cws, dtype=torch.uint8, device=dev)
+        w_dws = torch.zeros(256, dtype=torch.uint8, device=dev)
+        w_rec = torch.empty((F, n), dtype=torch.float64, device=dev)
+        in_ptrs = gpz._ptr_array([x64[f] for f in range(F)])
+        out_ptrs = gpz._ptr_array([w_rec[f] for f in range(F)])
+        hs = gpz._stream_handle(stream)
+        h_sz = C.c_uint64(0)
+        used = (C.c_double * F)()
+        rel_params = gpz.make_params(F, wide_rel, gpz.EB_REL, SEG_BITS)
+        st = gpz.lib.gpz_compress_wide(in_ptrs, n, C.byref(rel_params), w_out.data_ptr(), cap, None, C.byref(h_sz),
+                                       None, w_cws.data_ptr(), cws, used, hs)
+        if st != gpz.OK:
+            raise gpz.GpzError(st, "gpz_compress_wide")
+        params = gpz.make_params(F, [used[f] for f in range(F)], gpz.EB_ABS, SEG_BITS)
+
+        def wide_step():
+            st1 = gpz.lib.gpz_compress_wide(in_ptrs, n, C.byref(params), w_out.data_ptr(), cap, w_size.data_ptr(),
+                                            None, None, w_cws.data_ptr(), cws, None, hs)
+            st2 = gpz.lib.gpz_decompress_wide(w_out.data_ptr(), cap, out_ptrs, F, n, w_dws.data_ptr(), 256, hs)
+            if st1 != gpz.OK or st2 != gpz.OK:
+                raise gpz.GpzError(st1 or st2, "64-bit round trip")
+
+        for _ in range(args.warmup):
+            wide_step()
+        torch.cuda.synchronize()
+        kw = min(args.steps, 20)
+        gpz.gpz_set_stage_timing(True)
+        gpz.gpz_stage_times()
+        ev0.record(stream)
+        for _ in range(kw):
+            wide_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        st_w = gpz.gpz_stage_times()
+        gpz.gpz_set_stage_timing(False)
+        stc = gpz.gpz_sync_status(w_dws)
+        if stc != gpz.OK:
+            raise gpz.GpzError(stc, "64-bit round trip (device)")
+        ms_w = ranks_max([ev0.elapsed_time(ev1) / kw], dev)[0]
+        wsize = int(w_size.item())
+        # the bound on every value, in fp64 (x reordered by a permutation from one more call)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        gpz.lib.gpz_compress_wide(in_ptrs, n, C.byref(params), w_out.data_ptr(), cap, None, C.byref(h_sz),
+                                  perm.data_ptr(), w_cws.data_ptr(), cws, None, hs)
+        gpz.lib.gpz_decompress_wide(w_out.data_ptr(), cap, out_ptrs, F, n, w_dws.data_ptr(), 256, hs)
+        torch.cuda.synchronize()
+        pl = perm.long()
+        worst = max(float(((x64[f][pl] - w_rec[f]).abs().max() / used[f]).item()) for f in range(F))
+        result["wide"] = {"value": job_gbs(world, 8.0 * n * F, 1, ms_w / 1e3), "unit": "GB/s of fp64 input",
+                          "ms_per_step": ms_w, "steps": kw, "rel_eb": wide_rel,
+                          "ratio_vs_fp64": 8.0 * n * F / wsize, "max_err_over_eb": worst,
+                          "stage_ms": {k: v[0] / max(v[1], 1) for k, v in st_w.items()}}
+        del x64, w_out, w_cws, w_dws, w_rec, perm
 
     # end to end through the public API with host buffers: H2D input ->
     # compress -> D2H stream -> H2D stream -> decompress -> D2H output, every

@@ -179,28 +179,35 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
 gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, int n_fields,
                               uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
 
-/* fp64 input and output (Section 5.1: fp64 input is down-cast to
- * fp32 when that suffices for the error bound).  gpz_compress_f64 rounds every value to fp32 on the GPU and
- * compresses the fp32 values with each field's bound reduced by the largest
+/* fp64 input and output (Section 5.1: fp64 input is down-cast to fp32 when
+ * that suffices for the error bound; Section 5.2: 64-bit intermediates when
+ * the value range or precision needs them).  gpz_compress_f64 rounds every
+ * value to fp32 on the GPU and finds each field's bound reduced by the largest
  * rounding error over its finite values,
  *     eb'_f = eb_f - max_i |x_i - RN32(x_i)|,
  * where eb_f is the given absolute bound or, with GPZ_EB_REL, the relative
  * bound times the fp64 range of the field's non-NaN values (the relative
- * bound itself when that range is not a finite positive number).  The
- * result is an ordinary stream with absolute bounds eb'_f (header mode 0),
- * and every decompressed value lies within eb_f of its fp64 input.
+ * bound itself when that range is not a finite positive number).
+ *   - Every eb'_f positive (and no finite value beyond the fp32 range): the
+ *     fp32 values are compressed with absolute bounds eb'_f into an ordinary
+ *     version-1 stream (header mode 0); h_eb_used receives eb'_f.
+ *   - Otherwise the fp64 values are compressed with the 64-bit form and
+ *     bounds eb_f (gpz_compress_wide, below; header mode = p->mode); this
+ *     needs out_capacity >= gpz_bound_size_wide(n, F), else GPZ_ERR_CAPACITY;
+ *     h_eb_used receives eb_f.
+ * Either way every decompressed value lies within eb_f of its fp64 input.
  *   d_fields:   host array of n_fields device pointers to n doubles (8-byte aligned).
  *   d_ws:       required: at least gpz_compress_f64_workspace_size(n, F) bytes,
- *               256-byte aligned (4*n*F bytes more than gpz_compress needs).
- *   h_eb_used:  host array of n_fields doubles receiving eb'_f, or NULL.
+ *               256-byte aligned.
+ *   h_eb_used:  host array of n_fields doubles, or NULL.
  * The call synchronises `stream` once (after the rounding pass, to form eb').
- * GPZ_ERR_UNSUPPORTED when some eb'_f is not positive: the bound is finer than
- * fp32 can hold for that field (or a finite value lies beyond the fp32 range).
  * Other arguments, errors and ordering as gpz_compress; gpz_sync_status(d_ws)
  * reads the device-side status.
- * gpz_decompress_f64 decompresses into an fp32 copy in its workspace (at least
- * gpz_decompress_f64_workspace_size(n, F) bytes, required) and widens it to the
- * n_fields fp64 arrays (exact); otherwise as gpz_decompress. */
+ * gpz_decompress_f64 reads the stream's version word (one synchronisation).
+ * A version-1 stream is decompressed into an fp32 copy in the workspace (at
+ * least gpz_decompress_f64_workspace_size(n, F) bytes, required) and widened
+ * to the n_fields fp64 arrays (exact); a version-2 stream goes to
+ * gpz_decompress_wide.  Otherwise as gpz_decompress. */
 uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields);
 uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields);
 gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
@@ -209,6 +216,38 @@ gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz
                             void* stream);
 gpz_status gpz_decompress_f64(const void* d_in, uint64_t in_size, double* const* d_fields, int n_fields,
                               uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
+
+/* 64-bit intermediates (Section 5.2): fp64 values quantised in fp64.  Per
+ * field: s = RN64(eb * 63/32), inv = RN64(1/s); a value's code is the first of
+ * q, q - 1, q + 1, q = floor(fma(x - min, inv, 0.5)), below 2^53 whose
+ * reconstruction fma(q, s, min) satisfies |RN64(x - x^)| <= eb less two ulps
+ * (so the exact error is at most eb); a block with a non-finite value or no
+ * such code is stored raw.  Sorting, run-length + delta + fixed-length coding
+ * and compaction are those of the 32-bit form (Sections 4.2-4.4).  Stream
+ * version 2: the header's extension holds eb and s per field as doubles (4F
+ * words, low word first), block minima are doubles, code widths reach 53 bits,
+ * and a raw block holds the fp64 values (two words each).
+ *   gpz_bound_size_wide:  the largest stream, in bytes
+ *                         (4 * (16 + 4F + 2 nblocks + 1 + 2 F n)).
+ *   gpz_compress_wide:    as gpz_compress_f64 but always this form; eb_f is
+ *                         the absolute bound or (GPZ_EB_REL) the relative bound
+ *                         times the field's fp64 range, the rule above (the
+ *                         call then synchronises once for the range);
+ *                         d_ws required, gpz_compress_wide_workspace_size(n, F)
+ *                         bytes, 256-byte aligned; h_eb_used (or NULL)
+ *                         receives eb_f.
+ *   gpz_decompress_wide:  the inverse into n_fields fp64 arrays (8-byte
+ *                         aligned), block-sorted; d_ws as gpz_decompress
+ *                         (required here).  Device-detected errors as
+ *                         gpz_decompress. */
+uint64_t gpz_bound_size_wide(uint64_t n, int n_fields);
+uint64_t gpz_compress_wide_workspace_size(uint64_t n, int n_fields);
+gpz_status gpz_compress_wide(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                             uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size,
+                             uint32_t* d_perm, void* d_ws, uint64_t ws_size, double* h_eb_used,
+                             void* stream);
+gpz_status gpz_decompress_wide(const void* d_in, uint64_t in_size, double* const* d_fields, int n_fields,
+                               uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
 
 /* Static text for a status code. */
 const char* gpz_status_str(gpz_status s);

@@ -308,6 +308,7 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         for (int f = 0; f < F; ++f) ca.params[f] = hp[f];
         ca.d_params = rel ? d_params : nullptr;
         ca.d_out_size = d_out_size ? reinterpret_cast<unsigned long long*>(d_out_size) : ws_out_size;
+        ca.version = kVersion;
         if ((rc = cuda_status(launch_compact(ca, s))) != GPZ_OK) break;
         rec.mark("compact");
 

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
             uint32_t v = 0;
             switch (lane) {
                 case 0: v = kMagic; break;
-                case 1: v = kVersion; break;
+                case 1: v = a.version; break;
                 case 2: v = (uint32_t)a.F; break;
                 case 3: v = (uint32_t)a.G; break;
                 case 4: v = (uint32_t)kBlock; break;
@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
             }
             a.stream[lane] = v;
         }
-        if (lane < 2 * a.F) {
+        if (a.ext_words) {
+            if ((uint32_t)lane < a.ext_words) a.stream[kHeaderWords + lane] = a.ext[lane];
+        } else if (lane < 2 * a.F) {
             const int f = lane >> 1;
             FieldParams p = a.params[0];
 #pragma unroll

@@ -1,5 +1,6 @@
 // gpz_f64.cu -- fp64 input and output (Section 5.1: the paper down-casts fp64
-// input to fp32 when that suffices for the error bound).  Compression rounds every value to fp32 on the GPU and
+// input to fp32 when that suffices for the error bound; otherwise the 64-bit
+// form of gpz_wide.cu, Section 5.2).  Compression rounds every value to fp32 on the GPU and
 // compresses the fp32 values with each field's bound reduced by the largest
 // rounding error over its finite values, eb' = eb - max |x - RN32(x)|, so
 // that every decompressed value lies within eb of its fp64 input.  One
@@ -7,8 +8,10 @@
 // field, the fp64 extremes of the non-NaN values and the largest rounding
 // error; the host reads those (the call synchronises once), forms eb' (a
 // relative bound is taken over the fp64 range) and calls gpz_compress with
-// absolute bounds on the copy.  Decompression runs gpz_decompress into an
-// fp32 copy and widens it to fp64 (exact).
+// absolute bounds on the copy -- or, when some eb' is not positive, calls the
+// 64-bit form with the bounds eb.  Decompression of a version-1 stream runs
+// gpz_decompress into an fp32 copy and widens it to fp64 (exact); a version-2
+// stream goes to gpz_decompress_wide.
 #include <cmath>
 #include <cstring>
 
@@ -174,7 +177,9 @@ extern "C" {
 uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields) {
     const uint64_t c = gpz_compress_workspace_size(n, n_fields);
     if (c == 0) return 0;
-    return align_up(c, kF64Align) + kResBytes + f32_bytes(n, n_fields);
+    const uint64_t narrow = align_up(c, kF64Align) + kResBytes + f32_bytes(n, n_fields);
+    const uint64_t wide = wide_workspace_size(n, n_fields);  // the 64-bit form, when fp32 cannot hold the bound
+    return narrow > wide ? narrow : wide;
 }
 
 uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields) {
@@ -235,7 +240,8 @@ gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz
         return GPZ_ERR_CUDA;
 
     // the reduced absolute bounds (each step one IEEE double operation)
-    double ebp[kMaxFields];
+    double ebp[kMaxFields], ebf[kMaxFields];
+    bool narrow = true;
     for (int f = 0; f < F; ++f) {
         double e = p->eb[f];
         const bool any = got[3 * f] != ~0ull;  // some value is not NaN
@@ -249,8 +255,16 @@ gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz
         double delta;
         std::memcpy(&delta, &got[3 * f + 2], 8);
         const volatile double reduced = e - delta;
-        if (!(reduced > 0.0) || !std::isfinite(reduced)) return GPZ_ERR_UNSUPPORTED;
+        ebf[f] = e;
         ebp[f] = reduced;
+        if (!(reduced > 0.0) || !std::isfinite(reduced)) narrow = false;
+    }
+    if (!narrow) {
+        // fp32 cannot hold some field's bound: 64-bit intermediates with the bounds eb_f
+        if (h_eb_used)
+            for (int f = 0; f < F; ++f) h_eb_used[f] = ebf[f];
+        return wide_compress(d_fields, n, F, p->seg_bits, p->mode, ebf, d_out, out_capacity, d_out_size, h_out_size,
+                             d_perm, d_ws, ws_size, s);
     }
     if (h_eb_used)
         for (int f = 0; f < F; ++f) h_eb_used[f] = ebp[f];
@@ -278,6 +292,14 @@ gpz_status gpz_decompress_f64(const void* d_in, uint64_t in_size, double* const*
     if (!d_ws || ws_size < need) return d_ws ? GPZ_ERR_CAPACITY : GPZ_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_ws) % kF64Align) return GPZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (d_in && in_size >= 8 && aligned(d_in, 4)) {
+        // the stream's version word: version 2 is the 64-bit form
+        uint32_t head[2] = {0u, 0u};
+        if (cudaMemcpyAsync(head, d_in, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return GPZ_ERR_CUDA;
+        if (head[1] == 2u) return gpz_decompress_wide(d_in, in_size, d_fields, F, n, d_ws, ws_size, stream);
+    }
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
     const uint64_t dws = align_up(gpz_decompress_workspace_size(), kF64Align);
     float* y = reinterpret_cast<float*>(ws + dws);

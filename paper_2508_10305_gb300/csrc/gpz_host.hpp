@@ -93,5 +93,12 @@ inline gpz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GPZ_OK 
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// The 64-bit form (gpz_wide.cu): its workspace, and compression with
+// absolute bounds eb[f] (the header records `mode`).
+uint64_t wide_workspace_size(uint64_t n, int F);
+gpz_status wide_compress(const double* const* d_fields, uint64_t n, int F, int G, int mode, const double* eb,
+                         void* d_out, uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size,
+                         uint32_t* d_perm, void* d_ws, uint64_t ws_size, cudaStream_t s);
+
 }  // namespace host
 }  // namespace gpz

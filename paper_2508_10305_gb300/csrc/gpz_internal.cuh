@@ -116,6 +116,9 @@ struct CompactArgs {
     FieldParams params[kMaxFields];
     const FieldParams* d_params;
     unsigned long long* d_out_size; // nullable
+    uint32_t version;           // header word 1
+    uint32_t ext_words;         // nonzero: the header extension is ext[0..ext_words) instead of (eb, s) per field
+    uint32_t ext[4 * kMaxFields];
 };
 
 struct DecArgs {

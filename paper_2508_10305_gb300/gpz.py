@@ -103,6 +103,14 @@ def _load():
     L.gpz_compress_f64.restype = C.c_int
     L.gpz_decompress_f64.argtypes = [vp, u64, vp, C.c_int, u64, vp, u64, vp]
     L.gpz_decompress_f64.restype = C.c_int
+    L.gpz_bound_size_wide.argtypes = [u64, C.c_int]
+    L.gpz_bound_size_wide.restype = u64
+    L.gpz_compress_wide_workspace_size.argtypes = [u64, C.c_int]
+    L.gpz_compress_wide_workspace_size.restype = u64
+    L.gpz_compress_wide.argtypes = [vp, u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp, u64, P(C.c_double), vp]
+    L.gpz_compress_wide.restype = C.c_int
+    L.gpz_decompress_wide.argtypes = [vp, u64, vp, C.c_int, u64, vp, u64, vp]
+    L.gpz_decompress_wide.restype = C.c_int
     L.gpz_compress_aos_workspace_size.argtypes = [u64, C.c_int]
     L.gpz_compress_aos_workspace_size.restype = u64
     L.gpz_decompress_aos_workspace_size.argtypes = [u64, C.c_int]
@@ -237,7 +245,7 @@ def compress_f64(x, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
     F, n = x.shape
     dev = x.device
     params = make_params(F, eb, mode, seg_bits)
-    cap = gpz_bound_size(n, F)
+    cap = gpz_bound_size_wide(n, F)  # room for the 64-bit form, which it falls back to
     out = torch.empty(max(cap, 16), dtype=torch.uint8, device=dev)
     ws_size = int(lib.gpz_compress_f64_workspace_size(n, F))
     ws = torch.empty(max(ws_size, 256), dtype=torch.uint8, device=dev)
@@ -266,6 +274,48 @@ def decompress_f64(stream_buf, n_fields, n, size=None, stream=None):
     st = gpz_sync_status(ws, stream)
     if st != OK:
         raise GpzError(st, "gpz_decompress_f64 (device)")
+    return out[:, :n]
+
+
+def gpz_bound_size_wide(n, n_fields):
+    return int(lib.gpz_bound_size_wide(n, n_fields))
+
+
+def compress_wide(x, eb, mode=EB_ABS, seg_bits=3, want_perm=False, stream=None):
+    """64-bit intermediates: x is a CUDA float64 tensor [F, n].  Returns
+    (stream bytes as a CUDA uint8 tensor of the exact size, perm or None, the
+    absolute bounds eb_f used)."""
+    F, n = x.shape
+    dev = x.device
+    params = make_params(F, eb, mode, seg_bits)
+    cap = gpz_bound_size_wide(n, F)
+    out = torch.empty(max(cap, 16), dtype=torch.uint8, device=dev)
+    ws_size = int(lib.gpz_compress_wide_workspace_size(n, F))
+    ws = torch.empty(max(ws_size, 256), dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if want_perm else None
+    used = (C.c_double * F)()
+    h = C.c_uint64(0)
+    st = lib.gpz_compress_wide(_ptr_array([x[f] for f in range(F)]), n, C.byref(params), out.data_ptr(), cap, None,
+                               C.byref(h), perm.data_ptr() if want_perm else None, ws.data_ptr(), ws_size, used,
+                               _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_compress_wide")
+    return out[:h.value], (perm[:n] if want_perm else None), [used[f] for f in range(F)]
+
+
+def decompress_wide(stream_buf, n_fields, n, size=None, stream=None):
+    """The inverse of compress_wide: a CUDA float64 tensor [F, n] in block-sorted order."""
+    size = stream_buf.numel() if size is None else size
+    dev = stream_buf.device
+    out = torch.empty((n_fields, max(n, 1)), dtype=torch.float64, device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    st = lib.gpz_decompress_wide(stream_buf.data_ptr(), size, _ptr_array([out[f] for f in range(n_fields)]),
+                                 n_fields, n, ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_wide")
+    st = gpz_sync_status(ws, stream)
+    if st != OK:
+        raise GpzError(st, "gpz_decompress_wide (device)")
     return out[:, :n]
 
 

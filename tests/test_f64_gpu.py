@@ -70,20 +70,35 @@ def test_f64_rounding_edges(gpz, oracle):
     rs, rp, rused = oracle.compress_f64(x, 1e32)
     assert np.array_equal(np.array(used), rused) and np.array_equal(s.cpu().numpy(), rs)
     y = x.copy()
-    y[2, 7] = 3.4028235677973366e38  # rounds to +inf in fp32
+    y[2, 7] = 3.4028235677973366e38  # rounds to +inf in fp32: the fp32 form cannot hold it
     assert oracle.compress_f64_status(y, 1e32) == oracle.ERR_UNSUPPORTED
-    with pytest.raises(gpz.GpzError) as e:
-        gpz.compress_f64(torch.from_numpy(y).cuda(), 1e32)
-    assert e.value.status == gpz.ERR_UNSUPPORTED
+    s, p, used = gpz.compress_f64(torch.from_numpy(y).cuda(), 1e32, want_perm=True)
+    rs, rp, rused = oracle.compress_wide(y, 1e32)  # the 64-bit form instead
+    assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(p.cpu().numpy().astype(np.uint32), rp)
+    assert np.array_equal(np.array(used), rused)
+    out = gpz.decompress_f64(s, 3, x.shape[1]).cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), oracle.decompress_wide(rs, 3, x.shape[1]).view(np.uint64))
 
 
-def test_f64_refuses_bounds_finer_than_fp32(gpz, oracle):
-    x = np.full((1, 2048), 12345.678901234)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_f64_falls_back_to_64_bit_intermediates(gpz, oracle, mode):
+    """A bound finer than fp32 can hold: the fp32 form refuses, and
+    gpz_compress_f64 writes the 64-bit form's stream (version 2) with the
+    full bounds; gpz_decompress_f64 reads it back through the version word."""
+    x = np.full((2, 2048), 12345.678901234)
     x[0, 1::2] = 1.0
-    with pytest.raises(gpz.GpzError) as e:
-        gpz.compress_f64(torch.from_numpy(x).cuda(), 1e-9)
-    assert e.value.status == gpz.ERR_UNSUPPORTED
-    assert oracle.compress_f64_status(x, 1e-9) == oracle.ERR_UNSUPPORTED
+    x[1] = np.linspace(-3.0, 7.0, 2048)
+    eb = 1e-9 if mode == 0 else 1e-13
+    assert oracle.compress_f64_status(x, eb, mode) == oracle.ERR_UNSUPPORTED
+    s, p, used = gpz.compress_f64(torch.from_numpy(x).cuda(), eb, mode, want_perm=True)
+    rs, rp, rused = oracle.compress_wide(x, eb, mode)
+    assert s.cpu().numpy().view(np.uint32)[1] == 2
+    assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(p.cpu().numpy().astype(np.uint32), rp)
+    assert np.array_equal(np.array(used), rused)
+    out = gpz.decompress_f64(s, 2, 2048).cpu().numpy()
+    ref = oracle.decompress_wide(rs, 2, 2048)
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+    assert np.all(np.abs(x[:, rp] - out) <= np.array(used)[:, None])
 
 
 def test_f64_full_snapshot(gpz, oracle):
