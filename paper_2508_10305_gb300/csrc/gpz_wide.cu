@@ -92,10 +92,40 @@ __device__ __forceinline__ uint32_t bit_width64(unsigned long long v) { return 6
 
 __device__ __forceinline__ unsigned long long mask64(uint32_t w) { return w >= 64u ? ~0ull : ((1ull << w) - 1ull); }
 
-// The decompressor's reconstruction of code q, checked against the bound.
+constexpr double kTwo52 = 4503599627370496.0;  // 2^52
+
+// |d| <= c for a non-NaN d and c >= 0, on the bit patterns (integer pipe).
+__device__ __forceinline__ bool abs_le(double d, double c) {
+    return ((unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull) <=
+           (unsigned long long)__double_as_longlong(c);
+}
+
+// The decompressor's reconstruction of code q, checked against the bound
+// (x is finite, so x - x^ is never NaN).
 __device__ __forceinline__ bool wide_ok(double x, unsigned long long q, const WideParams& p, double mn) {
     const double xh = __fma_rn(__ull2double_rn(q), p.s, mn);
-    return fabs(__dsub_rn(x, xh)) <= p.ebchk;
+    return abs_le(__dsub_rn(x, xh), p.ebchk);
+}
+
+// floor(t) for 0 <= t < 2^52: the sum t + 2^52 rounded down lies on the
+// integer grid of [2^52, 2^53), so its low bits are floor(t).
+__device__ __forceinline__ unsigned long long floor_small(double t) {
+    return (unsigned long long)__double_as_longlong(__dadd_rd(t, kTwo52)) - 0x4330000000000000ull;
+}
+
+// When the first candidate needs no check.  With u = 2^-53, D = x - min >= 0,
+// r = D / s and the three roundings of t = fma(RN(D), RN(1/s), 1/2):
+// |q - r| <= 1/2 + e, e <= 3.01 u r + u/2; the reconstruction
+// X = q s + min rounds to x^ with |x^ - X| <= u |X|, and the check's
+// difference rounds once more.  So |RN(x - x^)| <= (s (1/2 + e) + u |X|)(1 + u).
+// With s <= eb (63/32)(1 + u), r <= 2^40 (then e < 3.7e-4) and
+// |X| <= max|x| + s <= eb (2^45 + 2) (then u |X| / eb < 0.0040), this is
+// below 0.990 eb, under the threshold eb (1 - 2^-51) -- the 1/64 margin of
+// the step absorbs the rounding.  eb >= 2^-1000 keeps every quantity normal
+// (a subnormal difference is exact; a subnormal x^ errs by 2^-1075 at most).
+__device__ __forceinline__ bool first_candidate_exact(double bmin, double bmax, const WideParams& p) {
+    return p.eb >= 0x1p-1000 && __dsub_ru(bmax, bmin) <= p.s * 0x1p40 &&
+           fmax(fabs(bmin), fabs(bmax)) <= p.eb * 0x1p45;
 }
 
 // Candidates q, q - 1, q + 1 (codes below 2^53); false when none passes.
@@ -146,6 +176,7 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_range_kernel(WideRangeA
 
 struct WideShared {
     unsigned long long nminkey[kMaxFields];  // max of ~key: the block minimum
+    unsigned long long maxkey[kMaxFields];   // the block maximum
     unsigned long long maxq[kMaxFields];
     uint32_t flags, maxcnt, maxdelta;
     uint32_t warp_tot[kWideWarps], warp_nz[kWideWarps];
@@ -198,7 +229,7 @@ __device__ __forceinline__ void wide_write_raw(const WideQseArgs& a, uint32_t b,
 }
 
 template <int F>
-__global__ void __launch_bounds__(kWideThreads) gpz_wide_qse_kernel(WideQseArgs a) {
+__global__ void __launch_bounds__(kWideThreads, F <= 6 ? 3 : 2) gpz_wide_qse_kernel(WideQseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ WideShared S;
     constexpr int P = F < 3 ? F : 3;
@@ -216,6 +247,7 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_qse_kernel(WideQseArgs 
 
     if (t < F) {
         S.nminkey[t] = 0ull;
+        S.maxkey[t] = 0ull;
         S.maxq[t] = 0ull;
     }
     if (t == 0) {
@@ -241,16 +273,23 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_qse_kernel(WideQseArgs 
     bool nonfinite = false;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-        unsigned long long nk = 0ull;
+        unsigned long long nk = 0ull, xk = 0ull;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (valid[r]) {
-                nonfinite |= !isfinite(x[f][r]);
-                nk = max(nk, ~wide_key(x[f][r]));
+                const unsigned long long u = (unsigned long long)__double_as_longlong(x[f][r]);
+                nonfinite |= ((u >> 52) & 0x7ffu) == 0x7ffu;  // infinite or NaN
+                const unsigned long long k = wide_key(x[f][r]);
+                nk = max(nk, ~k);
+                xk = max(xk, k);
             }
         }
         nk = warp_max_u64(nk);
-        if (lane == 0 && nk) atomicMax(&S.nminkey[f], nk);
+        xk = warp_max_u64(xk);
+        if (lane == 0 && nk) {
+            atomicMax(&S.nminkey[f], nk);
+            atomicMax(&S.maxkey[f], xk);
+        }
     }
     if (__any_sync(0xffffffffu, nonfinite) && lane == 0) atomicOr(&S.flags, 1u);
     __syncthreads();
@@ -258,6 +297,21 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_qse_kernel(WideQseArgs 
         wide_write_raw<F>(a, b, n_b, t);
         return;
     }
+    // fields whose first candidates pass for certain (flag bit 2 + f)
+    if (t < F) {
+        double lo = 0.0, hi = 0.0;
+        WideParams pf = a.params[0];
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if (f == t) {
+                lo = wide_from_key(~S.nminkey[f]);
+                hi = wide_from_key(S.maxkey[f]);
+                pf = a.params[f];
+            }
+        if (first_candidate_exact(lo, hi, pf)) atomicOr(&S.flags, 4u << t);
+    }
+    __syncthreads();
+    const uint32_t exact = S.flags >> 2;
 
     // ---- 2. codes with verification
     double mn[F];
@@ -271,12 +325,20 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_qse_kernel(WideQseArgs 
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         unsigned long long qm = 0ull;
+        if ((exact >> f) & 1u) {  // uniform over the block
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            q[f][r] = 0ull;
-            if (valid[r]) {
-                fail |= !wide_quantise(x[f][r], a.params[f], mn[f], q[f][r]);
+            for (int r = 0; r < 4; ++r) {
+                q[f][r] = valid[r] ? floor_small(__fma_rn(__dsub_rn(x[f][r], mn[f]), a.params[f].inv, 0.5)) : 0ull;
                 qm = max(qm, q[f][r]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                q[f][r] = 0ull;
+                if (valid[r]) {
+                    fail |= !wide_quantise(x[f][r], a.params[f], mn[f], q[f][r]);
+                    qm = max(qm, q[f][r]);
+                }
             }
         }
         qm = warp_max_u64(qm);

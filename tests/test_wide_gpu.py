@@ -83,6 +83,25 @@ def test_special_blocks(gpz, oracle):
     check_parity(gpz, oracle, x, 1e-13, 0, 3)
 
 
+def test_unchecked_first_candidates(gpz, oracle):
+    """Blocks at the edge of the condition under which the GPU skips the
+    check of first candidates (code range up to 2^40 steps, |x| up to
+    2^45 eb): values on the half-steps between lattice points, where the
+    first candidate's error is s/2 = 0.984 eb, and the same values shifted by
+    a few ulps.  The stream must equal the oracle's, which always checks;
+    a second field just outside the condition takes the checked path."""
+    rng = np.random.default_rng(40)
+    eb, s = 1.0, 1.96875
+    base = 2.0 ** 45 - 2.0 ** 41
+    k = np.sort(rng.integers(0, 2 ** 40 - 2, size=3000)).astype(np.float64)
+    k[0], k[-1] = 0.0, 2.0 ** 40 - 2
+    x0 = base + (k + 0.5) * s  # on the 2^-6 grid, exactly representable
+    x1 = np.nextafter(np.nextafter(x0, np.inf), np.inf)
+    x2 = -(2.0 ** 46) + (k + 0.5) * s * 2  # |x| above 2^45 eb: checked
+    x = np.stack([x0, x1, x2])
+    check_parity(gpz, oracle, x, eb, 0, 3)
+
+
 def test_empty_and_single(gpz, oracle):
     check_parity(gpz, oracle, np.zeros((3, 0)), 1e-6, 0, 3)
     check_parity(gpz, oracle, np.array([[1.5], [-2.0]]), 1e-6, 1, 2)
