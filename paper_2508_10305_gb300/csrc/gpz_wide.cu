@@ -92,25 +92,35 @@ __device__ __forceinline__ uint32_t bit_width64(unsigned long long v) { return 6
 
 __device__ __forceinline__ unsigned long long mask64(uint32_t w) { return w >= 64u ? ~0ull : ((1ull << w) - 1ull); }
 
-constexpr double kTwo52 = 4503599627370496.0;  // 2^52
-
 // |d| <= c for a non-NaN d and c >= 0, on the bit patterns (integer pipe).
 __device__ __forceinline__ bool abs_le(double d, double c) {
     return ((unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull) <=
            (unsigned long long)__double_as_longlong(c);
 }
 
+// (double)q for q < 2^53 (exact), assembled on the integer pipe: exponent
+// from the leading bit, the bits below it as the fraction.
+__device__ __forceinline__ double code_to_double(unsigned long long q) {
+    const int e = 63 - __clzll((long long)q);  // -1 for q = 0
+    const unsigned long long frac = (q << ((52 - e) & 63)) & 0xfffffffffffffull;
+    const unsigned long long bits = ((unsigned long long)(1023 + e) << 52) | frac;
+    return q ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// floor(t) for 0 <= t < 2^53, on the integer pipe: the significand shifted
+// right by the fraction bits the exponent leaves below the binary point.
+__device__ __forceinline__ unsigned long long code_floor(double t) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(t);
+    const int e = (int)(u >> 52) - 1023;  // t >= 0
+    const unsigned long long m = (u & 0xfffffffffffffull) | 0x10000000000000ull;
+    return e < 0 ? 0ull : (e >= 52 ? m : (m >> (52 - e)));
+}
+
 // The decompressor's reconstruction of code q, checked against the bound
 // (x is finite, so x - x^ is never NaN).
 __device__ __forceinline__ bool wide_ok(double x, unsigned long long q, const WideParams& p, double mn) {
-    const double xh = __fma_rn(__ull2double_rn(q), p.s, mn);
+    const double xh = __fma_rn(code_to_double(q), p.s, mn);
     return abs_le(__dsub_rn(x, xh), p.ebchk);
-}
-
-// floor(t) for 0 <= t < 2^52: the sum t + 2^52 rounded down lies on the
-// integer grid of [2^52, 2^53), so its low bits are floor(t).
-__device__ __forceinline__ unsigned long long floor_small(double t) {
-    return (unsigned long long)__double_as_longlong(__dadd_rd(t, kTwo52)) - 0x4330000000000000ull;
 }
 
 // When the first candidate needs no check.  With u = 2^-53, D = x - min >= 0,
@@ -132,7 +142,7 @@ __device__ __forceinline__ bool first_candidate_exact(double bmin, double bmax, 
 __device__ __forceinline__ bool wide_quantise(double x, const WideParams& p, double mn, unsigned long long& q) {
     const double t = __fma_rn(__dsub_rn(x, mn), p.inv, 0.5);
     if (!(t < kWideLimitD)) return false;
-    const unsigned long long q0 = __double2ull_rd(t);
+    const unsigned long long q0 = code_floor(t);
     if (wide_ok(x, q0, p, mn)) {
         q = q0;
         return true;
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(kWideThreads, F <= 6 ? 3 : 2) gpz_wide_qse_ker
         if ((exact >> f) & 1u) {  // uniform over the block
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                q[f][r] = valid[r] ? floor_small(__fma_rn(__dsub_rn(x[f][r], mn[f]), a.params[f].inv, 0.5)) : 0ull;
+                q[f][r] = valid[r] ? code_floor(__fma_rn(__dsub_rn(x[f][r], mn[f]), a.params[f].inv, 0.5)) : 0ull;
                 qm = max(qm, q[f][r]);
             }
         } else {
@@ -775,7 +785,7 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecAr
             const unsigned long long part = wide_get64(R, rwords, (uint32_t)j * W + S.rshift[f], S.wf[f]);
             unsigned long long qv = part;
             if (f < P) qv |= (unsigned long long)((key >> S.kshift[f]) & ((1u << S.g[f]) - 1u)) << S.o[f];
-            a.out[f][first + j] = __fma_rn(__ull2double_rn(qv), S.s[f], S.mn[f]);
+            a.out[f][first + j] = __fma_rn(code_to_double(qv), S.s[f], S.mn[f]);  // qv < 2^53
         }
     }
 }
