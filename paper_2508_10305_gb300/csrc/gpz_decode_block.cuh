@@ -114,7 +114,7 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
 
 struct DecCore {  // everything a block's decoding keeps in shared memory but its staged words
     uint16_t uniq[kMaxBins];
-    uint32_t mask[32], mpre[32];
+    uint32_t mask[32];
     uint32_t warp_uc[kDecWarps];  // per warp: id sum | count sum << 15
     uint32_t bad;
     // the block's constants, checked by warp 0 and read by every warp
@@ -263,7 +263,6 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
                                             const uint32_t* blk, uint32_t b, int n_b) {
     uint16_t* uniq = S.uniq;
     uint32_t* mask = S.mask;
-    uint32_t* mpre = S.mpre;
     uint32_t& s_bad = S.bad;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t hdr = 1u + (uint32_t)F + (uint32_t)((F + 3) >> 2);
@@ -345,16 +344,22 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
         if (t == 0) set_status(a.status, kStCorrupt);
         return;
     }
-    if (w == 0) {
-        const uint32_t pc = __popc(mask[lane]);
-        mpre[lane] = warp_incl_sum(pc) - pc;
+    // every warp scans the 32 mask words itself (no further barrier): lane i
+    // holds word i and the run starts before it; thread t's positions lie in
+    // word t/8
+    uint32_t mrow, prow;
+    {
+        const uint32_t mw = mask[lane];
+        const uint32_t pc = __popc(mw);
+        const uint32_t pre = warp_incl_sum(pc) - pc;
+        const int src = (t >> 3) & 31;
+        mrow = __shfl_sync(0xffffffffu, mw, src);
+        prow = __shfl_sync(0xffffffffu, pre, src);
     }
-    __syncthreads();
 
     // ---- 4. positions 4t..4t+3
     const int j0 = 4 * t;
     if (j0 >= n_b) return;
-    const uint32_t mrow = mask[t >> 3], prow = mpre[t >> 3];
     uint32_t key[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {

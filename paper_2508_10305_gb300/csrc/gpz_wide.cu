@@ -561,7 +561,7 @@ struct WideDecShared {
     double mn[kMaxFields], s[kMaxFields];
     uint32_t g[kMaxFields], o[kMaxFields], wf[kMaxFields], kshift[kMaxFields], rshift[kMaxFields];
     uint16_t uniq[kMaxBins];
-    uint32_t mask[32], mpre[32], warp_uc[kWideWarps];
+    uint32_t mask[32], warp_uc[kWideWarps];
     uint32_t ok, raw, bad, U, wd, wc, W, keybits, off, nw;
 };
 
@@ -764,20 +764,23 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecAr
         if (t == 0) set_status(a.status, kStCorrupt);
         return;
     }
-    if (w == 0) {
-        const uint32_t pc = __popc(S.mask[lane]);
-        S.mpre[lane] = warp_incl_sum(pc) - pc;
-    }
-    __syncthreads();
+    // every warp scans the 32 mask words itself: lane i holds word i and the
+    // run starts before it
+    const uint32_t mword = S.mask[lane];
+    const uint32_t mpc = __popc(mword);
+    const uint32_t mpre = warp_incl_sum(mpc) - mpc;
 
     // ---- 3. positions 4t..4t+3: run, key, record fields, q = segId * 2^o + segOffset
     const uint32_t* R = blk + hdr + dwords + cwords;
+    // thread t's four positions lie in mask word t/8 (every lane shuffles)
+    const int src = (t >> 3) & 31;
+    const uint32_t mrow = __shfl_sync(0xffffffffu, mword, src), prow = __shfl_sync(0xffffffffu, mpre, src);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int j = 4 * t + e;
         if (j >= n_b) break;
         const uint32_t bit = (uint32_t)j & 31u;
-        int run = (int)(S.mpre[j >> 5] + __popc(S.mask[j >> 5] & ((2u << bit) - 1u))) - 1;
+        int run = (int)(prow + __popc(mrow & ((2u << bit) - 1u))) - 1;
         run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
         const uint32_t key = S.uniq[run];
 #pragma unroll
