@@ -521,9 +521,8 @@ __global__ void __launch_bounds__(kWideThreads, F <= 6 ? 3 : 2) gpz_wide_qse_ker
     __syncthreads();
     for (uint32_t k = t; k < dwords + cwords; k += kWideThreads) out[hdr + k] = dc[k];
 
-    // ---- 7. record words, gathered from the sorted codes: word k holds
-    // stream bits [32k, 32k + 32) of the record array, record j at bits
-    // [jW, jW + W), field F-1 least significant
+    // ---- 7. record words: record j at stream bits [jW, jW + W) of the
+    // record array, field F-1 least significant
     uint32_t wfv[F], rshift[F];
     {
         uint32_t rs = 0;
@@ -535,20 +534,95 @@ __global__ void __launch_bounds__(kWideThreads, F <= 6 ? 3 : 2) gpz_wide_qse_ker
         }
     }
     uint32_t* rout = out + hdr + dwords + cwords;
-    for (uint32_t k = t; k < rwords; k += kWideThreads) {
-        const uint32_t lo = 32u * k;
-        uint32_t acc = 0;
-        for (uint32_t j = lo / W; j < (uint32_t)n_b && j * W < lo + 32u; ++j) {
+    if (W >= 8u) {
+        // Thread t appends sorted records 4t..4t+3 (bits [4tW, 4tW + 4W), at
+        // least 32 of them) into staging words that reuse the codes' space.
+        // It writes the words inside its range itself; its first word (shared
+        // with the left neighbour) and its unfinished last word (shared with
+        // the right one) go to an exchange area in the histograms' space and
+        // are merged after a barrier.  Every staging word is written once.
+        const int j0 = 4 * t;
+        const bool act = j0 < n_b;
+        const int nrec = act ? min(4, n_b - j0) : 0;
+        unsigned long long c[4][F];
 #pragma unroll
-            for (int f = 0; f < F; ++f) {
-                if (wfv[f] == 0u) continue;
-                const int s0 = (int)(j * W + rshift[f]) - (int)lo;
-                if (s0 >= 32 || s0 + (int)wfv[f] <= 0) continue;
-                const unsigned long long v = codes[f * kBlock + j];
-                acc |= s0 >= 0 ? (uint32_t)(v << s0) : (uint32_t)(v >> -s0);
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int f = 0; f < F; ++f) c[e][f] = e < nrec ? codes[f * kBlock + j0 + e] : 0ull;
+        __syncthreads();  // every code read: their space becomes the staging words
+        uint32_t* stage = reinterpret_cast<uint32_t*>(codes);  // 2048 F words >= ceil(1024 x 53 F / 32)
+        uint32_t* xl = reinterpret_cast<uint32_t*>(hist);      // first word, when finished here
+        uint32_t* xls = xl + kWideThreads;                      // ... and whether it was
+        uint32_t* xr = xls + kWideThreads;                      // unfinished last word
+        uint32_t* xri = xr + kWideThreads;                      // ... and its index (or none)
+        constexpr uint32_t kNone = 0xffffffffu;
+        const uint32_t start = (uint32_t)j0 * W;
+        const uint32_t w0 = start >> 5;
+        uint32_t nb = start & 31u, wi = w0, first_done = 0u;
+        unsigned long long acc = 0ull;
+        auto put = [&](uint32_t v, uint32_t w) {  // w <= 32, nb < 32 on entry
+            acc |= (unsigned long long)v << nb;
+            nb += w;
+            if (nb >= 32u) {
+                const uint32_t word = (uint32_t)acc;
+                if (wi == w0) {
+                    xl[t] = word;
+                    first_done = 1u;
+                } else {
+                    stage[wi] = word;
+                }
+                acc >>= 32;
+                nb -= 32u;
+                ++wi;
+            }
+        };
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= nrec) break;
+#pragma unroll
+            for (int f = F - 1; f >= 0; --f) {
+                const uint32_t w = wfv[f];
+                const unsigned long long v = c[e][f];
+                if (w > 32u) {
+                    put((uint32_t)v, 32u);
+                    put((uint32_t)(v >> 32), w - 32u);
+                } else if (w) {
+                    put((uint32_t)v, w);
+                }
             }
         }
-        rout[k] = acc;
+        xls[t] = first_done;
+        xri[t] = (act && nb) ? wi : kNone;
+        xr[t] = (uint32_t)acc;
+        __syncthreads();
+        if (act) {
+            uint32_t val = first_done ? xl[t] : 0u;
+            if (t > 0 && xri[t - 1] == w0) val |= xr[t - 1];
+            const uint32_t last = xri[t];
+            if (last == w0) val |= xr[t];
+            stage[w0] = val;
+            const bool next_act = j0 + 4 < n_b;
+            if (last != kNone && last != w0 && !next_act) stage[last] = xr[t];  // no right neighbour takes it
+        }
+        __syncthreads();
+        for (uint32_t k = t; k < rwords; k += kWideThreads) rout[k] = stage[k];
+    } else {
+        // short records: word k gathered from the codes of the records it overlaps
+        for (uint32_t k = t; k < rwords; k += kWideThreads) {
+            const uint32_t lo = 32u * k;
+            uint32_t acc = 0;
+            for (uint32_t j = lo / W; j < (uint32_t)n_b && j * W < lo + 32u; ++j) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    if (wfv[f] == 0u) continue;
+                    const int s0 = (int)(j * W + rshift[f]) - (int)lo;
+                    if (s0 >= 32 || s0 + (int)wfv[f] <= 0) continue;
+                    const unsigned long long v = codes[f * kBlock + j];
+                    acc |= s0 >= 0 ? (uint32_t)(v << s0) : (uint32_t)(v >> -s0);
+                }
+            }
+            rout[k] = acc;
+        }
     }
     if (a.perm)
         for (int j = t; j < n_b; j += kWideThreads) a.perm[first + j] = (uint32_t)first + sperm[j];

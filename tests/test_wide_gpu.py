@@ -102,6 +102,20 @@ def test_unchecked_first_candidates(gpz, oracle):
     check_parity(gpz, oracle, x, eb, 0, 3)
 
 
+@pytest.mark.parametrize("W", [1, 3, 7, 8, 9, 13, 31, 32, 33, 41, 47])
+@pytest.mark.parametrize("n", [1025, 3000])
+def test_record_widths(gpz, oracle, W, n):
+    """One field, no segment bits, values on the lattice k s with codes up to
+    2^W - 1: records of exactly W bits (below 8 bits words are gathered from
+    the codes, from 8 bits on each thread appends its four records), with a
+    last block of 1 or 952 records."""
+    rng = np.random.default_rng(W * 7 + n)
+    s = 63 * 2.0 ** -15
+    k = rng.integers(0, 2 ** W, size=n, dtype=np.uint64)
+    k[0], k[1] = 0, 2 ** W - 1
+    check_parity(gpz, oracle, (k.astype(np.float64) * s)[None, :], 2.0 ** -10, 0, 0)
+
+
 def test_empty_and_single(gpz, oracle):
     check_parity(gpz, oracle, np.zeros((3, 0)), 1e-6, 0, 3)
     check_parity(gpz, oracle, np.array([[1.5], [-2.0]]), 1e-6, 1, 2)
