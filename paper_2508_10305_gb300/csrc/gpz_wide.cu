@@ -648,21 +648,28 @@ __device__ __forceinline__ uint32_t wide_get(const uint32_t* A, uint32_t len, ui
     return __funnelshift_r(lo, hi, sh) & (w >= 32u ? 0xffffffffu : ((1u << w) - 1u));
 }
 
-// w (<= 53) bits at bit position pos of A[0..len).
-__device__ __forceinline__ unsigned long long wide_get64(const uint32_t* A, uint32_t len, uint32_t pos, uint32_t w) {
-    if (w == 0u) return 0ull;
+// w (<= 53) bits at bit position pos of the staged record words; the two
+// words after the array keep the reads in bounds (bits read past the array
+// lie above the field and are masked off).
+__device__ __forceinline__ unsigned long long wide_get64_s(const uint32_t* A, uint32_t pos, uint32_t w) {
+    if (w == 0u) return 0ull;  // (a zero-width field may sit at the very end of the array)
     const uint32_t wi = pos >> 5, sh = pos & 31u;
-    const unsigned long long w0 = wi < len ? __ldg(A + wi) : 0u;
-    const unsigned long long w1 = wi + 1u < len ? __ldg(A + wi + 1u) : 0u;
-    const unsigned long long w2 = (sh + w > 64u && wi + 2u < len) ? __ldg(A + wi + 2u) : 0u;
-    const unsigned long long lo = w0 | (w1 << 32);
-    const unsigned long long v = sh ? ((lo >> sh) | (w2 << (64u - sh))) : lo;
+    const unsigned long long lo = (unsigned long long)A[wi] | ((unsigned long long)A[wi + 1] << 32);
+    const unsigned long long hi = A[wi + 2];
+    const unsigned long long v = sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
     return v & mask64(w);
+}
+
+// Staged record words of one block: at most ceil(1024 x 53 F / 32), plus two.
+template <int F>
+constexpr uint32_t wide_dec_smem_bytes() {
+    return 4u * ((kBlock * kWideMaxBits * (uint32_t)F + 31u) / 32u + 2u);
 }
 
 template <int F>
 __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecArgs a) {
     __shared__ WideDecShared S;
+    extern __shared__ __align__(16) uint32_t srec[];  // the block's record words
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t* Sw = a.stream;
@@ -782,11 +789,16 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecAr
         return;
     }
 
-    // ---- 2. unique ids and run starts (Section 4.3, undone)
+    // ---- 2. unique ids and run starts (Section 4.3, undone); the record
+    // words are copied to shared memory meanwhile (visible after the barriers)
     const uint32_t U = S.U, wd = S.wd, wc = S.wc, W = S.W, keybits = S.keybits;
     const uint32_t dwords = ceil_words(U * wd), cwords = ceil_words(U * wc);
-    const uint32_t rwords = S.nw - hdr - dwords - cwords;
+    const uint32_t rwords = S.nw - hdr - dwords - cwords;  // <= ceil(n_b W / 32) by the size check
     const uint32_t idlimit = 1u << keybits;
+    {
+        const uint32_t* R = blk + hdr + dwords + cwords;
+        for (uint32_t k = t; k < rwords; k += kWideThreads) srec[k] = __ldg(R + k);
+    }
     {
         const uint32_t* D = blk + hdr;
         const uint32_t* Cc = D + dwords;
@@ -845,24 +857,40 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecAr
     const uint32_t mpre = warp_incl_sum(mpc) - mpc;
 
     // ---- 3. positions 4t..4t+3: run, key, record fields, q = segId * 2^o + segOffset
-    const uint32_t* R = blk + hdr + dwords + cwords;
     // thread t's four positions lie in mask word t/8 (every lane shuffles)
     const int src = (t >> 3) & 31;
     const uint32_t mrow = __shfl_sync(0xffffffffu, mword, src), prow = __shfl_sync(0xffffffffu, mpre, src);
+    const int j0 = 4 * t;
+    if (j0 >= n_b) return;
+    const int left = n_b - j0;
+    uint32_t key[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int j = 4 * t + e;
-        if (j >= n_b) break;
-        const uint32_t bit = (uint32_t)j & 31u;
+        const uint32_t bit = (uint32_t)(j0 + e) & 31u;
         int run = (int)(prow + __popc(mrow & ((2u << bit) - 1u))) - 1;
         run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
-        const uint32_t key = S.uniq[run];
+        key[e] = S.uniq[run];
+    }
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-            const unsigned long long part = wide_get64(R, rwords, (uint32_t)j * W + S.rshift[f], S.wf[f]);
-            unsigned long long qv = part;
-            if (f < P) qv |= (unsigned long long)((key >> S.kshift[f]) & ((1u << S.g[f]) - 1u)) << S.o[f];
-            a.out[f][first + j] = __fma_rn(code_to_double(qv), S.s[f], S.mn[f]);  // qv < 2^53
+    for (int f = 0; f < F; ++f) {
+        const uint32_t wf = S.wf[f], rs = S.rshift[f], ks = S.kshift[f], gm = (1u << S.g[f]) - 1u, of = S.o[f];
+        const double sf = S.s[f], mf = S.mn[f];
+        double v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t j = (uint32_t)min(j0 + e, n_b - 1);  // positions past the block repeat the last
+            unsigned long long qv = wide_get64_s(srec, j * W + rs, wf);
+            if (f < P) qv |= (unsigned long long)((key[e] >> ks) & gm) << of;
+            v[e] = __fma_rn(code_to_double(qv), sf, mf);  // qv < 2^53
+        }
+        double* dst = a.out[f] + first + j0;
+        if (left >= 4 && (reinterpret_cast<uintptr_t>(a.out[f]) & 15u) == 0) {
+            reinterpret_cast<double2*>(dst)[0] = make_double2(v[0], v[1]);
+            reinterpret_cast<double2*>(dst)[1] = make_double2(v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (e < left) dst[e] = v[e];
         }
     }
 }
@@ -884,7 +912,16 @@ cudaError_t launch_wide_qse_f(const WideQseArgs& a, uint32_t nblocks, cudaStream
 
 template <int F>
 cudaError_t launch_wide_dec_f(const WideDecArgs& a, cudaStream_t s) {
-    gpz_wide_decode_kernel<F><<<a.nblocks, kWideThreads, 0, s>>>(a);
+    constexpr uint32_t smem = wide_dec_smem_bytes<F>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gpz_wide_decode_kernel<F><<<a.nblocks, kWideThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
