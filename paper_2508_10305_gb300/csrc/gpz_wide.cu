@@ -82,10 +82,13 @@ __device__ __forceinline__ double wide_from_key(unsigned long long k) {
     return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
+// Maximum over the warp (every lane calls it): the largest high word, then
+// the largest low word among the lanes that hold it (two redux operations).
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    const uint32_t mh = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
 __device__ __forceinline__ uint32_t bit_width64(unsigned long long v) { return 64u - (uint32_t)__clzll((long long)v); }
