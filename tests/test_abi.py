@@ -214,3 +214,50 @@ def test_server_argument_errors_need_no_device(gpz):
     assert L.gpz_server_stats_get(None, None) == gpz.ERR_INVALID_ARG
     assert L.gpz_server_now_ns(None) == 0
     L.gpz_server_destroy(None)
+
+
+def test_wide_sizes_match_oracle(gpz, oracle):
+    """The 64-bit form's bound: 4 (16 + 4F + 2 nblocks + 1 + 2 F n) bytes."""
+    for n in (0, 1, 1023, 1025, 10**6):
+        for F in (1, 3, 6, 8):
+            nb = (n + 1023) // 1024
+            assert gpz.gpz_bound_size_wide(n, F) == oracle.bound_size_wide(n, F) == 4 * (16 + 4 * F + 2 * nb + 1 + 2 * F * n)
+            assert gpz.lib.gpz_compress_wide_workspace_size(n, F) >= 8 * F * n
+    assert gpz.gpz_bound_size_wide(10, 0) == 0 and gpz.gpz_bound_size_wide(10, 9) == 0
+    # gpz_compress_f64 may fall back to the 64-bit form: its workspace covers that form's
+    for n, F in ((1000, 3), (1 << 20, 6)):
+        assert gpz.lib.gpz_compress_f64_workspace_size(n, F) >= gpz.lib.gpz_compress_wide_workspace_size(n, F)
+
+
+def test_wide_argument_errors_need_no_device(gpz):
+    """Invalid arguments to the 64-bit entry points are rejected before anything is enqueued."""
+    L = gpz.lib
+    p = gpz.make_params(3, 1e-9)
+    fields = (C.c_void_p * 3)(4096, 8192, 12288)
+    out = C.c_void_p(1 << 20)
+    ws = C.c_void_p(1 << 24)
+    n = 1000
+    need = int(L.gpz_compress_wide_workspace_size(n, 3))
+    cap = gpz.gpz_bound_size_wide(n, 3)
+
+    def comp(params, flds=fields, o=out, c=cap, w=ws, wsz=need):
+        return L.gpz_compress_wide(flds, n, params, o, c, None, None, None, w, wsz, None, None)
+
+    assert comp(None) == gpz.ERR_INVALID_ARG
+    bad = gpz.make_params(3, 1e-9)
+    bad.eb[2] = -1.0
+    assert comp(C.byref(bad)) == gpz.ERR_INVALID_ARG
+    assert comp(C.byref(gpz.make_params(3, 1e-9, seg_bits=4))) == gpz.ERR_INVALID_ARG
+    assert comp(C.byref(p), flds=(C.c_void_p * 3)(4096, 8196, 12288)) == gpz.ERR_INVALID_ARG  # field not 8-byte aligned
+    assert comp(C.byref(p), w=None) == gpz.ERR_INVALID_ARG                                     # workspace required
+    assert comp(C.byref(p), w=C.c_void_p((1 << 24) + 64)) == gpz.ERR_INVALID_ARG              # not 256-byte aligned
+    assert comp(C.byref(p), wsz=need - 1) == gpz.ERR_CAPACITY
+    assert comp(C.byref(p), c=cap - 4) == gpz.ERR_CAPACITY                                     # absolute bound: no range pass first
+    assert comp(C.byref(p), o=C.c_void_p((1 << 20) + 2)) == gpz.ERR_INVALID_ARG
+    outs = (C.c_void_p * 3)(4096, 8192, 12288)
+    assert L.gpz_decompress_wide(None, 1024, outs, 3, n, ws, 256, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_decompress_wide(out, 1024, outs, 0, n, ws, 256, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_decompress_wide(out, 1024, outs, 3, n, None, 256, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_decompress_wide(out, 1024, outs, 3, n, ws, 8, None) == gpz.ERR_CAPACITY
+    assert L.gpz_decompress_wide(out, 1024, (C.c_void_p * 3)(4096, 8196, 12288), 3, n, ws, 256, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_decompress_wide(out, 60, outs, 3, n, ws, 256, None) == gpz.ERR_CORRUPT       # shorter than the header
