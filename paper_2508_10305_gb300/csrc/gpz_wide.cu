@@ -20,8 +20,9 @@
 // not smaller.
 //
 // Kernels: a range pass (relative bounds), one CTA per block for the stages
-// (the codes sorted into shared memory, the record words gathered from them),
-// the scan and copy of the 32-bit form, and one CTA per block to decode.
+// (the codes sorted into shared memory, each thread's four sorted records
+// appended into staging words), the scan and copy of the 32-bit form, and one
+// CTA per block to decode (the record words staged in shared memory).
 #include <cmath>
 #include <cstring>
 
