@@ -1029,6 +1029,21 @@ int gpzo_params_wide(double eb, double* s, double* inv, double* ebchk) {
     return GPZO_OK;
 }
 
+int gpzo_wide_first_candidate_failures(const double* x, uint64_t n, double boundary_min, double eb,
+                                       uint64_t* failures) {
+    if ((n > 0 && !x) || !failures || !(eb > 0.0) || !std::isfinite(eb)) return GPZO_ERR_INVALID_ARG;
+    WideParams p;
+    finalise_wide(eb, &p);
+    uint64_t bad = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        /* the first candidate of quantise_wide, and its check */
+        const double t = std::fma(x[i] - boundary_min, p.inv, 0.5);
+        if (!(t < Q_LIMIT_WIDE) || !within_bound_wide(x[i], (uint64_t)std::floor(t), p, boundary_min)) ++bad;
+    }
+    *failures = bad;
+    return GPZO_OK;
+}
+
 uint64_t gpzo_bound_size_wide(uint64_t n, int F) {
     if (F < 1 || F > MAX_FIELDS) return 0;
     const uint64_t nb = n_blocks_of(n);

@@ -128,6 +128,12 @@ int gpzo_compress_wide(const double* const* fields, uint64_t n, int n_fields, in
 int gpzo_decompress_wide(const uint8_t* in, uint64_t in_size, double* const* out, int n_fields,
                          uint64_t n);
 
+/* How many of x[0..n) fail the check with their first candidate
+ * floor(fma(x - boundary_min, inv, 0.5)) under bound eb (the 64-bit form's
+ * arithmetic); tests use it to probe when the check can be skipped. */
+int gpzo_wide_first_candidate_failures(const double* x, uint64_t n, double boundary_min, double eb,
+                                       uint64_t* failures);
+
 #ifdef __cplusplus
 }
 #endif

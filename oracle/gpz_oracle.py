@@ -57,6 +57,7 @@ def lib():
         L.gpzo_compress_wide.argtypes = [P(C.c_void_p), C.c_uint64, C.c_int, C.c_int, dp, C.c_int, u8p, C.c_uint64,
                                          P(C.c_uint64), u32p, dp]
         L.gpzo_decompress_wide.argtypes = [u8p, C.c_uint64, P(C.c_void_p), C.c_int, C.c_uint64]
+        L.gpzo_wide_first_candidate_failures.argtypes = [dp, C.c_uint64, C.c_double, C.c_double, P(C.c_uint64)]
         _lib = L
     return _lib
 
@@ -320,3 +321,14 @@ def decompress_wide(stream, n_fields, n):
     if rc != OK:
         raise RuntimeError("gpzo_decompress_wide failed: %d" % rc)
     return out
+
+
+def wide_first_candidate_failures(x, boundary_min, eb):
+    """Values of x whose first candidate fails the 64-bit form's check."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = C.c_uint64(0)
+    rc = lib().gpzo_wide_first_candidate_failures(_ptr(x, C.c_double), x.size, float(boundary_min), float(eb),
+                                                  C.byref(out))
+    if rc != OK:
+        raise ValueError("gpzo_wide_first_candidate_failures failed: %d" % rc)
+    return int(out.value)
