@@ -22,7 +22,7 @@ constexpr int kAosThreads = 256;
 template <int F>
 __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float* __restrict__ aos,
                                                                      float* __restrict__ soa, uint64_t n,
-                                                                     uint64_t ld) {
+                                                                     uint64_t ld, bool vec) {
     __shared__ float tile[(kAosTile + 1) * F];
     const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
     for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
@@ -30,14 +30,37 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float
         const int cnt = (int)min((uint64_t)kAosTile, n - first);
         const int words = cnt * F;
         const float* src = aos + first * (uint64_t)F;
-        for (int k = threadIdx.x; k < words; k += kAosThreads) {
-            const int i = k / F, f = k - i * F;
-            tile[f * (kAosTile + 1) + i] = __ldcs(src + k);  // field-major in shared memory, padded rows
-        }
-        __syncthreads();
+        if (vec && cnt == kAosTile) {  // whole tile, 16-byte aligned on both sides: 16-byte loads and stores
+            const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-        for (int f = 0; f < F; ++f)
-            for (int i = threadIdx.x; i < cnt; i += kAosThreads) soa[(uint64_t)f * ld + first + i] = tile[f * (kAosTile + 1) + i];
+            for (int k4 = threadIdx.x; k4 < kAosTile * F / 4; k4 += kAosThreads) {
+                const float4 v = __ldcs(s4 + k4);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = 4 * k4 + c, i = k / F, f = k - i * F;
+                    tile[f * (kAosTile + 1) + i] = e[c];  // field-major in shared memory, padded rows
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const float* row = tile + f * (kAosTile + 1);
+                const int i = 4 * threadIdx.x;  // 256 threads x 4 = the tile
+                __stcs(reinterpret_cast<float4*>(soa + (uint64_t)f * ld + first + i),
+                       make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]));
+            }
+        } else {
+            for (int k = threadIdx.x; k < words; k += kAosThreads) {
+                const int i = k / F, f = k - i * F;
+                tile[f * (kAosTile + 1) + i] = __ldcs(src + k);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < F; ++f)
+                for (int i = threadIdx.x; i < cnt; i += kAosThreads)
+                    soa[(uint64_t)f * ld + first + i] = tile[f * (kAosTile + 1) + i];
+        }
         __syncthreads();
     }
 }
@@ -46,22 +69,47 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float
 template <int F>
 __global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float* __restrict__ soa,
                                                                      float* __restrict__ aos, uint64_t n,
-                                                                     uint64_t ld) {
+                                                                     uint64_t ld, bool vec) {
     __shared__ float tile[(kAosTile + 1) * F];
     const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
     for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
         const uint64_t first = tl * kAosTile;
         const int cnt = (int)min((uint64_t)kAosTile, n - first);
-#pragma unroll
-        for (int f = 0; f < F; ++f)
-            for (int i = threadIdx.x; i < cnt; i += kAosThreads)
-                tile[f * (kAosTile + 1) + i] = __ldcs(soa + (uint64_t)f * ld + first + i);
-        __syncthreads();
         const int words = cnt * F;
         float* dst = aos + first * (uint64_t)F;
-        for (int k = threadIdx.x; k < words; k += kAosThreads) {
-            const int i = k / F, f = k - i * F;
-            dst[k] = tile[f * (kAosTile + 1) + i];
+        if (vec && cnt == kAosTile) {  // whole tile, 16-byte aligned on both sides
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const int i = 4 * threadIdx.x;
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(soa + (uint64_t)f * ld + first + i));
+                float* row = tile + f * (kAosTile + 1);
+                row[i] = v.x;
+                row[i + 1] = v.y;
+                row[i + 2] = v.z;
+                row[i + 3] = v.w;
+            }
+            __syncthreads();
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int k4 = threadIdx.x; k4 < kAosTile * F / 4; k4 += kAosThreads) {
+                float e[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = 4 * k4 + c, i = k / F, f = k - i * F;
+                    e[c] = tile[f * (kAosTile + 1) + i];
+                }
+                __stcs(d4 + k4, make_float4(e[0], e[1], e[2], e[3]));
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f)
+                for (int i = threadIdx.x; i < cnt; i += kAosThreads)
+                    tile[f * (kAosTile + 1) + i] = __ldcs(soa + (uint64_t)f * ld + first + i);
+            __syncthreads();
+            for (int k = threadIdx.x; k < words; k += kAosThreads) {
+                const int i = k / F, f = k - i * F;
+                dst[k] = tile[f * (kAosTile + 1) + i];
+            }
         }
         __syncthreads();
     }
@@ -70,10 +118,14 @@ __global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float
 template <int F>
 cudaError_t launch_transpose_f(bool to_soa, const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
                                cudaStream_t s) {
+    // 16-byte accesses when both bases are 16-byte aligned: a whole tile of the
+    // interleaved array starts at a multiple of 1024 F floats, a field of the
+    // other at a multiple of ld (a multiple of 4) plus a multiple of 1024
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && ld % 4 == 0;
     if (to_soa)
-        gpz_aos_to_soa_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld);
+        gpz_aos_to_soa_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec);
     else
-        gpz_soa_to_aos_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld);
+        gpz_soa_to_aos_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec);
     return cudaGetLastError();
 }
 
