@@ -115,6 +115,155 @@ __global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float
     }
 }
 
+__device__ __forceinline__ uint32_t aos_order_key(float x) {  // unsigned order = numeric order
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float aos_from_order_key(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The interleaved-to-fields transpose that also does the relative bound's
+// range pass: while a tile (one 1,024-particle block) sits in shared memory,
+// warp f reduces field f's row to the block's extremes (order keys, or
+// (0, 0) when the row holds a NaN or an infinity) and the CTA's running
+// extremes over the non-NaN values; the last CTA folds the CTAs' partials
+// into the per-field constants.  The outputs are those of the range pass of
+// gpz_compress, in the same places of its workspace, so compression then
+// skips that pass and its read of the fields.
+template <int F>
+__global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float* __restrict__ aos,
+                                                                    float* __restrict__ soa, uint64_t n,
+                                                                    uint64_t ld, bool vec, RangeArgs ra) {
+    __shared__ float tile[(kAosTile + 1) * F];
+    __shared__ uint32_t s_lo[kMaxFields], s_hi[kMaxFields];
+    __shared__ float2 red[kAosThreads / 32];
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kMaxFields) {
+        s_lo[tid] = 0xffffffffu;
+        s_hi[tid] = 0u;
+    }
+    const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
+    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const uint64_t first = tl * kAosTile;
+        const int cnt = (int)min((uint64_t)kAosTile, n - first);
+        const int words = cnt * F;
+        const float* src = aos + first * (uint64_t)F;
+        if (vec && cnt == kAosTile) {
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+            for (int k4 = tid; k4 < kAosTile * F / 4; k4 += kAosThreads) {
+                const float4 v = __ldcs(s4 + k4);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = 4 * k4 + c, i = k / F, f = k - i * F;
+                    tile[f * (kAosTile + 1) + i] = e[c];
+                }
+            }
+        } else {
+            for (int k = tid; k < words; k += kAosThreads) {
+                const int i = k / F, f = k - i * F;
+                tile[f * (kAosTile + 1) + i] = __ldcs(src + k);
+            }
+        }
+        __syncthreads();
+        if (warp < F) {  // the block's extremes of field `warp`
+            const float* row = tile + warp * (kAosTile + 1);
+            float lo = INFINITY, hi = -INFINITY, probe = 0.0f;  // probe: NaN if a value is NaN or infinite
+            for (int i = lane; i < cnt; i += 32) {
+                const float v = row[i];
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+                probe = __fmaf_rn(v, 0.0f, probe);
+            }
+            lo = warp_min_f32(lo);
+            hi = warp_max_f32(hi);
+            const bool nonfinite = __any_sync(0xffffffffu, probe != probe);
+            if (lane == 0) {
+                ra.bext[tl * (uint64_t)F + warp] =
+                    nonfinite ? make_uint2(0u, 0u) : make_uint2(aos_order_key(lo), aos_order_key(hi));
+                if (lo <= hi) {  // some value is not NaN
+                    atomicMin(&s_lo[warp], aos_order_key(lo));
+                    atomicMax(&s_hi[warp], aos_order_key(hi));
+                }
+            }
+        }
+        if (vec && cnt == kAosTile) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const float* row = tile + f * (kAosTile + 1);
+                const int i = 4 * tid;
+                __stcs(reinterpret_cast<float4*>(soa + (uint64_t)f * ld + first + i),
+                       make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]));
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f)
+                for (int i = tid; i < cnt; i += kAosThreads)
+                    soa[(uint64_t)f * ld + first + i] = tile[f * (kAosTile + 1) + i];
+        }
+        __syncthreads();
+    }
+    if (tid < F) {
+        const uint32_t kl = s_lo[tid], kh = s_hi[tid];
+        const bool any = kl != 0xffffffffu || kh != 0u;
+        ra.partials[(size_t)blockIdx.x * F + tid] =
+            any ? make_float2(aos_from_order_key(kl), aos_from_order_key(kh)) : make_float2(INFINITY, -INFINITY);
+    }
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(ra.done_counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int f = 0; f < F; ++f) {  // the last CTA folds every CTA's partial extremes of field f
+        float lo = INFINITY, hi = -INFINITY;
+        for (unsigned c = tid; c < gridDim.x; c += kAosThreads) {
+            const float2 pp = __ldcg(ra.partials + (size_t)c * F + f);
+            lo = fminf(lo, pp.x);
+            hi = fmaxf(hi, pp.y);
+        }
+        lo = warp_min_f32(lo);
+        hi = warp_max_f32(hi);
+        if (lane == 0) red[warp] = make_float2(lo, hi);
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kAosThreads / 32; ++w) {
+                lo = fminf(lo, red[w].x);
+                hi = fmaxf(hi, red[w].y);
+            }
+            ra.d_params[f] = range_params(lo, hi, ra.rel[f]);
+        }
+        __syncthreads();
+    }
+}
+
+template <int F>
+cudaError_t launch_transpose_range_f(const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
+                                     const RangeArgs& ra, cudaStream_t s) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && ld % 4 == 0;
+    gpz_aos_range_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec, ra);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_range(const float* src, float* dst, uint64_t n, int F, uint64_t ld, unsigned grid,
+                                   const RangeArgs& ra, cudaStream_t s) {
+    switch (F) {
+        case 1: return launch_transpose_range_f<1>(src, dst, n, ld, grid, ra, s);
+        case 2: return launch_transpose_range_f<2>(src, dst, n, ld, grid, ra, s);
+        case 3: return launch_transpose_range_f<3>(src, dst, n, ld, grid, ra, s);
+        case 4: return launch_transpose_range_f<4>(src, dst, n, ld, grid, ra, s);
+        case 5: return launch_transpose_range_f<5>(src, dst, n, ld, grid, ra, s);
+        case 6: return launch_transpose_range_f<6>(src, dst, n, ld, grid, ra, s);
+        case 7: return launch_transpose_range_f<7>(src, dst, n, ld, grid, ra, s);
+        case 8: return launch_transpose_range_f<8>(src, dst, n, ld, grid, ra, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int F>
 cudaError_t launch_transpose_f(bool to_soa, const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
                                cudaStream_t s) {
@@ -157,7 +306,7 @@ uint64_t soa_bytes(uint64_t n, int F) { return align_up(4ull * soa_ld(n) * (uint
 
 unsigned transpose_grid(uint64_t n) {
     const uint64_t tiles = (n + kAosTile - 1) / kAosTile;
-    const uint64_t cap = 152ull * 8ull;  // eight CTAs per SM of a GB300
+    const uint64_t cap = (uint64_t)kRangeCtasMax;  // eight CTAs per SM of a GB300
     return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 
@@ -197,17 +346,36 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
     float* soa = reinterpret_cast<float*>(ws + cws);
     const uint64_t ld = soa_ld(n);
     gpz_status rc = GPZ_OK;
+    bool range_done = false;
     if (n > 0) {
         Recorder rec(s);
         rec.begin(1);
-        rc = cuda_status(launch_transpose(true, d_aos, soa, n, F, ld, transpose_grid(n), s));
+        if (p->mode == GPZ_EB_REL) {
+            // the transpose also does the range pass, into the compression workspace
+            const RangeTargets rt = compress_range_targets(n, F);
+            RangeArgs ra{};
+            ra.n = n;
+            ra.F = F;
+            for (int f = 0; f < F; ++f) ra.rel[f] = p->eb[f];
+            ra.partials = reinterpret_cast<float2*>(ws + rt.partials);
+            ra.done_counter = reinterpret_cast<uint32_t*>(ws + rt.ctrl) + 2;
+            ra.d_params = reinterpret_cast<FieldParams*>(ws + rt.params);
+            ra.bext = reinterpret_cast<uint2*>(ws + rt.bext);
+            rc = cuda_status(cudaMemsetAsync(ws + rt.ctrl, 0, 64, s));
+            const unsigned grid = transpose_grid(n);  // <= kRangeCtasMax CTAs: their partials fit
+            if (rc == GPZ_OK) rc = cuda_status(launch_transpose_range(d_aos, soa, n, F, ld, grid, ra, s));
+            range_done = rc == GPZ_OK;
+        } else {
+            rc = cuda_status(launch_transpose(true, d_aos, soa, n, F, ld, transpose_grid(n), s));
+        }
         if (rc == GPZ_OK) rec.mark("aos");
     }
     if (rc == GPZ_OK) {
         const float* fields[kMaxFields];
         for (int f = 0; f < F; ++f) fields[f] = soa + (uint64_t)f * ld;
         // the compression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
-        rc = gpz_compress(fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream);
+        rc = compress_impl(fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream,
+                           range_done);
     }
     if (own) {  // as gpz_compress without a workspace: synchronise and return the device-side status
         if (rc == GPZ_OK) {

@@ -171,9 +171,28 @@ gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_f
     return GPZ_OK;
 }
 
-gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
-                        uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
-                        void* d_ws, uint64_t ws_size, void* stream) {
+}  // extern "C"
+
+namespace gpz {
+namespace host {
+
+RangeTargets compress_range_targets(uint64_t n, int F) {
+    const WsLayout L = layout_of(n, F);
+    RangeTargets r;
+    r.ctrl = L.ctrl;
+    r.params = L.params;
+    r.partials = L.partials;
+    r.bext = L.bext;
+    return r;
+}
+
+// gpz_compress; with range_done the range pass's outputs (the block
+// extremes, the CTAs' partial extremes folded into the constants) are
+// already in the workspace, written on this stream by a kernel that read the
+// fields anyway, and are neither cleared nor recomputed.
+gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                         uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                         void* d_ws, uint64_t ws_size, void* stream, bool range_done) {
     if (!p || !d_out || !aligned(d_out, 4)) return GPZ_ERR_INVALID_ARG;
     const int F = p->n_fields;
     if (F < 1 || F > kMaxFields || p->seg_bits < 0 || p->seg_bits > kMaxSegBits ||
@@ -209,8 +228,14 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
 
     gpz_status rc = GPZ_OK;
     Recorder rec(s);
+    range_done = range_done && p->mode == GPZ_EB_REL && d_ws != nullptr && !own_ws;
     do {
-        if ((rc = cuda_status(cudaMemsetAsync(ws, 0, L.zero_bytes, s))) != GPZ_OK) break;
+        if (range_done) {  // keep the constants: clear the control words and the look-back states only
+            if ((rc = cuda_status(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, s))) != GPZ_OK) break;
+            if ((rc = cuda_status(cudaMemsetAsync(ws + L.states, 0, L.zero_bytes - L.states, s))) != GPZ_OK) break;
+        } else if ((rc = cuda_status(cudaMemsetAsync(ws, 0, L.zero_bytes, s))) != GPZ_OK) {
+            break;
+        }
         rec.begin();
         FieldParams hp[kMaxFields] = {};
         const bool rel = p->mode == GPZ_EB_REL;
@@ -234,8 +259,10 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
             ra.bext = reinterpret_cast<uint2*>(ws + L.bext);
             uint64_t want = (nb * F + kRangeThreads / 32 - 1) / (kRangeThreads / 32);  // a warp per (block, field)
             const int grid = (int)(want < 1 ? 1 : (want > (uint64_t)kRangeGridMax ? kRangeGridMax : want));
-            if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
-            rec.mark("range");
+            if (!range_done) {
+                if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
+                rec.mark("range");
+            }
             if (nb > 0) {
                 if ((rc = cuda_status(launch_block_info(ra.bext, d_params, (uint32_t)nb, F,
                                                         reinterpret_cast<unsigned long long*>(ws + L.binfo), s))) !=
@@ -326,6 +353,18 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
         if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
     }
     return rc;
+}
+
+}  // namespace host
+}  // namespace gpz
+
+extern "C" {
+
+gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                        uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                        void* d_ws, uint64_t ws_size, void* stream) {
+    return compress_impl(d_fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, d_ws, ws_size, stream,
+                         false);
 }
 
 gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fields, int F, uint64_t n,

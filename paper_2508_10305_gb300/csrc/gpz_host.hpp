@@ -93,6 +93,20 @@ inline gpz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GPZ_OK 
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Where gpz_compress's workspace holds the range pass's outputs (byte
+// offsets): control words (word 2 counts the finished range CTAs), the
+// per-field constants, the CTAs' partial extremes and the block extremes.
+struct RangeTargets {
+    uint64_t ctrl, params, partials, bext;
+};
+RangeTargets compress_range_targets(uint64_t n, int F);
+constexpr int kRangeCtasMax = 152 * 8;  // partials held for this many CTAs
+
+// gpz_compress, optionally with the range pass already done (gpz_api.cu).
+gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
+                         uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
+                         void* d_ws, uint64_t ws_size, void* stream, bool range_done);
+
 // The 64-bit form (gpz_wide.cu): its workspace, and compression with
 // absolute bounds eb[f] (the header records `mode`).
 uint64_t wide_workspace_size(uint64_t n, int F);

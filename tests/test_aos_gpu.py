@@ -26,6 +26,8 @@ def gpz():
     (6, 100_000, 1, "clustered", 0),
     (8, 5000, 0, "mixed", 3),
     (2, 1023, 0, "uniform", 2),
+    (8, 3_000_000, 1, "mixed", 0),   # relative bound: more tiles than CTAs in the fused range pass
+    (5, 70_001, 1, "uniform", 0),    # ragged last tile, aligned base
 ])
 def test_aos_matches_oracle(gpz, oracle, F, n, mode, kind, offset):
     rng = np.random.default_rng(F * 1000 + n % 997)
@@ -40,6 +42,34 @@ def test_aos_matches_oracle(gpz, oracle, F, n, mode, kind, offset):
     out = gpz.decompress_aos(stream, F, n)
     ro = oracle.decompress(rs, F, n)
     assert np.array_equal(out.cpu().numpy().view(np.uint32), np.ascontiguousarray(ro.T).view(np.uint32))
+
+
+@pytest.mark.parametrize("own_ws", [False, True])
+def test_aos_relative_bound_with_non_finite_values(gpz, oracle, own_ws):
+    """The transpose that also does the range pass: blocks with NaN or an
+    infinity go raw, the range of a field is taken over its non-NaN values
+    (an infinity makes it infinite, so eb = rel), and a field holding only
+    NaN keeps eb = rel -- the stream is the oracle's either way."""
+    import ctypes as C
+    rng = np.random.default_rng(17)
+    F, n = 4, 9000
+    x = gen("clustered", F, n, rng)
+    x[0, 5] = np.nan
+    x[1, 4000] = np.inf
+    x[2, :] = np.nan
+    x[3, 8999] = -np.inf
+    xa = torch.from_numpy(np.ascontiguousarray(x.T).reshape(-1)).cuda()
+    params = gpz.make_params(F, 1e-3, gpz.EB_REL)
+    cap = gpz.gpz_bound_size(n, F)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    h = C.c_uint64(0)
+    need = gpz.gpz_compress_aos_workspace_size(n, F)
+    ws = None if own_ws else torch.empty(need, dtype=torch.uint8, device="cuda")
+    st = gpz.lib.gpz_compress_aos(xa.data_ptr(), n, C.byref(params), out.data_ptr(), cap, None, C.byref(h), None,
+                                  ws.data_ptr() if ws is not None else None, need if ws is not None else 0, None)
+    assert st == gpz.OK
+    rs, _ = oracle.compress(x, 1e-3, 1, 3)
+    assert h.value == rs.size and np.array_equal(out[:h.value].cpu().numpy(), rs)
 
 
 def test_aos_workspace_checks(gpz):
