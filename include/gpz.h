@@ -204,10 +204,11 @@ gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, 
  * Other arguments, errors and ordering as gpz_compress; gpz_sync_status(d_ws)
  * reads the device-side status.
  * gpz_decompress_f64 reads the stream's version word (one synchronisation).
- * A version-1 stream is decompressed into an fp32 copy in the workspace (at
- * least gpz_decompress_f64_workspace_size(n, F) bytes, required) and widened
- * to the n_fields fp64 arrays (exact); a version-2 stream goes to
- * gpz_decompress_wide.  Otherwise as gpz_decompress. */
+ * A version-1 stream is decoded straight into the n_fields fp64 arrays (each
+ * value its fp32 reconstruction, widened exactly); a version-2 stream goes to
+ * gpz_decompress_wide.  The workspace (gpz_decompress_f64_workspace_size(n, F)
+ * bytes, required, 256-byte aligned) holds the status word.  Otherwise as
+ * gpz_decompress. */
 uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields);
 uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields);
 gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,

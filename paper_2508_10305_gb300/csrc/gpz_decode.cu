@@ -47,4 +47,29 @@ cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// The same decoder storing fp64 (gpz_decompress_f64 on a version-1 stream):
+// a.out[f] holds the address of field f's double array, and every value is
+// the fp32 reconstruction widened exactly.
+template <int F>
+__global__ void __launch_bounds__(kDecThreads, 8) gpz_decompress64_kernel(DecArgs a) {
+    __shared__ DecShared S;
+    decode_block<F, DecGridBlock, true>(a, S, DecGridBlock{});
+}
+
+cudaError_t launch_decompress64(const DecArgs& a, cudaStream_t s) {
+    if (a.nblocks == 0) return cudaSuccess;
+    switch (a.F) {
+        case 1: gpz_decompress64_kernel<1><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 2: gpz_decompress64_kernel<2><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 3: gpz_decompress64_kernel<3><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 4: gpz_decompress64_kernel<4><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 5: gpz_decompress64_kernel<5><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 6: gpz_decompress64_kernel<6><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 7: gpz_decompress64_kernel<7><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 8: gpz_decompress64_kernel<8><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace gpz

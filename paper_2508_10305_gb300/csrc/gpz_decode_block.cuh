@@ -43,8 +43,33 @@ __device__ __forceinline__ float small_u2f(uint32_t q) {
     return __fsub_rn(__uint_as_float(q + 0x4B000000u), 8388608.0f);
 }
 
-// Rebuild four consecutive values x = fma((float)q, step, min) and store them.
-__device__ __forceinline__ void store4(float* dst, const uint32_t* qv, uint32_t bits, float s, float mn, int left) {
+// Rebuild four consecutive values x = fma((float)q, step, min) and store them
+// at out[first .. first + 3]: fp32, or widened to fp64 (exact) when OUT64 --
+// then `out` holds a double array's address.
+template <bool OUT64>
+__device__ __forceinline__ void store4(float* out, uint64_t first, const uint32_t* qv, uint32_t bits, float s, float mn,
+                                       int left) {
+    if (OUT64) {
+        float v[4];
+        if (bits <= 23u) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = __fmaf_rn(small_u2f(qv[e]), s, mn);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = __fmaf_rn(__uint2float_rn(qv[e]), s, mn);
+        }
+        double* dst = reinterpret_cast<double*>(out) + first;
+        if (left >= 4 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+            reinterpret_cast<double2*>(dst)[0] = make_double2((double)v[0], (double)v[1]);
+            reinterpret_cast<double2*>(dst)[1] = make_double2((double)v[2], (double)v[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (e < left) dst[e] = (double)v[e];
+        }
+        return;
+    }
+    float* dst = out + first;
     float v[4];
     if (bits <= 23u) {  // uniform: codes below 2^23 convert with one add
 #pragma unroll
@@ -65,7 +90,7 @@ __device__ __forceinline__ void store4(float* dst, const uint32_t* qv, uint32_t 
 // Records wider than 128 bits (rare): every code is read field by field from
 // the stream itself; the block header is re-read here so that the common path
 // passes nothing through memory.
-template <int F>
+template <int F, bool OUT64 = false>
 __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* blk, uint32_t rwords_off,
                                          uint32_t rwords, uint32_t W, uint32_t G, int j0, int n_b, uint64_t first,
                                          uint32_t key0, uint32_t key1, uint32_t key2, uint32_t key3) {
@@ -108,7 +133,7 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
             }
             qv[e] = f < P ? (code | (((key[e] >> kacc[f]) & gm) << wfv[f])) : code;
         }
-        store4(a.out[f] + first + j0, qv, bf, sf, mnf, n_b - j0);
+        store4<OUT64>(a.out[f], first + j0, qv, bf, sf, mnf, n_b - j0);
     }
 }
 
@@ -134,7 +159,7 @@ struct DecShared : DecCore {
 // four); after each field the record is shifted right by the field's width
 // and the key right by the axis' segId bits.  q = segId * 2^o + segOffset for
 // a position axis, the whole code otherwise.
-template <int F, bool WIDE>
+template <int F, bool WIDE, bool OUT64 = false>
 __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4][4], uint32_t (&key)[4],
                                               const DecCore& L, uint64_t first, int left) {
     constexpr int P = F < 3 ? F : 3;
@@ -163,7 +188,7 @@ __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4
             }
         }
         const float2 ms = L.ms[f];
-        store4(a.out[f] + first, qv, lay.w, ms.y, ms.x, left);
+        store4<OUT64>(a.out[f], first, qv, lay.w, ms.y, ms.x, left);
     }
 }
 
@@ -258,7 +283,7 @@ __device__ __forceinline__ void decode_checks(const DecArgs& a, DecCore& S, uint
 // Decode a block whose constants warp 0 has published in S (after a
 // barrier): stage holds the block's words after its header, blk the block in
 // the stream (read directly for raw blocks and records wider than 128 bits).
-template <int F>
+template <int F, bool OUT64 = false>
 __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const uint32_t* stage,
                                             const uint32_t* blk, uint32_t b, int n_b) {
     uint16_t* uniq = S.uniq;
@@ -276,7 +301,13 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
 #pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = t; i < n_b; i += kDecThreads)
-                a.out[f][(uint64_t)b * kBlock + i] = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
+            {
+                const float v = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
+                if (OUT64)
+                    reinterpret_cast<double*>(a.out[f])[(uint64_t)b * kBlock + i] = (double)v;
+                else
+                    a.out[f][(uint64_t)b * kBlock + i] = v;
+            }
         return;
     }
 
@@ -369,7 +400,7 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
         key[e] = uniq[run];
     }
     if (!fast) {
-        decode_wide<F>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)b * kBlock, key[0],
+        decode_wide<F, OUT64>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)b * kBlock, key[0],
                        key[1], key[2], key[3]);
         return;
     }
@@ -394,13 +425,13 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
     }
     const uint64_t first = (uint64_t)b * kBlock + j0;
     if (wide)
-        decode_fields<F, true>(a, rr, key, S, first, n_b - j0);
+        decode_fields<F, true, OUT64>(a, rr, key, S, first, n_b - j0);
     else
-        decode_fields<F, false>(a, rr, key, S, first, n_b - j0);
+        decode_fields<F, false, OUT64>(a, rr, key, S, first, n_b - j0);
 }
 
 
-template <int F, class Idx>
+template <int F, class Idx, bool OUT64 = false>
 __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx idx) {
     uint32_t* stage = S.stage;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -444,7 +475,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
 
     if (w == 0) decode_checks<F>(a, S, hv, bw, step, inside, b, off, end, payload_words, n_b);
     __syncthreads();
-    decode_tail<F>(a, S, stage, blk, b, n_b);
+    decode_tail<F, OUT64>(a, S, stage, blk, b, n_b);
 }
 
 }  // namespace gpz

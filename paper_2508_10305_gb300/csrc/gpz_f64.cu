@@ -10,8 +10,8 @@
 // relative bound is taken over the fp64 range) and calls gpz_compress with
 // absolute bounds on the copy -- or, when some eb' is not positive, calls the
 // 64-bit form with the bounds eb.  Decompression of a version-1 stream runs
-// gpz_decompress into an fp32 copy and widens it to fp64 (exact); a version-2
-// stream goes to gpz_decompress_wide.
+// the block decoder storing fp64 (each value widened exactly from its fp32
+// reconstruction); a version-2 stream goes to gpz_decompress_wide.
 #include <cmath>
 #include <cstring>
 
@@ -119,35 +119,6 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
     }
 }
 
-// (double)x: exact; normal values re-biased with integer operations
-__device__ __forceinline__ double widen(float x) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 255u) return (double)x;  // zero, subnormal, infinite or NaN
-    const unsigned long long u = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
-                                 ((unsigned long long)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)u);
-}
-
-// out64[f][i] = (double)in32[f][i]
-__global__ void __launch_bounds__(kF64Threads) gpz_f64_widen_kernel(F64Args a) {
-    const uint64_t stride = (uint64_t)gridDim.x * kF64Threads;
-    for (int f = 0; f < a.F; ++f) {
-        const float* src = a.in32[f];
-        double* dst = a.out64[f];
-        uint64_t i = (uint64_t)blockIdx.x * kF64Threads + threadIdx.x;
-        for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
-            const float v0 = __ldcs(src + i), v1 = __ldcs(src + i + stride), v2 = __ldcs(src + i + 2 * stride),
-                        v3 = __ldcs(src + i + 3 * stride);
-            dst[i] = widen(v0);
-            dst[i + stride] = widen(v1);
-            dst[i + 2 * stride] = widen(v2);
-            dst[i + 3 * stride] = widen(v3);
-        }
-        for (; i < a.n; i += stride) dst[i] = widen(__ldcs(src + i));
-    }
-}
-
 }  // namespace gpz
 
 namespace {
@@ -183,8 +154,9 @@ uint64_t gpz_compress_f64_workspace_size(uint64_t n, int n_fields) {
 }
 
 uint64_t gpz_decompress_f64_workspace_size(uint64_t n, int n_fields) {
+    (void)n;
     if (n_fields < 1 || n_fields > kMaxFields) return 0;
-    return align_up(gpz_decompress_workspace_size(), kF64Align) + f32_bytes(n, n_fields);
+    return align_up(gpz_decompress_workspace_size(), kF64Align);  // the status word
 }
 
 gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
@@ -300,27 +272,27 @@ gpz_status gpz_decompress_f64(const void* d_in, uint64_t in_size, double* const*
             return GPZ_ERR_CUDA;
         if (head[1] == 2u) return gpz_decompress_wide(d_in, in_size, d_fields, F, n, d_ws, ws_size, stream);
     }
-    uint8_t* ws = static_cast<uint8_t*>(d_ws);
-    const uint64_t dws = align_up(gpz_decompress_workspace_size(), kF64Align);
-    float* y = reinterpret_cast<float*>(ws + dws);
-    const uint64_t ld = f32_ld(n);
-    float* fields[kMaxFields];
-    for (int f = 0; f < F; ++f) fields[f] = y + (uint64_t)f * ld;
-    // the decompression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
-    gpz_status rc = gpz_decompress(d_in, in_size, fields, F, n, ws, dws, stream);
-    if (rc != GPZ_OK || n == 0) return rc;
-    F64Args fa{};
-    fa.F = F;
-    fa.n = n;
-    for (int f = 0; f < F; ++f) {
-        fa.in32[f] = y + (uint64_t)f * ld;
-        fa.out64[f] = d_fields[f];
-    }
+    // version 1: the block decoder stores fp64 directly (each value the fp32
+    // reconstruction, widened exactly); the workspace holds the status word
+    if (!d_in || !aligned(d_in, 4)) return GPZ_ERR_INVALID_ARG;
+    if (in_size % 4 != 0 || in_size < 4ull * kHeaderWords) return GPZ_ERR_CORRUPT;
+    const uint64_t nb = (n + kBlock - 1) / kBlock;
+    if (nb + (uint64_t)F * n >= (1ull << 32)) return GPZ_ERR_UNSUPPORTED;
+    uint32_t* status = static_cast<uint32_t*>(d_ws);
+    if (cudaMemsetAsync(status, 0, 4, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    if (nb == 0) return GPZ_OK;
+    DecArgs da{};
+    da.stream = static_cast<const uint32_t*>(d_in);
+    da.total_words = in_size / 4;
+    for (int f = 0; f < F; ++f) da.out[f] = reinterpret_cast<float*>(d_fields[f]);  // double arrays
+    da.n = n;
+    da.F = F;
+    da.nblocks = (uint32_t)nb;
+    da.status = status;
     Recorder rec(s);
     rec.begin(1);
-    gpz_f64_widen_kernel<<<f64_grid(n), kF64Threads, 0, s>>>(fa);
-    if (cudaGetLastError() != cudaSuccess) return GPZ_ERR_CUDA;
-    rec.mark("f64");
+    if (launch_decompress64(da, s) != cudaSuccess) return GPZ_ERR_CUDA;
+    rec.mark("decompress");
     return GPZ_OK;
 }
 

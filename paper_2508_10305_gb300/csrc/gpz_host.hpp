@@ -107,6 +107,14 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
                          uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
                          void* d_ws, uint64_t ws_size, void* stream, bool range_done);
 
+}  // namespace host
+
+// The block decoder storing fp64 values (gpz_decode.cu): a.out[f] holds the
+// address of a double array.
+cudaError_t launch_decompress64(const DecArgs& a, cudaStream_t s);
+
+namespace host {
+
 // The 64-bit form (gpz_wide.cu): its workspace, and compression with
 // absolute bounds eb[f] (the header records `mode`).
 uint64_t wide_workspace_size(uint64_t n, int F);
