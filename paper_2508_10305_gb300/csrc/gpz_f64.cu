@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
         const double* x = a.in[f];
         float* y = a.out32[f];
         unsigned long long kmin = ~0ull, kmax = 0ull, dmax = 0ull;
-        auto visit = [&](double v, uint64_t i) {
+        auto round1 = [&](double v) -> float {
             const unsigned long long u = (unsigned long long)__double_as_longlong(v);
             const int e = (int)((u >> 52) & 0x7ffu);
             const int e32 = e - 1023 + 127;
@@ -56,7 +56,6 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
                 const uint32_t m24 = (uint32_t)(m >> 29), rem = (uint32_t)(m & 0x1fffffffu);
                 const bool up = rem > 0x10000000u || (rem == 0x10000000u && (m24 & 1u));
                 const uint32_t rb = (((uint32_t)(u >> 63)) << 31) | (((uint32_t)e32 << 23) + m24 + (up ? 1u : 0u));
-                y[i] = __uint_as_float(rb);  // a carry into exponent 255 is the correct +-Inf
                 const uint32_t res = up ? 0x20000000u - rem : rem;  // < 2^29
                 unsigned long long d = 0ull;
                 if (res) {
@@ -69,10 +68,9 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
                 const unsigned long long k = order_key64(v);
                 kmin = min(kmin, k);
                 kmax = max(kmax, k);
-                return;
+                return __uint_as_float(rb);  // a carry into exponent 255 is the correct +-Inf
             }
             const float r = __double2float_rn(v);  // zero, fp32-subnormal, beyond fp32, infinite or NaN
-            y[i] = r;
             if (v == v) {  // not NaN
                 const unsigned long long k = order_key64(v);
                 kmin = min(kmin, k);
@@ -82,17 +80,40 @@ __global__ void __launch_bounds__(kF64Threads) gpz_f64_prepass_kernel(F64Args a)
                     dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
                 }
             }
+            return r;
         };
-        uint64_t i = (uint64_t)blockIdx.x * kF64Threads + tid;
-        for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
-            const double v0 = __ldcs(x + i), v1 = __ldcs(x + i + stride), v2 = __ldcs(x + i + 2 * stride),
-                         v3 = __ldcs(x + i + 3 * stride);
-            visit(v0, i);
-            visit(v1, i + stride);
-            visit(v2, i + 2 * stride);
-            visit(v3, i + 3 * stride);
+        auto visit = [&](double v, uint64_t i) { y[i] = round1(v); };
+        if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+            // pairs of values: 16-byte loads (four in flight per thread), 8-byte stores
+            const double2* x2 = reinterpret_cast<const double2*>(x);
+            float2* y2 = reinterpret_cast<float2*>(y);  // y is 16-byte aligned
+            const uint64_t npairs = a.n / 2;
+            uint64_t q = (uint64_t)blockIdx.x * kF64Threads + tid;
+            for (; q + 3 * stride < npairs; q += 4 * stride) {
+                const double2 v0 = __ldcs(x2 + q), v1 = __ldcs(x2 + q + stride), v2 = __ldcs(x2 + q + 2 * stride),
+                              v3 = __ldcs(x2 + q + 3 * stride);
+                y2[q] = make_float2(round1(v0.x), round1(v0.y));
+                y2[q + stride] = make_float2(round1(v1.x), round1(v1.y));
+                y2[q + 2 * stride] = make_float2(round1(v2.x), round1(v2.y));
+                y2[q + 3 * stride] = make_float2(round1(v3.x), round1(v3.y));
+            }
+            for (; q < npairs; q += stride) {
+                const double2 v = __ldcs(x2 + q);
+                y2[q] = make_float2(round1(v.x), round1(v.y));
+            }
+            if ((a.n & 1ull) && blockIdx.x == 0 && tid == 0) visit(__ldcs(x + a.n - 1), a.n - 1);  // odd last value
+        } else {
+            uint64_t i = (uint64_t)blockIdx.x * kF64Threads + tid;
+            for (; i + 3 * stride < a.n; i += 4 * stride) {  // four loads in flight per thread
+                const double v0 = __ldcs(x + i), v1 = __ldcs(x + i + stride), v2 = __ldcs(x + i + 2 * stride),
+                             v3 = __ldcs(x + i + 3 * stride);
+                visit(v0, i);
+                visit(v1, i + stride);
+                visit(v2, i + 2 * stride);
+                visit(v3, i + 3 * stride);
+            }
+            for (; i < a.n; i += stride) visit(__ldcs(x + i), i);
         }
-        for (; i < a.n; i += stride) visit(__ldcs(x + i), i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));

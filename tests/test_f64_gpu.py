@@ -33,6 +33,7 @@ def make(F, n, seed, special):
     (1, 1, 0, 1e-2, False),
     (6, 40_000, 1, 1e-5, False),
     (8, 3000, 0, 1e-1, True),  # field 5 reaches 7e5: half an fp32 ulp there is 0.016
+    (2, 7777, 1, 1e-4, True),  # odd length: field 0 16-byte aligned (pairs and a last single value), field 1 not
 ])
 def test_f64_matches_oracle(gpz, oracle, F, n, mode, eb, special):
     x = make(F, n, F * 7 + n % 13, special)
