@@ -261,3 +261,36 @@ def test_wide_argument_errors_need_no_device(gpz):
     assert L.gpz_decompress_wide(out, 1024, outs, 3, n, ws, 8, None) == gpz.ERR_CAPACITY
     assert L.gpz_decompress_wide(out, 1024, (C.c_void_p * 3)(4096, 8196, 12288), 3, n, ws, 256, None) == gpz.ERR_INVALID_ARG
     assert L.gpz_decompress_wide(out, 60, outs, 3, n, ws, 256, None) == gpz.ERR_CORRUPT       # shorter than the header
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """The product path has no fallback: a copy of the binding with no
+    libgpz.so beside it must fail at import, naming the missing library."""
+    shutil.copy(os.path.join(ROOT, "paper_2508_10305_gb300", "gpz.py"), tmp_path / "gpz.py")
+    code = ("import importlib.util, sys\n"
+            "spec = importlib.util.spec_from_file_location('gpz_copy', sys.argv[1])\n"
+            "m = importlib.util.module_from_spec(spec)\n"
+            "try:\n"
+            "    spec.loader.exec_module(m)\n"
+            "except ImportError as e:\n"
+            "    print('refused:', e); sys.exit(3)\n"
+            "sys.exit(0)\n")
+    r = subprocess.run(["python", "-c", code, str(tmp_path / "gpz.py")], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 3, r.stdout + r.stderr
+    assert "libgpz.so is not built" in r.stdout
+
+
+def test_package_never_reaches_the_oracle():
+    """Only the tests, the smoke check and the benchmark's CPU leg may use the
+    oracle; no source file of the package (Python or CUDA) imports it, links
+    its library or calls one of its functions."""
+    pkg = os.path.join(ROOT, "paper_2508_10305_gb300")
+    offenders = []
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".hpp", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                if re.search(r"(from|import)\s+oracle\b|gpz_oracle|gpzo_|oracle[/\\]", text):
+                    offenders.append(f)
+    assert not offenders, offenders
