@@ -65,3 +65,28 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         n, steps, warmup, gpus = 4096, 1, 0, 2
     bench.run_reference(A, 1, 2)  # rank 1: no work, no output
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys):
+    """Rank 0 of the reference arm times the oracle on a sample of the
+    snapshot and prints one JSON line with the same metric, unit and config
+    as the GPU arm, marked as the reference, with its CPU baseline and an
+    e2e object of zero transfer bytes."""
+    import json
+    import bench
+    from oracle import build as oracle_build
+    oracle_build.build()
+
+    class A:
+        n, steps, warmup, gpus = 1 << 16, 1, 0, 1
+    bench.run_reference(A, 0, 1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GB/s"
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["n_gpus"] == 1
+    assert line["config"]["workload"] == bench.WORKLOAD and line["config"]["n"] == 1 << 16
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "GB/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
