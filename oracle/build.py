@@ -17,7 +17,14 @@ CXXFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle/libgpz_oracle.so if it is missing or older than its sources."""
+    """Compile oracle/libgpz_oracle.so if it is missing or older than its sources.
+
+    GPZ_ORACLE_LIB names another build of the oracle to load instead; the
+    mutation test uses it to run the pins against copies with planted
+    mistakes."""
+    override = os.environ.get("GPZ_ORACLE_LIB")
+    if override:
+        return override
     deps = [SRC, os.path.join(HERE, "gpz_oracle.h"), os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         if os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
