@@ -65,14 +65,34 @@ typedef enum {
  *   seg_bits: G in 0..3, the segment-id bits per axis (at most 2^G segments
  *             per axis and block; the segment size m scales with the block's
  *             extent, Section 4.1).  3 is the default.
+ *   flags:    0, or GPZ_FLAG_* bits selecting an implementation variant of
+ *             this one call; the stream is the same bytes either way.  Zero-
+ *             initialised parameters take the defaults.
  *   eb[f]:    error bound of field f, > 0 and finite.  Every decompressed
  *             value is within eb (absolute) of its input value. */
 typedef struct {
     int mode;
     int n_fields;
     int seg_bits;
+    unsigned int flags;
     double eb[GPZ_MAX_FIELDS];
 } gpz_params;
+
+/* Compaction form (Section 4.4) of one gpz_compress call; the stream is the
+ * same bytes in either form.
+ *   default (no flag): Section 4.4's three steps -- every block is encoded
+ *     into a temporary slot, a scan computes the offsets, a copy kernel moves
+ *     every block into the stream.
+ *   GPZ_FLAG_FUSED_COMPACTION: every block publishes its size and looks back
+ *     over its predecessors' sizes, waiting for them (a decoupled look-back
+ *     over blocks, the in-kernel form of Table 1); a block whose offset is
+ *     known is written straight into the stream, the others (raw blocks, and
+ *     the blocks behind one that needed the general path) go through their
+ *     temporary slots and the copy kernel.  After such a call, word 8 of the
+ *     compression workspace (bytes 32..35) holds the number of blocks the
+ *     copy kernel moved (a diagnostic).
+ * Other bits are refused (GPZ_ERR_INVALID_ARG). */
+#define GPZ_FLAG_FUSED_COMPACTION 1u
 
 /* Worst-case size in bytes of the stream for n particles of n_fields fields
  * (every block stored raw).  Returns 0 for n_fields outside 1..8. */
@@ -112,27 +132,47 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
 /* Compress without allocating anything (the paper has no counterpart: this is
  * a convenience of this library).  Same arguments, stream and behaviour as
  * gpz_compress with d_ws = NULL, except that no device memory is allocated:
- * the scratch space comes from a fixed 32 MiB array built into the library
- * (reserved on every GPU that loads the library, until the process exits).
+ * the scratch space comes from a fixed 32 MiB array built into the library.
  * It is meant for callers that cannot allocate device memory when they
  * compress -- for example an in-situ hook inside a simulation whose device
  * memory is fully reserved by the simulation's own pool allocator, or a
  * latency-critical loop in which an allocation may stall the device.
+ *   - When the array is taken: with CUDA's lazy module loading (the default
+ *     since CUDA 12.2, and what PyTorch sets) the 32 MiB are taken on a
+ *     device when the library first looks the array up there, that is at the
+ *     first gpz_noalloc_prepare or gpz_compress_noalloc call with that device
+ *     current; with eager loading (CUDA_MODULE_LOADING=EAGER) when the
+ *     library's module is loaded.  Either way it is held until the process
+ *     exits.  A caller whose own pool later reserves all remaining device
+ *     memory must call gpz_noalloc_prepare on each device first, and should
+ *     also do so before any stream capture.
  *   - Limit: gpz_compress_workspace_size(n, n_fields) must not exceed 32 MiB
  *     (about 8 million values n * n_fields); larger inputs return
  *     GPZ_ERR_CAPACITY and enqueue nothing.
- *   - The first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture on that device.
  *   - All calls on a device share the one array, and it keeps the last
  *     call's contents; every call clears what must start at zero.  Calls whose
  *     work overlaps on the GPU (different streams, or host threads issuing
  *     concurrently) race on the array: serialise them.
- *   - Device-side errors are returned only when h_out_size is given (the call
- *     then synchronises `stream`). */
+ *   - Device-side errors are recorded in the array's status word.  With
+ *     h_out_size the call synchronises `stream` and returns that status;
+ *     without, gpz_noalloc_sync_status reads it.
+ *   - The array's address is looked up on every call, so the entry point
+ *     stays valid after cudaDeviceReset (the array is then taken again). */
 gpz_status gpz_compress_noalloc(const float* const* d_fields, uint64_t n, const gpz_params* p,
                                 void* d_out, uint64_t out_capacity, uint64_t* d_out_size,
                                 uint64_t* h_out_size, uint32_t* d_perm, void* stream);
+
+/* Take the scratch array of gpz_compress_noalloc on the current device now
+ * (see there), so that a later pool reservation or stream capture cannot
+ * stand in its way.  Returns GPZ_OK, or GPZ_ERR_CUDA when the array cannot
+ * be taken (for example the device has no 32 MiB left). */
+gpz_status gpz_noalloc_prepare(void);
+
+/* Synchronise `stream`, return the status that the kernels of earlier
+ * gpz_compress_noalloc calls on the current device recorded in the scratch
+ * array (GPZ_OK if none), and clear it.  The next gpz_compress_noalloc call
+ * also clears it when it starts. */
+gpz_status gpz_noalloc_sync_status(void* stream);
 
 /* Decompress (Section 3.2, last paragraph: the inverse without sorting).
  *   d_in/in_size: the stream (device, 4-byte aligned) and its size in bytes.
@@ -253,27 +293,16 @@ gpz_status gpz_decompress_wide(const void* d_in, uint64_t in_size, double* const
 /* Static text for a status code. */
 const char* gpz_status_str(gpz_status s);
 
-/* Compaction form of later gpz_compress calls (per process; default 0).
- *   0: Section 4.4's three steps: every block is encoded into a temporary
- *      slot, a scan computes the offsets, a copy kernel moves the blocks.
- *   1: fused compaction: every block publishes its size and looks back over
- *      its predecessors' sizes (a decoupled look-back over blocks); a block
- *      whose offset is known is written straight into the stream, and only
- *      the others go through the temporary slots and the copy.  A block left
- *      to the general path breaks the chain for the blocks behind it.
- * The stream is the same byte for byte.  Word 8 of the compression workspace
- * (bytes 32..35) holds, after a fused call, the number of blocks that were not
- * placed directly (a diagnostic).  Returns the previous setting. */
-int gpz_set_fused_compaction(int enable);
-
-/* Measurement hooks.  When enabled (per process), every later call records
- * CUDA events on its stream before its first kernel and after each kernel
- * (up to 8192 events between reads).  gpz_stage_times synchronises on the
- * last recorded event, writes up to max stage names ("range", "qse", "scan",
- * "compact", "decompress") with their summed elapsed milliseconds and launch
- * counts since the previous read, returns the number of stages, and clears
- * the log.  names[] receives static strings. */
-void gpz_set_stage_timing(int enable);
+/* Measurement hooks.  gpz_set_stage_timing(stream, 1) makes every later call
+ * enqueued on that one stream (the handle passed as the calls' `stream`)
+ * record CUDA events before its first kernel and after each kernel (up to
+ * 8192 events between reads); calls on other streams are not affected.
+ * gpz_set_stage_timing(stream, 0) stops it.  gpz_stage_times synchronises on
+ * the last recorded event, writes up to max stage names ("range", "qse",
+ * "scan", "compact", "decompress", ...) with their summed elapsed
+ * milliseconds and launch counts since the previous read, returns the number
+ * of stages, and clears the log.  names[] receives static strings. */
+void gpz_set_stage_timing(void* stream, int enable);
 int gpz_stage_times(const char** names, float* total_ms, int* launches, int max);
 
 /* Kernel launches enqueued by this process since the last reset. */

@@ -338,7 +338,7 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
         if (ws_size < need) return GPZ_ERR_CAPACITY;
         if (reinterpret_cast<uintptr_t>(d_ws) % kAosAlign) return GPZ_ERR_INVALID_ARG;
     } else {
-        if (cudaMallocAsync(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
+        if (dev_malloc_async(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
         own = true;
     }
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
@@ -404,7 +404,7 @@ gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, 
         if (ws_size < need) return GPZ_ERR_CAPACITY;
         if (reinterpret_cast<uintptr_t>(d_ws) % kAosAlign) return GPZ_ERR_INVALID_ARG;
     } else {
-        if (cudaMallocAsync(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
+        if (dev_malloc_async(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
         if (cudaMemsetAsync(d_ws, 0, 4, s) != cudaSuccess) {
             cudaFreeAsync(d_ws, s);
             return GPZ_ERR_CUDA;

@@ -27,9 +27,10 @@ namespace {
 constexpr uint64_t kAlign = 256;
 constexpr int kRangeGridMax = 152 * 8;  // range-pass CTAs: 8 per SM of a GB300 (full occupancy)
 constexpr uint64_t kCtrlBytes = 256;    // words: 0 status, 1 scan tile counter, 2 range counter,
-                                        // 3 general-list count, 4-5 out size, 8 blocks not placed
-                                        // directly (fused compaction)
+                                        // 3 general-list count, 4-5 out size, 8 blocks left to the
+                                        // copy kernel (fused compaction)
 constexpr uint64_t kParamBytes = 256;   // FieldParams[8]
+constexpr unsigned kKnownFlags = GPZ_FLAG_FUSED_COMPACTION;
 
 uint32_t slot_words_of(int F) { return (uint32_t)align_up(1ull + (uint64_t)F * kBlock, 4); }
 
@@ -38,8 +39,6 @@ uint64_t ntiles_of(uint64_t nblocks) { return (nblocks + 1 + kScanTile - 1) / kS
 struct WsLayout {
     uint64_t ctrl, params, states, bstates, partials, bext, binfo, sizes, list, temp, total, zero_bytes;
 };
-
-std::atomic<int> g_fused{0};  // gpz_set_fused_compaction
 
 WsLayout layout_of(uint64_t n, int F) {
     WsLayout L{};
@@ -95,8 +94,6 @@ uint64_t gpz_compress_workspace_size(uint64_t n, int F) {
 
 uint64_t gpz_decompress_workspace_size(void) { return kCtrlBytes; }
 
-int gpz_set_fused_compaction(int enable) { return g_fused.exchange(enable ? 1 : 0); }
-
 const char* gpz_status_str(gpz_status s) {
     switch (s) {
         case GPZ_OK: return "ok";
@@ -111,9 +108,10 @@ const char* gpz_status_str(gpz_status s) {
     return "unknown status";
 }
 
-void gpz_set_stage_timing(int enable) {
+void gpz_set_stage_timing(void* stream, int enable) {
     std::lock_guard<std::mutex> g(g_timer.mu);
     g_timer.enabled = enable != 0;
+    g_timer.stream = (cudaStream_t)stream;
 }
 
 int gpz_stage_times(const char** names, float* total_ms, int* launches, int max) {
@@ -200,6 +198,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         return GPZ_ERR_INVALID_ARG;
     for (int f = 0; f < F; ++f)
         if (!(p->eb[f] > 0.0) || !std::isfinite(p->eb[f])) return GPZ_ERR_INVALID_ARG;
+    if ((p->flags & ~kKnownFlags) != 0u) return GPZ_ERR_INVALID_ARG;
     if (n > 0) {
         if (!d_fields) return GPZ_ERR_INVALID_ARG;
         for (int f = 0; f < F; ++f)
@@ -216,7 +215,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         if (ws_size < L.total) return GPZ_ERR_CAPACITY;
         if (!aligned(d_ws, kAlign)) return GPZ_ERR_INVALID_ARG;
     } else {
-        if (cudaMallocAsync(&d_ws, L.total, s) != cudaSuccess) return GPZ_ERR_OOM;
+        if (dev_malloc_async(&d_ws, L.total, s) != cudaSuccess) return GPZ_ERR_OOM;
         own_ws = true;
     }
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
@@ -292,7 +291,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         qa.status = status;
         qa.general_list = reinterpret_cast<uint32_t*>(ws + L.list);
         qa.general_count = status + 3;
-        const bool fused = g_fused.load() != 0;
+        const bool fused = (p->flags & GPZ_FLAG_FUSED_COMPACTION) != 0u;
         const uint32_t table_start = (uint32_t)(kHeaderWords + 2 * F);
         if (fused) {
             const uint64_t payload_start = table_start + nb + 1;
@@ -302,7 +301,8 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
             qa.deferred_count = status + 8;
         }
         if (nb > 0) {
-            if ((rc = cuda_status(fused ? launch_qse_direct(qa, s) : launch_qse(qa, s))) != GPZ_OK) break;
+            const cudaError_t e = fused ? launch_qse_direct(qa, s) : launch_qse(qa, s);
+            if ((rc = cuda_status(e)) != GPZ_OK) break;
             rec.mark("qse");
             ++g_launches;  // launch_qse enqueues two kernels: the fast path and the general list
         }
@@ -335,6 +335,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         for (int f = 0; f < F; ++f) ca.params[f] = hp[f];
         ca.d_params = rel ? d_params : nullptr;
         ca.d_out_size = d_out_size ? reinterpret_cast<unsigned long long*>(d_out_size) : ws_out_size;
+        ca.unplaced = fused ? status + 8 : nullptr;
         ca.version = kVersion;
         if ((rc = cuda_status(launch_compact(ca, s))) != GPZ_OK) break;
         rec.mark("compact");
@@ -384,7 +385,7 @@ gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fi
         if (ws_size < gpz_decompress_workspace_size()) return GPZ_ERR_CAPACITY;
         if (!aligned(d_ws, 16)) return GPZ_ERR_INVALID_ARG;
     } else {
-        if (cudaMallocAsync(&d_ws, gpz_decompress_workspace_size(), s) != cudaSuccess) return GPZ_ERR_OOM;
+        if (dev_malloc_async(&d_ws, gpz_decompress_workspace_size(), s) != cudaSuccess) return GPZ_ERR_OOM;
         own_ws = true;
     }
     uint32_t* status = static_cast<uint32_t*>(d_ws);

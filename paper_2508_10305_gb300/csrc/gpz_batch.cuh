@@ -78,6 +78,7 @@ struct BatchScanArgs {
     unsigned long long* tile_state; // zeroed
     uint32_t* tile_counter;      // zeroed
     uint32_t* status;
+    long long wait_cycles;       // limit of a look-back wait in SM cycles; 0: kWaitCycles
 };
 
 struct BatchCompactArgs {
@@ -124,7 +125,7 @@ cudaError_t launch_batch_map(const BatchMapArgs& a, cudaStream_t s);
 cudaError_t launch_batch_range(const BatchCompressArgs& a, cudaStream_t s);
 cudaError_t launch_batch_compress(const BatchCompressArgs& a, int F, cudaStream_t s);
 cudaError_t launch_batch_general(const BatchCompressArgs& a, int F, int grid, cudaStream_t s);
-cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s);
+cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s, unsigned grid = 0);  // grid 0: one CTA per tile
 cudaError_t launch_batch_compact(const BatchCompactArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_batch_decompress(const BatchDecompressArgs& a, int F, cudaStream_t s);
 bool batch_prepare_kernels(int F);  // shared-memory attributes of the compression kernels; false on error

@@ -48,7 +48,7 @@ gpz_status upload(gpz_batch* p) {
 gpz_status make_plan(gpz_batch* p) {
     gpz_status st = core_finish(p->core, nullptr);
     if (st != GPZ_OK) return st;
-    if (cudaMalloc(&p->d_mem, core_device_bytes(p->core)) != cudaSuccess) {
+    if (dev_malloc(&p->d_mem, core_device_bytes(p->core)) != cudaSuccess) {
         p->d_mem = nullptr;
         return GPZ_ERR_OOM;
     }

@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(kThreads, 5) gpz_batch_compress_kernel(BatchCo
     __syncthreads();
     const SlotBlock idx{slot};
     if ((uint64_t)(idx.b() + 1) * kBlock <= A.n)
-        qse_block_fast<F, true, SlotBlock, false, PRE>(A, dsm, S, idx);
+        qse_block_fast<F, true, SlotBlock, kCmTemp, PRE>(A, dsm, S, idx);
     else
-        qse_block_fast<F, false, SlotBlock, false, PRE>(A, dsm, S, idx);
+        qse_block_fast<F, false, SlotBlock, kCmTemp, PRE>(A, dsm, S, idx);
 }
 
 // Blocks the fast path left to the general one (rare); the grid walks the
@@ -205,15 +205,16 @@ constexpr unsigned long long kPrefix = 2ull << 62;
 constexpr uint32_t kMaxBlockWords = 1u + (uint32_t)kMaxFields * (uint32_t)kBlock;
 
 __device__ unsigned long long lookback64(const BatchScanArgs& a, uint32_t tile) {
+    const long long limit = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
     unsigned long long excl = 0;
     int p = (int)tile - 1;
     while (p >= 0) {
         const long long t0 = clock64();
         unsigned long long st;
         for (;;) {
-            st = ld_acquire_u64(a.tile_state + p);
+            st = ld_relaxed_u64(a.tile_state + p);
             if ((st >> 62) != 0ull) break;
-            if (clock64() - t0 > (1ll << 31)) {
+            if (clock64() - t0 > limit) {
                 set_status(a.status, kStTimeout);
                 st = kPrefix;  // give up: treat the predecessor's prefix as 0
                 break;
@@ -436,9 +437,9 @@ cudaError_t launch_batch_general(const BatchCompressArgs& a, int F, int grid, cu
     return launch_group(a, F, grid, s, true);
 }
 
-cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s) {
+cudaError_t launch_batch_scan(const BatchScanArgs& a, cudaStream_t s, unsigned grid) {
     const unsigned tiles = (unsigned)(((uint64_t)a.total_blocks + 1 + kScanTile - 1) / kScanTile);
-    gpz_batch_scan_kernel<<<tiles, kScanThreads, 0, s>>>(a);
+    gpz_batch_scan_kernel<<<grid ? grid : tiles, kScanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -19,15 +19,16 @@ constexpr unsigned long long kFlagAggregate = 1ull << 32;
 constexpr unsigned long long kFlagPrefix = 2ull << 32;
 
 __device__ uint32_t lookback(const ScanArgs& a, uint32_t tile) {
+    const long long limit = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
     uint32_t excl = 0;
     int p = (int)tile - 1;
     while (p >= 0) {
         const long long t0 = clock64();
         unsigned long long st;
         for (;;) {
-            st = ld_acquire_u64(a.tile_state + p);
+            st = ld_relaxed_u64(a.tile_state + p);
             if ((st >> 32) != 0ull) break;
-            if (clock64() - t0 > (1ll << 31)) {
+            if (clock64() - t0 > limit) {
                 set_status(a.status, kStTimeout);
                 st = kFlagPrefix;  // give up: treat the predecessor's prefix as 0
                 break;
@@ -107,9 +108,9 @@ __global__ void __launch_bounds__(kScanThreads) gpz_scan_kernel(ScanArgs a) {
     }
 }
 
-cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s) {
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s, unsigned grid) {
     const unsigned tiles = (unsigned)((a.nblocks + 1 + kScanTile - 1) / kScanTile);
-    gpz_scan_kernel<<<tiles, kScanThreads, 0, s>>>(a);
+    gpz_scan_kernel<<<grid ? grid : tiles, kScanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
     uint32_t* payload = a.stream + a.payload_start;
     for (uint32_t b = blockIdx.x * kCompactWarps + warp; b < a.nblocks; b += nwarps) {
         if (__ldcg(a.sizes + b) & kPlaced) continue;  // written into the stream by the fused kernel
+        if (a.unplaced && lane == 0) atomicAdd(a.unplaced, 1u);
         const uint32_t len = __ldcg(a.table + b + 1) - __ldcg(a.table + b);  // clamped by the scan
         const uint32_t* src = a.temp + (size_t)b * a.slot_words;
         uint32_t* dst = payload + __ldcg(a.table + b);

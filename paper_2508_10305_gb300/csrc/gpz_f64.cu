@@ -265,6 +265,7 @@ gpz_status gpz_compress_f64(const double* const* d_fields, uint64_t n, const gpz
     q.mode = GPZ_EB_ABS;
     q.n_fields = F;
     q.seg_bits = p->seg_bits;
+    q.flags = p->flags;
     for (int f = 0; f < F; ++f) q.eb[f] = ebp[f];
     const float* fields[kMaxFields];
     for (int f = 0; f < F; ++f) fields[f] = y + (uint64_t)f * ld;

@@ -36,15 +36,17 @@ inline FieldParams finalise(double eb) {
 
 // ---------------------------------------------------------------- stage timing
 //
-// When enabled, each call records one event on its stream before its first
-// kernel and one after each kernel, from a pool; gpz_stage_times resolves
-// the logged pairs into per-stage totals and recycles the pool.
+// When enabled for a stream, each call on that stream records one event
+// before its first kernel and one after each kernel, from a pool;
+// gpz_stage_times resolves the logged pairs into per-stage totals and
+// recycles the pool.  Calls on other streams record nothing.
 
 constexpr int kEventPool = 8192;
 
 struct StageTimer {
     std::mutex mu;
     bool enabled = false;
+    cudaStream_t stream = nullptr;  // the one stream whose calls are timed
     bool created = false;
     cudaEvent_t ev[kEventPool] = {};
     int used = 0;
@@ -67,7 +69,7 @@ struct Recorder {
     // are reserved for the call's kernels.
     void begin(int marks = 8) {
         std::lock_guard<std::mutex> g(g_timer.mu);
-        if (!g_timer.enabled) return;
+        if (!g_timer.enabled || g_timer.stream != s) return;
         if (!g_timer.created) {
             for (auto& e : g_timer.ev) cudaEventCreate(&e);
             g_timer.created = true;
@@ -90,6 +92,25 @@ struct Recorder {
 };
 
 inline gpz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GPZ_OK : GPZ_ERR_CUDA; }
+
+// Device allocations made by the library (workspaces of calls given none,
+// batch plans, the serving arena) go through these, so that a test can make
+// the next ones fail as an exhausted device would (gpz_test_fail_next_allocations).
+extern std::atomic<int> g_fail_allocs;
+inline bool injected_alloc_failure() {
+    int k = g_fail_allocs.load();
+    while (k > 0)
+        if (g_fail_allocs.compare_exchange_weak(k, k - 1)) return true;
+    return false;
+}
+inline cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
+}
+inline cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

@@ -31,6 +31,11 @@ constexpr uint32_t kStCapacity = 2;
 constexpr uint32_t kStCorrupt = 3;
 constexpr uint32_t kStTimeout = 6;
 
+// Limit of every device-side wait on another CTA, in SM cycles (about a
+// second at 2 GHz): a wait that runs out records kStTimeout and the waiting
+// CTA carries on without the value it waited for.
+constexpr long long kWaitCycles = 1ll << 31;
+
 struct FieldParams {
     float eb;    // RN32(eb), stored in the header
     float s;     // quantisation step RN32(eb * 63/32)
@@ -80,6 +85,11 @@ struct QseArgs {
 
 constexpr uint32_t kPlaced = 0x80000000u;  // in a block's word count: already in the stream
 
+// Compaction forms of the per-block code: the temporary slot only (Section
+// 4.4's three steps), or fused (placed by the block itself after its
+// look-back over its predecessors' published sizes).
+constexpr int kCmTemp = 0, kCmDirect = 1;
+
 struct F64Args {                // fp64 input and output (gpz_f64.cu)
     const double* in[kMaxFields];
     float* out32[kMaxFields];
@@ -99,6 +109,7 @@ struct ScanArgs {
     unsigned long long* tile_state; // [ntiles], zeroed
     uint32_t* tile_counter;     // zeroed
     uint32_t* status;
+    long long wait_cycles;      // limit of a look-back wait in SM cycles; 0: kWaitCycles
 };
 
 struct CompactArgs {
@@ -116,6 +127,7 @@ struct CompactArgs {
     FieldParams params[kMaxFields];
     const FieldParams* d_params;
     unsigned long long* d_out_size; // nullable
+    uint32_t* unplaced;         // nullable: counts the blocks this kernel moves (in-kernel compaction forms)
     uint32_t version;           // header word 1
     uint32_t ext_words;         // nonzero: the header extension is ext[0..ext_words) instead of (eb, s) per field
     uint32_t ext[4 * kMaxFields];
@@ -240,54 +252,36 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// ---------------------------------------------------------------- mbarrier + bulk copy (sm_90+)
+// ---------------------------------------------------------------- bulk copy shared -> global (async proxy)
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// Orders this thread's earlier shared-memory writes before later reads of
+// them by the async proxy (a bulk copy issued after a barrier).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+// One thread: copy `bytes` (a multiple of 16) from shared memory to global
+// memory, both 16-byte aligned, with one bulk copy, and wait until the copy
+// has read its source (so that the CTA may exit or reuse the words).
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
                  : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait: gives up after ~2^31 SM cycles (about a second), records
-// kStTimeout, and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1ll << 31)) {
-            set_status(status, kStTimeout);
-            return false;
-        }
-    }
-    return true;
-}
-
-// One-dimensional bulk copy global -> shared, completing on the mbarrier.
-// Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(smem_dst)),
-        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- acquire / release (look-back scan)
+
+// A look-back reads other CTAs' published states with relaxed loads: the
+// value it needs is in the state word itself, and a gpu-scope acquire load
+// would also invalidate the SM's L1 for every CTA resident there.  A reader
+// that goes on to read data the state vouches for issues one fence first.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -308,7 +302,7 @@ cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
 cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
                               unsigned long long* binfo, cudaStream_t s);
-cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s);
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s, unsigned grid = 0);  // grid 0: one CTA per tile
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s);
 

@@ -7,10 +7,10 @@
 // device) is not acceptable.  For them this entry point takes its scratch
 // space -- the per-block temporary output, the block sizes and the prefix-sum
 // state of the compaction -- from a fixed array that is part of the library
-// image.  Every GPU that loads the library reserves that array until the
-// process exits.
-#include <mutex>
-
+// image.  The array lives in this file's own module, which holds no kernel:
+// under lazy module loading the module, and so the array's 32 MiB, is loaded
+// on a device at the first symbol lookup with that device current
+// (gpz_noalloc_prepare or the first call), and stays until the process exits.
 #include "gpz.h"
 #include "gpz_internal.cuh"
 
@@ -22,26 +22,31 @@ constexpr uint64_t kNoAllocScratchBytes = 32ull << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
-
-// Address of this device's scratch array (looked up once per device, with the
-// device current; host code must not use the symbol itself as an address).
+// Device address of the current device's scratch array.  Host code must not
+// use the symbol itself as an address.  The lookup is repeated on every call
+// (a host-side table lookup once the module is loaded), so no address
+// outlives a cudaDeviceReset.
 gpz_status scratch_of_current_device(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GPZ_ERR_CUDA;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GPZ_ERR_CUDA;
-        g_scratch[dev] = p;
-    }
-    *out = g_scratch[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GPZ_ERR_CUDA;
+    *out = p;
     return GPZ_OK;
 }
 
 }  // namespace
+
+extern "C" gpz_status gpz_noalloc_prepare(void) {
+    void* scratch = nullptr;
+    return scratch_of_current_device(&scratch);
+}
+
+extern "C" gpz_status gpz_noalloc_sync_status(void* stream) {
+    void* scratch = nullptr;
+    const gpz_status st = scratch_of_current_device(&scratch);
+    if (st != GPZ_OK) return st;
+    // the compression workspace's status word is its first word
+    return gpz_sync_status(scratch, stream);
+}
 
 extern "C" gpz_status gpz_compress_noalloc(const float* const* d_fields, uint64_t n, const gpz_params* p,
                                            void* d_out, uint64_t out_capacity, uint64_t* d_out_size,

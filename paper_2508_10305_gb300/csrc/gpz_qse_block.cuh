@@ -555,9 +555,15 @@ constexpr unsigned long long kBlkBroken = 3ull << 62;  // no prefix will follow
 constexpr uint32_t kNotPlaced = 0xffffffffu;
 constexpr long long kLookbackCycles = 1ll << 17;       // about 60 us
 
+
 // Exclusive prefix of the sizes of blocks 0..b-1 (every lane of one warp),
-// or kNotPlaced when the chain is broken.
-static __device__ __noinline__ uint32_t block_lookback(const QseArgs& a, uint32_t b) {
+// or kNotPlaced when the chain is broken: a predecessor left to the general
+// path, or one that has not published within `limit` SM cycles (0:
+// kLookbackCycles).  Giving up is not an error: the block then goes through
+// its temporary slot and the copy kernel.
+static __device__ __noinline__ uint32_t block_lookback(const unsigned long long* bstate, uint32_t b,
+                                                       long long limit = 0) {
+    if (limit <= 0) limit = kLookbackCycles;
     const int lane = threadIdx.x & 31;
     uint32_t excl = 0;
     for (int base = (int)b - 1;; base -= 32) {
@@ -566,9 +572,9 @@ static __device__ __noinline__ uint32_t block_lookback(const QseArgs& a, uint32_
         if (j >= 0) {
             const long long t0 = clock64();
             for (;;) {
-                st = ld_acquire_u64(a.bstate + j);
+                st = ld_relaxed_u64(bstate + j);
                 if (st >> 62) break;
-                if (clock64() - t0 > kLookbackCycles) {
+                if (clock64() - t0 > limit) {
                     st = kBlkBroken;
                     break;
                 }
@@ -589,13 +595,14 @@ static __device__ __noinline__ uint32_t block_lookback(const QseArgs& a, uint32_
 // A block stored raw (its words go to the temporary slot).  With fused
 // compaction it publishes its size and then, so that the blocks behind it
 // need not walk past it, its inclusive prefix (warp 0).
-template <int F, bool DIRECT>
+template <int F, int CM>
 __device__ __forceinline__ void raw_block(const QseArgs& a, uint32_t b, int n_b, int t) {
+    constexpr bool DIRECT = CM == kCmDirect;
     const uint32_t raw_words = 1u + (uint32_t)F * (uint32_t)n_b;
     if (DIRECT && t == 0) st_release_u64(a.bstate + b, (b == 0 ? kBlkIncl : kBlkAgg) | raw_words);
     write_raw<F>(a, b, n_b, t);
     if (DIRECT && b != 0 && (t >> 5) == 0) {
-        const uint32_t off = block_lookback(a, b);
+        const uint32_t off = block_lookback(a.bstate, b);
         if (t == 0) st_release_u64(a.bstate + b, off == kNotPlaced ? kBlkBroken : (kBlkIncl | (off + raw_words)));
     }
 }
@@ -676,9 +683,10 @@ constexpr int kInfoExact = 62;    // no first candidate of the block can fail it
 
 // PRE: the range pass has already found each block's extremes (a.bext);
 // otherwise the block finds them itself.
-template <int F, bool FULL, class Idx, bool DIRECT = false, bool PRE = false>
+template <int F, bool FULL, class Idx, int CM = kCmTemp, bool PRE = false>
 __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, QseFastShared& S, Idx idx) {
     constexpr int P = F < 3 ? F : 3;
+    constexpr bool DIRECT = CM == kCmDirect;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int n_b = FULL ? kBlock : (int)(a.n - (uint64_t)idx.b() * kBlock);
     uint16_t* hist = reinterpret_cast<uint16_t*>(dsm + kFastHist);          // [8][512] per-warp histograms
@@ -731,7 +739,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
 #pragma unroll
         for (int f = 0; f < F; ++f) nonfinite |= kmin[f] == 0u;
         if (nonfinite) {  // uniform: every thread read the same extremes
-            raw_block<F, DIRECT>(a, idx.b(), n_b, t);
+            raw_block<F, CM>(a, idx.b(), n_b, t);
             return;
         }
     } else {
@@ -758,7 +766,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         if (__any_sync(0xffffffffu, probe != probe) && lane == 0) atomicOr(&S.flags, 1u);
         __syncthreads();  // A
         if (S.flags & 1u) {
-            raw_block<F, DIRECT>(a, idx.b(), n_b, t);
+            raw_block<F, CM>(a, idx.b(), n_b, t);
             return;
         }
 #pragma unroll
@@ -951,7 +959,7 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
     const uint32_t rwords = ceil_words((uint32_t)n_b * W);
     const uint32_t enc = hdr + dwords + cwords + rwords;
     if (enc >= 1u + (uint32_t)F * (uint32_t)n_b) {
-        raw_block<F, DIRECT>(a, idx.b(), n_b, t);
+        raw_block<F, CM>(a, idx.b(), n_b, t);
         return;
     }
     if (DIRECT && t == 0) st_release_u64(a.bstate + idx.b(), (idx.b() == 0 ? kBlkIncl : kBlkAgg) | enc);
@@ -1008,16 +1016,16 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
             if (end > 128u) atomicOr(stage + wi + 4, __funnelshift_l(rw[r][3], 0u, sh));
         }
     }
+    fence_proxy_async_shared();  // the staging words may be read by a bulk copy (async proxy)
     __syncthreads();
     uint32_t off = kNotPlaced;
     if constexpr (DIRECT) {  // the block's offset from its predecessors' sizes
         if (w == 0) {
             const uint32_t b = idx.b();
-            uint32_t o = b == 0 ? 0u : block_lookback(a, b);
+            uint32_t o = b == 0 ? 0u : block_lookback(a.bstate, b);
             if (o != kNotPlaced && (uint64_t)o + enc > a.direct_capacity) o = kNotPlaced;
             if (lane == 0) {
                 if (b != 0) st_release_u64(a.bstate + b, o == kNotPlaced ? kBlkBroken : (kBlkIncl | (o + enc)));
-                if (o == kNotPlaced) atomicAdd(a.deferred_count, 1u);
                 S.offset = o;
             }
         }
@@ -1029,12 +1037,11 @@ __device__ __forceinline__ void qse_block_fast(const QseArgs& a, uint8_t* dsm, Q
         if (off != kNotPlaced) {  // straight into the stream (word-aligned)
             uint32_t* out = a.direct + off;
             for (uint32_t k = t; k < enc; k += kThreads) out[k] = stage[k];
-        } else {
-            uint32_t* out = a.temp + (size_t)b * a.slot_words;
-            const uint4* s4 = reinterpret_cast<const uint4*>(stage);
-            uint4* o4 = reinterpret_cast<uint4*>(out);
-            for (uint32_t k = t; k < (enc >> 2); k += kThreads) o4[k] = s4[k];
-            for (uint32_t k = (enc & ~3u) + t; k < enc; k += kThreads) out[k] = stage[k];
+        } else if (t == 0) {
+            // to the temporary slot (16-byte aligned, room for the rounding
+            // words) by one bulk copy, which the CTA's shared memory outlives:
+            // thread 0 waits until the copy has read the staging words
+            bulk_s2g(a.temp + (size_t)b * a.slot_words, stage, ((enc + 3u) & ~3u) * 4u);
         }
         const uint64_t first = (uint64_t)b * kBlock;
         if (a.perm)

@@ -12,9 +12,9 @@ __global__ void __launch_bounds__(kThreads, 5) gpz_qse_pre_kernel(QseArgs a) {
     extern __shared__ __align__(16) uint8_t dsm[];
     __shared__ QseFastShared S;
     if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
-        qse_block_fast<F, true, GridBlock, false, true>(a, dsm, S, GridBlock{});
+        qse_block_fast<F, true, GridBlock, kCmTemp, true>(a, dsm, S, GridBlock{});
     else
-        qse_block_fast<F, false, GridBlock, false, true>(a, dsm, S, GridBlock{});
+        qse_block_fast<F, false, GridBlock, kCmTemp, true>(a, dsm, S, GridBlock{});
 }
 
 // After the range pass, one thread per block: the widths and flags the fused

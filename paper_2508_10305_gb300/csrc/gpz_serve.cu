@@ -431,7 +431,7 @@ gpz_status gpz_server_create(const gpz_server_config* cfg, gpz_server_config* us
         free_server(S);
         return GPZ_ERR_CUDA;
     }
-    if (cudaMalloc(&S->d_arena, cfg->budget_bytes) != cudaSuccess) {
+    if (dev_malloc(reinterpret_cast<void**>(&S->d_arena), cfg->budget_bytes) != cudaSuccess) {
         S->d_arena = nullptr;
         free_server(S);
         return GPZ_ERR_OOM;

@@ -17,12 +17,13 @@ LIB_PATH = os.path.join(_HERE, "libgpz.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 EB_ABS, EB_REL = 0, 1
+FLAG_FUSED_COMPACTION = 1
 MAX_FIELDS = 8
 BLOCK = 1024
 
 
 class gpz_params(C.Structure):
-    _fields_ = [("mode", C.c_int), ("n_fields", C.c_int), ("seg_bits", C.c_int),
+    _fields_ = [("mode", C.c_int), ("n_fields", C.c_int), ("seg_bits", C.c_int), ("flags", C.c_uint),
                 ("eb", C.c_double * MAX_FIELDS)]
 
 
@@ -83,6 +84,10 @@ def _load():
     L.gpz_compress.restype = C.c_int
     L.gpz_compress_noalloc.argtypes = [P(vp), u64, P(gpz_params), vp, u64, vp, P(u64), vp, vp]
     L.gpz_compress_noalloc.restype = C.c_int
+    L.gpz_noalloc_prepare.argtypes = []
+    L.gpz_noalloc_prepare.restype = C.c_int
+    L.gpz_noalloc_sync_status.argtypes = [vp]
+    L.gpz_noalloc_sync_status.restype = C.c_int
     L.gpz_decompress.argtypes = [vp, u64, P(vp), C.c_int, u64, vp, u64, vp]
     L.gpz_decompress.restype = C.c_int
     L.gpz_sync_status.argtypes = [vp, vp]
@@ -91,10 +96,8 @@ def _load():
     L.gpz_inspect.restype = C.c_int
     L.gpz_status_str.argtypes = [C.c_int]
     L.gpz_status_str.restype = C.c_char_p
-    L.gpz_set_stage_timing.argtypes = [C.c_int]
+    L.gpz_set_stage_timing.argtypes = [vp, C.c_int]
     L.gpz_set_stage_timing.restype = None
-    L.gpz_set_fused_compaction.argtypes = [C.c_int]
-    L.gpz_set_fused_compaction.restype = C.c_int
     L.gpz_compress_f64_workspace_size.argtypes = [u64, C.c_int]
     L.gpz_compress_f64_workspace_size.restype = u64
     L.gpz_decompress_f64_workspace_size.argtypes = [u64, C.c_int]
@@ -123,6 +126,15 @@ def _load():
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
     L.gpz_launch_count.restype = u64
+    # failure-injection hooks (include/gpz_test.h)
+    L.gpz_test_fail_next_allocations.argtypes = [C.c_int]
+    L.gpz_test_fail_next_allocations.restype = C.c_int
+    L.gpz_test_scan_workspace_size.argtypes = []
+    L.gpz_test_scan_workspace_size.restype = u64
+    L.gpz_test_scan_timeout.argtypes = [C.c_int, C.c_uint32, vp, u64, vp]
+    L.gpz_test_scan_timeout.restype = C.c_int
+    L.gpz_test_block_lookback_timeout.argtypes = [C.c_uint32, C.c_uint32, vp, u64, P(C.c_int), vp]
+    L.gpz_test_block_lookback_timeout.restype = C.c_int
     # batched entry points (include/gpz_batch.h)
     L.gpz_batch_create_compress.argtypes = [P(gpz_compress_chunk), C.c_uint32, P(vp)]
     L.gpz_batch_create_compress.restype = C.c_int
@@ -185,13 +197,9 @@ def gpz_status_str(status):
     return lib.gpz_status_str(status).decode()
 
 
-def gpz_set_stage_timing(enable):
-    lib.gpz_set_stage_timing(1 if enable else 0)
-
-
-def gpz_set_fused_compaction(enable):
-    """Select the compaction form of later gpz_compress calls; returns the previous one."""
-    return bool(lib.gpz_set_fused_compaction(1 if enable else 0))
+def gpz_set_stage_timing(enable, stream=None):
+    """Time the later calls enqueued on `stream` (the current stream when None)."""
+    lib.gpz_set_stage_timing(_stream_handle(stream), 1 if enable else 0)
 
 
 def gpz_compress_aos_workspace_size(n, n_fields):
@@ -320,7 +328,7 @@ def decompress_wide(stream_buf, n_fields, n, size=None, stream=None):
 
 
 def compress_deferred_blocks(ws):
-    """After a fused-compaction call: the blocks that went through the copy kernel."""
+    """After a fused-compaction call: the blocks the copy kernel moved."""
     return int(ws[32:36].view(torch.int32).item())
 
 
@@ -335,6 +343,26 @@ def gpz_stage_times(max_stages=8):
 
 def gpz_launch_count(reset=False):
     return int(lib.gpz_launch_count(1 if reset else 0))
+
+
+def gpz_test_fail_next_allocations(count):
+    """Arm `count` injected device-allocation failures; returns how many were armed before."""
+    return int(lib.gpz_test_fail_next_allocations(count))
+
+
+def gpz_test_scan_timeout(batched, wait_cycles, ws, stream=None):
+    """Run a look-back scan whose first tile never publishes; returns the device status."""
+    return lib.gpz_test_scan_timeout(1 if batched else 0, wait_cycles, ws.data_ptr() if ws is not None else None,
+                                     ws.numel() if ws is not None else 0, _stream_handle(stream))
+
+
+def gpz_test_block_lookback_timeout(block, wait_cycles, ws, stream=None):
+    """One block's look-back with no predecessor published: (status, placed)."""
+    placed = C.c_int(-1)
+    st = lib.gpz_test_block_lookback_timeout(block, wait_cycles, ws.data_ptr() if ws is not None else None,
+                                             ws.numel() if ws is not None else 0, C.byref(placed),
+                                             _stream_handle(stream))
+    return st, placed.value
 
 
 def gpz_inspect(header_bytes):
@@ -361,9 +389,9 @@ def _ptr_array(tensors):
     return arr
 
 
-def make_params(n_fields, eb, mode=EB_ABS, seg_bits=3):
+def make_params(n_fields, eb, mode=EB_ABS, seg_bits=3, flags=0):
     p = gpz_params()
-    p.mode, p.n_fields, p.seg_bits = mode, n_fields, seg_bits
+    p.mode, p.n_fields, p.seg_bits, p.flags = mode, n_fields, seg_bits, flags
     ebs = list(eb) if hasattr(eb, "__len__") else [eb] * n_fields
     if len(ebs) != n_fields:
         raise ValueError("need one error bound per field")
@@ -396,6 +424,16 @@ def gpz_compress_noalloc(fields, n, params, out, out_capacity, d_out_size=None, 
                                     d_out_size.data_ptr() if d_out_size is not None else None,
                                     C.byref(h_out_size) if h_out_size is not None else None,
                                     perm.data_ptr() if perm is not None else None, _stream_handle(stream))
+
+
+def gpz_noalloc_prepare():
+    """Take gpz_compress_noalloc's scratch array on the current device now."""
+    return lib.gpz_noalloc_prepare()
+
+
+def gpz_noalloc_sync_status(stream=None):
+    """Read and clear the device-side status of earlier gpz_compress_noalloc calls."""
+    return lib.gpz_noalloc_sync_status(_stream_handle(stream))
 
 
 def gpz_decompress(stream_buf, in_size, fields, n_fields, n, ws=None, ws_size=0, stream=None):
@@ -479,10 +517,10 @@ class Compressor:
     allocate nothing: out (bound size), workspace, size word and optional
     permutation."""
 
-    def __init__(self, n, n_fields, eb, mode=EB_ABS, seg_bits=3, want_perm=False, device=None):
+    def __init__(self, n, n_fields, eb, mode=EB_ABS, seg_bits=3, want_perm=False, device=None, flags=0):
         device = device or torch.device("cuda")
         self.n, self.F = n, n_fields
-        self.params = make_params(n_fields, eb, mode, seg_bits)
+        self.params = make_params(n_fields, eb, mode, seg_bits, flags)
         self.capacity = gpz_bound_size(n, n_fields)
         self.out = torch.empty(max(self.capacity, 16), dtype=torch.uint8, device=device)
         self.ws_size = gpz_compress_workspace_size(n, n_fields)

@@ -1,6 +1,6 @@
-"""The C ABI library loads and exports every entry point include/gpz.h,
-include/gpz_batch.h and include/gpz_serve.h declare; host-side entry points
-behave without touching a GPU."""
+"""The C ABI library loads and exports every entry point the headers under
+include/ declare (gpz.h, gpz_batch.h, gpz_serve.h, gpz_test.h); host-side
+entry points behave without touching a GPU."""
 import ctypes as C
 import os
 import re
@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("gpz.h", "gpz_batch.h", "gpz_serve.h")]
+HEADERS = sorted(os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))
+                 if h.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -34,6 +35,13 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gpz_bound_size", "gpz_compress", "gpz_decompress", "gpz_compress_workspace_size",
                      "gpz_decompress_workspace_size", "gpz_sync_status", "gpz_inspect", "gpz_status_str"):
+        assert required in names
+
+
+def test_header_declares_the_test_hooks():
+    names = declared_functions()
+    for required in ("gpz_test_fail_next_allocations", "gpz_test_scan_workspace_size", "gpz_test_scan_timeout",
+                     "gpz_test_block_lookback_timeout"):
         assert required in names
 
 
@@ -116,6 +124,7 @@ def test_batch_struct_layout_matches_the_header(gpz, tmp_path):
 #include "gpz_batch.h"
 #include "gpz_serve.h"
 int main(void) {
+    printf("%zu %zu %zu ", sizeof(gpz_params), offsetof(gpz_params, flags), offsetof(gpz_params, eb));
     printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu ", sizeof(gpz_compress_chunk), offsetof(gpz_compress_chunk, n),
            offsetof(gpz_compress_chunk, params), offsetof(gpz_compress_chunk, out),
            offsetof(gpz_compress_chunk, perm), sizeof(gpz_decompress_chunk),
@@ -132,7 +141,8 @@ int main(void) {
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     cc, dc = gpz.gpz_compress_chunk, gpz.gpz_decompress_chunk
     sc, rr = gpz.gpz_server_config, gpz.gpz_request_result
-    want = [C.sizeof(cc), cc.n.offset, cc.params.offset, cc.out.offset, cc.perm.offset, C.sizeof(dc),
+    gp = gpz.gpz_params
+    want = [C.sizeof(gp), gp.flags.offset, gp.eb.offset, C.sizeof(cc), cc.n.offset, cc.params.offset, cc.out.offset, cc.perm.offset, C.sizeof(dc),
             dc.n_fields.offset, dc.n.offset, C.sizeof(gpz.gpz_batch_config),
             C.sizeof(sc), sc.max_batch_bytes.offset, sc.lane_bytes.offset, C.sizeof(rr), rr.out.offset, rr.batch.offset,
             C.sizeof(gpz.gpz_server_stats)]
@@ -294,3 +304,27 @@ def test_package_never_reaches_the_oracle():
                 if re.search(r"(from|import)\s+oracle\b|gpz_oracle|gpzo_|oracle[/\\]", text):
                     offenders.append(f)
     assert not offenders, offenders
+
+
+def test_failure_hooks_need_no_device(gpz):
+    """The hooks refuse bad arguments before any device call, and an armed
+    allocation failure makes a call without a workspace return
+    GPZ_ERR_OOM before it touches the device (its arguments are checked
+    first, and the allocation is the call's first device operation)."""
+    L = gpz.lib
+    assert L.gpz_test_scan_timeout(0, 1000, None, 0, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_test_scan_timeout(1, 0, 256, 1 << 20, None) == gpz.ERR_INVALID_ARG
+    placed = C.c_int(0)
+    assert L.gpz_test_block_lookback_timeout(0, 1000, 256, 4096, C.byref(placed), None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_test_block_lookback_timeout(5, 1000, None, 4096, C.byref(placed), None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_test_scan_workspace_size() > 8 * 8193
+    assert gpz.gpz_test_fail_next_allocations(2) == 0
+    try:
+        params = gpz.make_params(3, 1e-2)
+        fake = (C.c_void_p * 3)(4096, 8192, 12288)  # never dereferenced: the call stops at the allocation
+        cap = gpz.gpz_bound_size(100, 3)
+        assert L.gpz_compress(fake, 100, C.byref(params), 65536, cap, None, None, None, None, 0, None) == gpz.ERR_OOM
+        assert L.gpz_decompress(65536, 4 * 64, fake, 3, 100, None, 0, None) == gpz.ERR_OOM
+        assert gpz.gpz_test_fail_next_allocations(0) == 0
+    finally:
+        gpz.gpz_test_fail_next_allocations(0)

@@ -25,7 +25,7 @@ def gpz():
     return g
 
 
-def run_gpu(gpz, x, eb, mode, G, offset=0):
+def run_gpu(gpz, x, eb, mode, G, offset=0, flags=0):
     """Compress + decompress x [F, n] on the GPU; `offset` shifts every field
     by that many floats from a 16-byte boundary (exercises the plain-load
     staging path)."""
@@ -33,7 +33,7 @@ def run_gpu(gpz, x, eb, mode, G, offset=0):
     buf = torch.zeros((F, n + 8), dtype=torch.float32, device="cuda")
     buf[:, offset:offset + n] = torch.from_numpy(x).cuda()
     fields = [buf[f, offset:offset + n] for f in range(F)]
-    c = gpz.Compressor(n, F, eb, mode, G, want_perm=True)
+    c = gpz.Compressor(n, F, eb, mode, G, want_perm=True, flags=flags)
     size = c(fields)
     stream = c.out[:size].clone()
     d = gpz.Decompressor(n, F)
@@ -42,9 +42,9 @@ def run_gpu(gpz, x, eb, mode, G, offset=0):
     return stream.cpu().numpy(), c.perm[:n].cpu().numpy().astype(np.uint32), out.cpu().numpy().copy()
 
 
-def assert_parity(gpz, oracle, x, eb, mode=0, G=3, offset=0):
+def assert_parity(gpz, oracle, x, eb, mode=0, G=3, offset=0, flags=0):
     F, n = x.shape
-    s, p, o = run_gpu(gpz, x, eb, mode, G, offset)
+    s, p, o = run_gpu(gpz, x, eb, mode, G, offset, flags)
     rs, rp = oracle.compress(x, eb, mode, G)
     if s.size != rs.size or not np.array_equal(s, rs):
         w, rw = s.view(np.uint32), rs.view(np.uint32)
@@ -272,15 +272,97 @@ def test_lidar_200m_sampled(gpz, oracle):
     assert x.numel() * 4 / size > 2.0
 
 
-@pytest.fixture
-def fused(gpz):
-    prev = gpz.gpz_set_fused_compaction(True)
-    yield
-    gpz.gpz_set_fused_compaction(prev)
+def _whole_stream(gpz, oracle, x_dev, eb, mode, G):
+    """Compress and decompress the whole array on the GPU (the benchmark's
+    launch configuration) and compare everything with the oracle run over
+    all host threads by block ranges.  Returns (ratio, raw blocks, blocks
+    left to the general kernel)."""
+    from tests import _whole
+    F, n = x_dev.shape
+    c = gpz.Compressor(n, F, eb, mode, G, want_perm=True)
+    size = c([x_dev[f] for f in range(F)])
+    general = int(c.ws[12:16].view(torch.int32).item())
+    d = gpz.Decompressor(n, F)
+    out = d(c.out[:size], size).cpu().numpy()
+    words = c.out[:size].cpu().numpy().view(np.uint32)
+    perm = c.perm[:n].cpu().numpy().view(np.uint32)
+    x = x_dev.cpu().numpy()
+    raw = _whole.compare_whole(oracle, x, eb, mode, G, words, perm, out)
+    return x.nbytes / size, raw, general
+
+
+def test_cosmology_64m_whole(gpz, oracle):
+    """2^26 particles x 6 fields, relative bound 1e-4 (the benchmark
+    workload): the whole stream, permutation and output, bit for bit."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.cosmology(1 << 26, seed=2, device="cuda")
+    ratio, raw, general = _whole_stream(gpz, oracle, x, 1e-4, 1, 3)
+    print("cosmology 2^26 x 6: ratio %.4f, raw blocks %d, general-path blocks %d" % (ratio, raw, general))
+    assert ratio > 2.0
+
+
+def test_lidar_200m_whole(gpz, oracle):
+    """2e8 points x 3, absolute bound 1e-3 m: the whole stream, bit for bit,
+    including the blocks the fast kernel leaves to the general kernel
+    (values that need a fallback candidate)."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.lidar(200_000_000, seed=3, device="cuda")
+    ratio, raw, general = _whole_stream(gpz, oracle, x, 1e-3, 0, 3)
+    print("lidar 2e8 x 3: ratio %.4f, raw blocks %d, general-path blocks %d" % (ratio, raw, general))
+    assert ratio > 2.0 and general > 0
 
 
 @pytest.mark.parametrize("case", ["all_fast", "raw_blocks", "general_block"])
-def test_fused_compaction(gpz, oracle, fused, case):
+@pytest.mark.parametrize("flags", [0, 1])
+def test_midsize_compaction(gpz, oracle, case, flags):
+    """Arrays of a few thousand blocks (more than one wave of CTAs), with raw
+    blocks and a block left to the general path, in both compaction forms:
+    the stream, permutation and decompressed values are the oracle's, bit
+    for bit."""
+    rng = np.random.default_rng({"all_fast": 11, "raw_blocks": 12, "general_block": 13}[case])
+    F, nb = 3, 3000
+    n = (nb - 1) * 1024 + 333  # ragged last block
+    x = (rng.random((F, n)) * 256).astype(np.float32)
+    if case == "raw_blocks":
+        for b in (0, 5, 1535, 1536, 1700, nb - 1):
+            x[b % F, b * 1024 + 3 if b < nb - 1 else n - 2] = np.nan
+    if case == "general_block":
+        x[0, 2000 * 1024:2001 * 1024] *= 1e5  # codes far above 2^23: the general path
+    assert_parity(gpz, oracle, x, 1e-2, 0, 3, flags=flags)
+
+
+@pytest.mark.parametrize("n,F,G,mode,kind,eb,seed", [
+    (1600 * 1024 + 1, 6, 3, 1, "clustered", 1e-4, 5),
+    (1537 * 1024, 3, 2, 0, "lidar", 1e-3, 6),
+    (2100 * 1024 + 777, 8, 1, 1, "mixed", 1e-3, 7),
+    (1800 * 1024 + 5, 2, 0, 0, "uniform", 1e-2, 8),
+])
+def test_midsize_random(gpz, oracle, n, F, G, mode, kind, eb, seed):
+    rng = np.random.default_rng(seed)
+    assert_parity(gpz, oracle, gen(kind, F, n, rng), eb, mode, G)
+
+
+def test_compaction_forms_agree(gpz):
+    """Both compaction forms write the same bytes on the 2^26 x 6 cosmology
+    snapshot (the benchmark workload); the fused form places every block
+    itself."""
+    from paper_2508_10305_gb300 import synth
+    x = synth.cosmology(1 << 26, seed=2, device="cuda")
+    F, n = x.shape
+    ref = None
+    for flags in (0, gpz.FLAG_FUSED_COMPACTION):
+        c = gpz.Compressor(n, F, 1e-4, gpz.EB_REL, 3, flags=flags)
+        size = c([x[f] for f in range(F)])
+        if ref is None:
+            ref = c.out[:size].clone()
+        else:
+            assert size == ref.numel() and torch.equal(c.out[:size], ref)
+            assert gpz.compress_deferred_blocks(c.ws) < n // 1024 // 100
+        del c
+
+
+@pytest.mark.parametrize("case", ["all_fast", "raw_blocks", "general_block"])
+def test_fused_compaction(gpz, oracle, case):
     """Fused compaction writes a block straight into the stream once every
     block before it has published its size.  Raw blocks (non-finite values)
     keep that chain going; a block left to the general path breaks it, and
@@ -296,42 +378,25 @@ def test_fused_compaction(gpz, oracle, fused, case):
         x[0, 5 * 1024:6 * 1024] *= 1e5  # codes far above 2^23 at eb 1e-2: the general path
     nb = (n + 1023) // 1024
     xd = torch.from_numpy(x).cuda()
-    c = gpz.Compressor(n, F, 1e-2, 0, 3, want_perm=True)
+    c = gpz.Compressor(n, F, 1e-2, 0, 3, want_perm=True, flags=gpz.FLAG_FUSED_COMPACTION)
     size = c([xd[f] for f in range(F)])
     torch.cuda.synchronize()
     rs, rp = oracle.compress(x, 1e-2, 0, 3)
     assert size == rs.size and np.array_equal(c.out[:size].cpu().numpy(), rs)
     assert np.array_equal(c.perm[:n].cpu().numpy().astype(np.uint32), rp)
-    deferred = gpz.compress_deferred_blocks(c.ws)
+    deferred = gpz.compress_deferred_blocks(c.ws)  # blocks the copy kernel moved
     if case == "general_block":
-        assert 0 < deferred <= nb - 6
+        assert 0 < deferred <= nb - 5
+    elif case == "raw_blocks":
+        assert deferred == 2  # raw blocks always go through their slots
     else:
         assert deferred == 0  # every block found its offset (ordinary launch order)
 
 
 @pytest.mark.parametrize("n,F,G,mode,kind,eb,seed", CASES[:16])
-def test_fused_compaction_random(gpz, oracle, fused, n, F, G, mode, kind, eb, seed):
+def test_fused_compaction_random(gpz, oracle, n, F, G, mode, kind, eb, seed):
     rng = np.random.default_rng(seed)
-    assert_parity(gpz, oracle, gen(kind, F, n, rng), eb, mode, G)
-
-
-def test_fused_compaction_full_size(gpz):
-    """The 2^26 x 6 cosmology snapshot: the fused and the three-step
-    compaction write the same bytes."""
-    from paper_2508_10305_gb300 import synth
-    x = synth.cosmology(1 << 26, seed=2, device="cuda")
-    F, n = x.shape
-    c = gpz.Compressor(n, F, 1e-4, gpz.EB_REL, 3)
-    size = c([x[f] for f in range(F)])
-    ref = c.out[:size].clone()
-    prev = gpz.gpz_set_fused_compaction(True)
-    try:
-        size2 = c([x[f] for f in range(F)])
-        deferred = gpz.compress_deferred_blocks(c.ws)
-    finally:
-        gpz.gpz_set_fused_compaction(prev)
-    assert size2 == size and torch.equal(c.out[:size], ref)
-    assert deferred < n // 1024 // 100
+    assert_parity(gpz, oracle, gen(kind, F, n, rng), eb, mode, G, flags=gpz.FLAG_FUSED_COMPACTION)
 
 
 def test_unchecked_first_candidates_boundary(gpz, oracle):
