@@ -1,7 +1,9 @@
 // gpz_api.cu -- host side of libgpz: the C ABI declared in include/gpz.h.
 // Validates arguments, lays out the workspace, finalises the per-field
 // constants and enqueues the kernels on the caller's stream:
-//   compress:   [range (relative bound)] -> Q.S.E. -> look-back scan -> copy
+//   compress:   [range (relative bound)] -> Q.S.E. (shared-memory tile kernel,
+//               or, for fields not 16-byte aligned, block widths + register
+//               kernel) -> look-back scan -> copy
 //   decompress: decode
 #include <atomic>
 #include <cmath>
@@ -242,6 +244,11 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
             for (int f = 0; f < F; ++f) hp[f] = finalise(p->eb[f]);
         bool vec_ok = true;
         for (int f = 0; f < F && n > 0; ++f) vec_ok = vec_ok && aligned(d_fields[f], 16);
+        const bool fused = (p->flags & GPZ_FLAG_FUSED_COMPACTION) != 0u;
+        // the shared-memory tile kernel takes 16-byte aligned fields and derives
+        // each block's widths itself; the register kernel reads them from the
+        // block-info pass (relative bound)
+        const bool tile = vec_ok && !fused;
 
         if (rel) {
             RangeArgs ra{};
@@ -262,7 +269,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
                 if ((rc = cuda_status(launch_range(ra, grid, s))) != GPZ_OK) break;
                 rec.mark("range");
             }
-            if (nb > 0) {
+            if (nb > 0 && !tile) {
                 if ((rc = cuda_status(launch_block_info(ra.bext, d_params, (uint32_t)nb, F,
                                                         reinterpret_cast<unsigned long long*>(ws + L.binfo), s))) !=
                     GPZ_OK)
@@ -283,7 +290,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         qa.bulk_ok = vec_ok ? 1 : 0;
         qa.d_params = rel ? d_params : nullptr;
         qa.bext = rel ? reinterpret_cast<const uint2*>(ws + L.bext) : nullptr;
-        qa.binfo = rel ? reinterpret_cast<const unsigned long long*>(ws + L.binfo) : nullptr;
+        qa.binfo = rel && !tile ? reinterpret_cast<const unsigned long long*>(ws + L.binfo) : nullptr;
         qa.temp = reinterpret_cast<uint32_t*>(ws + L.temp);
         qa.slot_words = slot_words_of(F);
         qa.sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
@@ -291,7 +298,6 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         qa.status = status;
         qa.general_list = reinterpret_cast<uint32_t*>(ws + L.list);
         qa.general_count = status + 3;
-        const bool fused = (p->flags & GPZ_FLAG_FUSED_COMPACTION) != 0u;
         const uint32_t table_start = (uint32_t)(kHeaderWords + 2 * F);
         if (fused) {
             const uint64_t payload_start = table_start + nb + 1;
@@ -301,7 +307,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
             qa.deferred_count = status + 8;
         }
         if (nb > 0) {
-            const cudaError_t e = fused ? launch_qse_direct(qa, s) : launch_qse(qa, s);
+            const cudaError_t e = fused ? launch_qse_direct(qa, s) : tile ? launch_qse_tile(qa, s) : launch_qse(qa, s);
             if ((rc = cuda_status(e)) != GPZ_OK) break;
             rec.mark("qse");
             ++g_launches;  // launch_qse enqueues two kernels: the fast path and the general list

@@ -252,6 +252,59 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// ---------------------------------------------------------------- mbarrier + bulk copy global -> shared
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive (the one expected arrival) and announce `bytes` of bulk copies.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of the mbarrier, for at most kWaitCycles SM
+// cycles; on expiry record kStTimeout, wait once more as long (so that bulk
+// copies still in flight into this CTA's shared memory are not left behind
+// by an exiting CTA), and return false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            set_status(status, kStTimeout);
+            t0 = clock64();
+            while (!mbar_try_wait(bar, parity))
+                if (clock64() - t0 > kWaitCycles) break;
+            return false;
+        }
+    }
+    return true;
+}
+
+// One-dimensional bulk copy global -> shared, completing on the mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---------------------------------------------------------------- bulk copy shared -> global (async proxy)
 
 // Orders this thread's earlier shared-memory writes before later reads of
@@ -300,6 +353,7 @@ cudaError_t launch_qse(const QseArgs& a, cudaStream_t s);         // fast kernel
 cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s);  // the same with blocks placed directly
 cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
+cudaError_t launch_qse_tile(const QseArgs& a, cudaStream_t s);    // shared-memory tile kernel (16-byte aligned fields)
 cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
                               unsigned long long* binfo, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s, unsigned grid = 0);  // grid 0: one CTA per tile
