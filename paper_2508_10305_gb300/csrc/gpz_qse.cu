@@ -59,15 +59,14 @@ __global__ void __launch_bounds__(kRangeThreads, 8) gpz_range_kernel(RangeArgs a
         const float* x = a.fields[f] + b * kBlock;
         const int n_b = (int)min((uint64_t)kBlock, a.n - b * kBlock);
         float lo = INFINITY, hi = -INFINITY, probe = 0.0f;  // probe: NaN if any value is NaN or infinite
-        if (a.vec_ok && n_b == kBlock) {  // 256 16-byte words: two rounds of four loads in flight per lane
+        if (a.vec_ok && n_b == kBlock) {  // 256 16-byte words: all eight of a lane in flight at once
             const float4* x4 = reinterpret_cast<const float4*>(x);
+            float4 v[8];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float4 v[4];
+            for (int k = 0; k < 8; ++k) v[k] = __ldcs(x4 + lane + 32 * k);
+            {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) v[k] = __ldcs(x4 + lane + 32 * (4 * h + k));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     lo = fminf(lo, fminf(fminf(v[k].x, v[k].y), fminf(v[k].z, v[k].w)));
                     hi = fmaxf(hi, fmaxf(fmaxf(v[k].x, v[k].y), fmaxf(v[k].z, v[k].w)));
                     probe = __fmaf_rn(v[k].x, 0.0f, probe);

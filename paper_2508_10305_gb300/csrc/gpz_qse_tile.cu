@@ -353,9 +353,9 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
     }
 
     // ---- 5. block header and the three arrays (Section 4.3), assembled in the
-    // cleared staging words -- the deltas and counts by thread-serial
-    // appenders, the records each at its sorted position -- then one bulk
-    // copy to the temporary slot
+    // cleared staging words -- each thread ORs in two deltas, two counts and
+    // its four records at their positions -- then one bulk copy to the
+    // temporary slot
     if (t == 0) stage[0] = (U << 1) | (wd << 12) | (wc << 17);
     if (t >= 1 && t <= F) stage[t] = __float_as_uint(S.fc[t - 1].mn);
     if (t < ((F + 3) >> 2)) {
@@ -366,18 +366,24 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
         stage[1 + F + t] = word;
     }
     {
+        // deltas and counts of unique ids 2t and 2t+1: at most 2 x 9 and
+        // 2 x 11 bits, so each pair is ORed into at most two words
         const uint32_t k0 = 2u * (uint32_t)t;
-        if (k0 < U && wd) {
-            BitAppender ap(32u * hdr + k0 * wd);
-            ap.put(stage, (uint32_t)uniq[k0] - (k0 ? (uint32_t)uniq[k0 - 1] : 0u), wd);
-            if (k0 + 1 < U) ap.put(stage, (uint32_t)uniq[k0 + 1] - (uint32_t)uniq[k0], wd);
-            ap.finish(stage);
-        }
-        if (k0 < U && wc) {
-            BitAppender ap(32u * (hdr + dwords) + k0 * wc);
-            ap.put(stage, (uint32_t)cnt[k0], wc);
-            if (k0 + 1 < U) ap.put(stage, (uint32_t)cnt[k0 + 1], wc);
-            ap.finish(stage);
+        if (k0 < U) {
+            const bool two = k0 + 1 < U;
+            const uint32_t u0 = uniq[k0], u1 = two ? (uint32_t)uniq[k0 + 1] : u0;
+            const uint32_t dv = (u0 - (k0 ? (uint32_t)uniq[k0 - 1] : 0u)) | ((u1 - u0) << wd);
+            const uint32_t cv = (uint32_t)cnt[k0] | ((two ? (uint32_t)cnt[k0 + 1] : 0u) << wc);
+            const uint32_t nd = (two ? 2u : 1u) * wd, nc = (two ? 2u : 1u) * wc;
+            const uint32_t dp = 32u * hdr + k0 * wd, cp = 32u * (hdr + dwords) + k0 * wc;
+            if (nd) {
+                atomicOr(stage + (dp >> 5), dv << (dp & 31u));
+                if ((dp & 31u) + nd > 32u) atomicOr(stage + (dp >> 5) + 1, dv >> (32u - (dp & 31u)));
+            }
+            if (nc) {
+                atomicOr(stage + (cp >> 5), cv << (cp & 31u));
+                if ((cp & 31u) + nc > 32u) atomicOr(stage + (cp >> 5) + 1, cv >> (32u - (cp & 31u)));
+            }
         }
     }
     // the records: each thread ORs its own four at their sorted positions
