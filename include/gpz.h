@@ -188,6 +188,24 @@ gpz_status gpz_noalloc_sync_status(void* stream);
 gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fields, int n_fields,
                           uint64_t n, void* d_ws, uint64_t ws_size, void* stream);
 
+/* Copy a stream whose size is known only on the device -- the d_out_size
+ * word of an earlier gpz_compress call -- from src to dst, with no host
+ * round trip (the paper has no counterpart: a convenience for pipelines that
+ * move compressed streams between host and device memory).  Exactly
+ * min(*d_size, capacity) bytes (rounded down to whole words) are copied, by
+ * a kernel enqueued on `stream` that reads *d_size when it runs.
+ *   dst, src: device memory, or page-locked host memory that the device can
+ *             address (with unified addressing, every cudaHostAlloc /
+ *             cudaMallocHost allocation), 4-byte aligned (16-byte alignment of
+ *             both enables 16-byte copies); the ranges must not overlap.
+ *   d_size:   device (or device-addressable) uint64, 8-byte aligned.
+ *   capacity: the most bytes dst can take.
+ * A stream copied this way can be decompressed with in_size = the buffer's
+ * capacity: gpz_decompress reads only the words the stream's header says it
+ * has.  Returns GPZ_ERR_INVALID_ARG for a NULL or misaligned pointer,
+ * GPZ_ERR_CUDA if the launch fails. */
+gpz_status gpz_copy_stream(void* dst, const void* src, const uint64_t* d_size, uint64_t capacity, void* stream);
+
 /* Synchronise `stream`, return the status recorded in the workspace d_ws by
  * the kernels of earlier calls (GPZ_OK if none), and clear it. */
 gpz_status gpz_sync_status(void* d_ws, void* stream);

@@ -90,6 +90,8 @@ def _load():
     L.gpz_noalloc_sync_status.restype = C.c_int
     L.gpz_decompress.argtypes = [vp, u64, P(vp), C.c_int, u64, vp, u64, vp]
     L.gpz_decompress.restype = C.c_int
+    L.gpz_copy_stream.argtypes = [vp, vp, vp, u64, vp]
+    L.gpz_copy_stream.restype = C.c_int
     L.gpz_sync_status.argtypes = [vp, vp]
     L.gpz_sync_status.restype = C.c_int
     L.gpz_inspect.argtypes = [vp, u64, P(u64), P(C.c_int), P(C.c_int), P(C.c_int)]
@@ -444,6 +446,12 @@ def gpz_decompress(stream_buf, in_size, fields, n_fields, n, ws=None, ws_size=0,
                               ws.data_ptr() if ws is not None else None, ws_size, _stream_handle(stream))
 
 
+def gpz_copy_stream(dst, src, d_size, capacity, stream=None):
+    """Mirror of the C entry point: dst/src/d_size are tensors (device, or
+    pinned host memory); the byte count is read from d_size on the device."""
+    return lib.gpz_copy_stream(dst.data_ptr(), src.data_ptr(), d_size.data_ptr(), capacity, _stream_handle(stream))
+
+
 def gpz_sync_status(ws, stream=None):
     return lib.gpz_sync_status(ws.data_ptr(), _stream_handle(stream))
 
@@ -753,11 +761,17 @@ class Server:
         return out
 
     def stream_of(self, result):
-        """A polled compress result's stream as a CUDA uint8 view (valid until release)."""
+        """A polled compress result's stream as a CUDA uint8 view (valid until
+        release).  A copy of it runs on the caller's current stream, which the
+        engine's lanes do not wait for: synchronise that stream before
+        releasing the result, or a later request may overwrite the memory
+        first."""
         return device_bytes(result["out"], result["out_bytes"])
 
     def fields_of(self, result, n_fields, n):
-        """Decompressed fields of a polled result as a [F, n] float32 CUDA tensor (a copy)."""
+        """Decompressed fields of a polled result as a [F, n] float32 CUDA
+        tensor (a copy, enqueued on the caller's current stream: synchronise
+        it before releasing the result)."""
         stride = result["field_stride"]
         raw = device_bytes(result["out"], stride * n_fields)
         return torch.stack([raw[f * stride:f * stride + 4 * n].view(torch.float32) for f in range(n_fields)])

@@ -328,3 +328,10 @@ def test_failure_hooks_need_no_device(gpz):
         assert gpz.gpz_test_fail_next_allocations(0) == 0
     finally:
         gpz.gpz_test_fail_next_allocations(0)
+
+
+def test_copy_stream_argument_errors_need_no_device(gpz):
+    L = gpz.lib
+    assert L.gpz_copy_stream(None, 256, 256, 64, None) == gpz.ERR_INVALID_ARG
+    assert L.gpz_copy_stream(256, 258, 256, 64, None) == gpz.ERR_INVALID_ARG  # src not 4-byte aligned
+    assert L.gpz_copy_stream(256, 512, 260, 64, None) == gpz.ERR_INVALID_ARG  # size word not 8-byte aligned

@@ -90,3 +90,31 @@ def test_reference_arm_line_on_rank_zero(capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_encodes_the_gpu_arms_blocks():
+    """The reference arm turns the relative bound into absolute bounds over
+    the whole snapshot (bench.absolute_bounds) before compressing its block
+    samples, so every sampled block is encoded word for word as in the
+    stream of the whole snapshot with the relative bound -- the stream the
+    GPU arm writes.  Checked with the oracle on a small snapshot, and the
+    reference line's config is the GPU arm's."""
+    import numpy as np
+    import bench
+    from oracle import gpz_oracle as o
+    from paper_2508_10305_gb300 import synth
+    x = synth.cosmology(1 << 15, seed=2).numpy()
+    F, n = x.shape
+    whole, _ = o.compress(x, bench.REL_EB, 1, bench.SEG_BITS)
+    ebs = bench.absolute_bounds(x, bench.REL_EB)
+    blocks = np.arange(1, n // 1024, 5)
+    sel = (blocks[:, None] * 1024 + np.arange(1024)[None, :]).reshape(-1)
+    part, _ = o.compress(np.ascontiguousarray(x[:, sel]), ebs, 0, bench.SEG_BITS)
+    w, p = whole.view(np.uint32), part.view(np.uint32)
+    nb, nbp = n // 1024, blocks.size
+    tw, tp = w[16 + 2 * F:16 + 2 * F + nb + 1], p[16 + 2 * F:16 + 2 * F + nbp + 1]
+    pw, pp = w[16 + 2 * F + nb + 1:], p[16 + 2 * F + nbp + 1:]
+    for k, b in enumerate(blocks):
+        assert np.array_equal(pw[tw[b]:tw[b + 1]], pp[tp[k]:tp[k + 1]]), b
+    assert w[16:16 + 2 * F].tolist() == p[16:16 + 2 * F].tolist()  # eb and step of every field
+    assert bench.gpu_config(1 << 26, 1)["workload"] == bench.WORKLOAD

@@ -66,6 +66,7 @@ def serve(gpz, reqs, **cfg):
                 got[k] = (res, srv.stream_of(res).clone())
             else:
                 got[k] = (res, srv.fields_of(res, r["F"], r["n"]).clone())
+            torch.cuda.current_stream().synchronize()  # the copy is done before the memory is reused
             srv.release(res["id"])
     stats = srv.stats()
     srv.close()
