@@ -26,6 +26,12 @@ namespace {
 
 /* Section 4 / Section 4.2: one block = one warp of 32 threads x 32 points. */
 const uint32_t BLOCK = 1024;
+/* Reading of the paper: the block size B is recorded in the stream header,
+ * and the sweep of Section 4.2's trade-off (smaller blocks, more per-block
+ * overhead; larger blocks, more values per sort) takes B from {256, 512,
+ * 1024, 2048}; 1024 is the paper's and the default. */
+const uint32_t MAX_BLOCK = 2048;
+bool valid_block_size(uint32_t B) { return B == 256 || B == 512 || B == 1024 || B == 2048; }
 const uint32_t STREAM_MAGIC = 0x315A5047u; /* bytes 'G','P','Z','1' */
 const uint32_t STREAM_VERSION = 1;
 const uint32_t STREAM_HEADER_WORDS = 16;
@@ -341,7 +347,7 @@ std::vector<uint32_t> encode_block(const float* const* fields, int F, int n_b, i
 /* Decode one encoded or raw block into out[f][0..n_b).  Returns false on a
  * malformed block. */
 bool decode_block(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, const float* s,
-                  float* const* out) {
+                  float* const* out, uint32_t B = BLOCK) {
     if (nwords < 1) return false;
     if (w[0] & 1u) {
         if (w[0] != 1u || nwords != 1 + (uint32_t)F * (uint32_t)n_b) return false;
@@ -376,10 +382,10 @@ bool decode_block(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, con
         W += f < P ? o[f] : bits[f];
     }
     if (U < 1 || U > (uint32_t)n_b || U > (1u << key_bits)) return false;
-    /* The deltas are at most 2^key_bits - 1 and the counts at most BLOCK
-       (Section 4.3), so a width above key_bits or bit_width(BLOCK) is never
+    /* The deltas are at most 2^key_bits - 1 and the counts at most B
+       (Section 4.3), so a width above key_bits or bit_width(B) is never
        written. */
-    if (w_delta > key_bits || w_count > bit_width(BLOCK)) return false;
+    if (w_delta > key_bits || w_count > bit_width(B)) return false;
     const uint32_t d_len = ceil_div((uint64_t)U * w_delta, 32);
     const uint32_t c_len = ceil_div((uint64_t)U * w_count, 32);
     const uint32_t r_len = ceil_div((uint64_t)n_b * W, 32);
@@ -429,7 +435,7 @@ bool decode_block(const uint32_t* w, uint32_t nwords, int F, int n_b, int G, con
     return true;
 }
 
-uint64_t n_blocks_of(uint64_t n) { return (n + BLOCK - 1) / BLOCK; }
+uint64_t n_blocks_of(uint64_t n, uint32_t B = BLOCK) { return (n + B - 1) / B; }
 
 bool valid_shape(int F, int G) { return F >= 1 && F <= MAX_FIELDS && G >= 0 && G <= MAX_SEG_BITS; }
 
@@ -471,16 +477,18 @@ int gpzo_params_rel(double rel, const float* x, uint64_t n, gpzo_field_params* o
     return GPZO_OK;
 }
 
-uint64_t gpzo_bound_size(uint64_t n, int F) {
-    if (F < 1 || F > MAX_FIELDS) return 0;
-    uint64_t nb = n_blocks_of(n);
+uint64_t gpzo_bound_size_b(uint64_t n, int F, uint32_t B) {
+    if (F < 1 || F > MAX_FIELDS || !valid_block_size(B)) return 0;
+    uint64_t nb = n_blocks_of(n, B);
     return 4ull * (STREAM_HEADER_WORDS + 2ull * F + (nb + 1) + nb + (uint64_t)F * n);
 }
+
+uint64_t gpzo_bound_size(uint64_t n, int F) { return gpzo_bound_size_b(n, F, BLOCK); }
 
 int gpzo_encode_block(const float* const* fields, int F, int n_b, int G,
                       const gpzo_field_params* params, uint32_t* out, uint32_t cap_words,
                       uint32_t* nwords, uint32_t* perm_b) {
-    if (!fields || !params || !out || !nwords || !valid_shape(F, G) || n_b < 1 || n_b > (int)BLOCK)
+    if (!fields || !params || !out || !nwords || !valid_shape(F, G) || n_b < 1 || n_b > (int)MAX_BLOCK)
         return GPZO_ERR_INVALID_ARG;
     std::vector<uint32_t> perm;
     std::vector<uint32_t> words = encode_block(fields, F, n_b, G, params, perm_b ? &perm : nullptr);
@@ -495,7 +503,7 @@ int gpzo_block_stages(const float* const* fields, int F, int n_b, int G,
                       const gpzo_field_params* params, int* is_raw, float* mins, uint32_t* bits,
                       uint32_t* q, uint32_t* seg_id, uint32_t* seg_off, uint32_t* key,
                       uint32_t* perm_b, uint32_t* n_unique, uint32_t* uniq, uint32_t* counts) {
-    if (!fields || !params || !valid_shape(F, G) || n_b < 1 || n_b > (int)BLOCK)
+    if (!fields || !params || !valid_shape(F, G) || n_b < 1 || n_b > (int)MAX_BLOCK)
         return GPZO_ERR_INVALID_ARG;
     BlockStages st;
     compute_stages(fields, F, n_b, G, params, &st);
@@ -528,21 +536,28 @@ void gpzo_unpack_fixed(const uint32_t* words, uint32_t len, uint32_t w, uint32_t
 
 int gpzo_decode_block(const uint32_t* words, uint32_t nwords, int F, int n_b, int G, const float* s,
                       float* const* out) {
-    if (!words || !s || !out || !valid_shape(F, G) || n_b < 1 || n_b > (int)BLOCK)
+    if (!words || !s || !out || !valid_shape(F, G) || n_b < 1 || n_b > (int)MAX_BLOCK)
         return GPZO_ERR_INVALID_ARG;
-    return decode_block(words, nwords, F, n_b, G, s, out) ? GPZO_OK : GPZO_ERR_CORRUPT;
+    /* the block size of a stream holding a block of n_b particles: 1024, or 2048 above it */
+    const uint32_t B = n_b <= (int)BLOCK ? BLOCK : MAX_BLOCK;
+    return decode_block(words, nwords, F, n_b, G, s, out, B) ? GPZO_OK : GPZO_ERR_CORRUPT;
 }
 
 int gpzo_compress(const float* const* fields, uint64_t n, int F, int mode, const double* eb,
                   int G, uint8_t* out, uint64_t cap, uint64_t* out_size, uint32_t* perm) {
-    if (!valid_shape(F, G) || (mode != 0 && mode != 1) || !eb || !out || !out_size)
+    return gpzo_compress_b(fields, n, F, mode, eb, G, BLOCK, out, cap, out_size, perm);
+}
+
+int gpzo_compress_b(const float* const* fields, uint64_t n, int F, int mode, const double* eb,
+                    int G, uint32_t B, uint8_t* out, uint64_t cap, uint64_t* out_size, uint32_t* perm) {
+    if (!valid_shape(F, G) || !valid_block_size(B) || (mode != 0 && mode != 1) || !eb || !out || !out_size)
         return GPZO_ERR_INVALID_ARG;
     if (n > 0 && !fields) return GPZO_ERR_INVALID_ARG;
     for (int f = 0; f < F && n > 0; ++f)
         if (!fields[f]) return GPZO_ERR_INVALID_ARG;
-    const uint64_t nb = n_blocks_of(n);
+    const uint64_t nb = n_blocks_of(n, B);
     if (nb + (uint64_t)F * n > 0xFFFFFFFFull) return GPZO_ERR_UNSUPPORTED;
-    if (cap < gpzo_bound_size(n, F)) return GPZO_ERR_CAPACITY;
+    if (cap < gpzo_bound_size_b(n, F, B)) return GPZO_ERR_CAPACITY;
 
     std::vector<gpzo_field_params> params(F);
     for (int f = 0; f < F; ++f) {
@@ -556,8 +571,8 @@ int gpzo_compress(const float* const* fields, uint64_t n, int F, int mode, const
     std::vector<uint32_t> sizes(nb);
     std::vector<const float*> block_fields(F);
     for (uint64_t b = 0; b < nb; ++b) {
-        const uint64_t first = b * BLOCK;
-        const int n_b = (int)std::min<uint64_t>(BLOCK, n - first);
+        const uint64_t first = b * B;
+        const int n_b = (int)std::min<uint64_t>(B, n - first);
         for (int f = 0; f < F; ++f) block_fields[f] = fields[f] + first;
         std::vector<uint32_t> perm_b;
         temp[b] = encode_block(block_fields.data(), F, n_b, G, params.data(), perm ? &perm_b : nullptr);
@@ -576,7 +591,7 @@ int gpzo_compress(const float* const* fields, uint64_t n, int F, int mode, const
     words.push_back(STREAM_VERSION);
     words.push_back((uint32_t)F);
     words.push_back((uint32_t)G);
-    words.push_back(BLOCK);
+    words.push_back(B);
     words.push_back((uint32_t)mode);
     words.push_back((uint32_t)(n & 0xFFFFFFFFull));
     words.push_back((uint32_t)(n >> 32));
@@ -646,15 +661,22 @@ int gpzo_compress_f64(const double* const* fields, uint64_t n, int F, int mode, 
 }
 
 int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int F, uint64_t n) {
+    return gpzo_decompress_b(in, in_size, out, F, n, 0);
+}
+
+int gpzo_decompress_b(const uint8_t* in, uint64_t in_size, float* const* out, int F, uint64_t n,
+                      int any_block_size) {
     if (!in || F < 1 || F > MAX_FIELDS || (n > 0 && !out)) return GPZO_ERR_INVALID_ARG;
     if (in_size % 4 != 0 || in_size < 4ull * STREAM_HEADER_WORDS) return GPZO_ERR_CORRUPT;
     const uint64_t total_words = in_size / 4;
     std::vector<uint32_t> w(total_words);
     std::memcpy(w.data(), in, in_size);
-    const uint64_t nb = n_blocks_of(n);
+    const uint32_t B = w[4];
+    if (any_block_size ? !valid_block_size(B) : B != BLOCK) return GPZO_ERR_CORRUPT;
+    const uint64_t nb = n_blocks_of(n, B);
     const uint64_t stream_n = (uint64_t)w[6] | ((uint64_t)w[7] << 32);
     if (w[0] != STREAM_MAGIC || w[1] != STREAM_VERSION || w[2] != (uint32_t)F ||
-        w[3] > (uint32_t)MAX_SEG_BITS || w[4] != BLOCK || w[5] > 1 || stream_n != n || w[8] != nb)
+        w[3] > (uint32_t)MAX_SEG_BITS || w[5] > 1 || stream_n != n || w[8] != nb)
         return GPZO_ERR_CORRUPT;
     for (uint32_t k = 10; k < STREAM_HEADER_WORDS; ++k)
         if (w[k] != 0) return GPZO_ERR_CORRUPT;
@@ -670,11 +692,11 @@ int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int 
     std::vector<float*> block_out(F);
     for (uint64_t b = 0; b < nb; ++b) {
         if (offsets[b + 1] < offsets[b]) return GPZO_ERR_CORRUPT;
-        const uint64_t first = b * BLOCK;
-        const int n_b = (int)std::min<uint64_t>(BLOCK, n - first);
+        const uint64_t first = b * B;
+        const int n_b = (int)std::min<uint64_t>(B, n - first);
         for (int f = 0; f < F; ++f) block_out[f] = out[f] + first;
         if (!decode_block(w.data() + payload + offsets[b], offsets[b + 1] - offsets[b], F, n_b, G,
-                          s.data(), block_out.data()))
+                          s.data(), block_out.data(), B))
             return GPZO_ERR_CORRUPT;
     }
     return GPZO_OK;

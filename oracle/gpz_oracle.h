@@ -47,10 +47,12 @@ int gpzo_params_abs(double eb, gpzo_field_params* out);
 /* Relative bound: eb = rel * (max - min) over the non-NaN values of x[0..n). */
 int gpzo_params_rel(double rel, const float* x, uint64_t n, gpzo_field_params* out);
 
-/* Worst-case stream size in bytes for n particles of n_fields fields. */
+/* Worst-case stream size in bytes for n particles of n_fields fields
+ * (block size 1024; _b: block size B in {256, 512, 1024, 2048}, else 0). */
 uint64_t gpzo_bound_size(uint64_t n, int n_fields);
+uint64_t gpzo_bound_size_b(uint64_t n, int n_fields, uint32_t block_size);
 
-/* Encode one block of n_b (1..1024) particles.  fields[f] points at the
+/* Encode one block of n_b (1..2048) particles.  fields[f] points at the
  * block's n_b values of field f.  Writes the block's words to out
  * (capacity cap_words), their count to *nwords, and, if perm_b is not NULL,
  * the block-local permutation (perm_b[j] = input index of output slot j). */
@@ -88,6 +90,14 @@ int gpzo_compress(const float* const* fields, uint64_t n, int n_fields, int mode
                   const double* eb, int seg_bits, uint8_t* out, uint64_t cap,
                   uint64_t* out_size, uint32_t* perm);
 
+/* The same with particles grouped in blocks of block_size in {256, 512,
+ * 1024, 2048} (Section 4.2 fixes 1024: 32 threads x 32 points); the header
+ * records the block size, and gpzo_decompress takes it from there.  Used to
+ * sweep the block size; the GPU library writes 1024 only. */
+int gpzo_compress_b(const float* const* fields, uint64_t n, int n_fields, int mode,
+                    const double* eb, int seg_bits, uint32_t block_size, uint8_t* out,
+                    uint64_t cap, uint64_t* out_size, uint32_t* perm);
+
 /* fp64 input (Section 5.1: fp64 input is lowered to fp32 when that is enough
  * for the bound; the test used here is the following): each
  * value is rounded to fp32 (round to nearest), and the fp32 values are
@@ -108,6 +118,12 @@ int gpzo_compress_f64(const double* const* fields, uint64_t n, int n_fields, int
 /* Inverse.  Writes n values per field, in the stream's (block-sorted) order. */
 int gpzo_decompress(const uint8_t* in, uint64_t in_size, float* const* out, int n_fields,
                     uint64_t n);
+
+/* The same, accepting a stream of any block size gpzo_compress_b writes when
+ * any_block_size is nonzero (gpzo_decompress, like the GPU library, takes
+ * block size 1024 only: a header with another is a corrupt stream). */
+int gpzo_decompress_b(const uint8_t* in, uint64_t in_size, float* const* out, int n_fields, uint64_t n,
+                      int any_block_size);
 
 /* 64-bit intermediates (Section 5.2: 32-bit intermediates unless the value
  * range or the precision needs 64-bit ones).  fp64 values are quantised in

@@ -36,6 +36,8 @@ def lib():
         L.gpzo_params_rel.argtypes = [C.c_double, f32p, C.c_uint64, P(FieldParams)]
         L.gpzo_bound_size.argtypes = [C.c_uint64, C.c_int]
         L.gpzo_bound_size.restype = C.c_uint64
+        L.gpzo_bound_size_b.argtypes = [C.c_uint64, C.c_int, C.c_uint32]
+        L.gpzo_bound_size_b.restype = C.c_uint64
         L.gpzo_encode_block.argtypes = [P(f32p), C.c_int, C.c_int, C.c_int, P(FieldParams), u32p,
                                         C.c_uint32, u32p, u32p]
         L.gpzo_decode_block.argtypes = [u32p, C.c_uint32, C.c_int, C.c_int, C.c_int, f32p, P(f32p)]
@@ -47,7 +49,10 @@ def lib():
         L.gpzo_unpack_fixed.argtypes = [u32p, C.c_uint32, C.c_uint32, u32p]
         L.gpzo_compress.argtypes = [P(f32p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
                                     u8p, C.c_uint64, P(C.c_uint64), u32p]
+        L.gpzo_compress_b.argtypes = [P(f32p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
+                                      C.c_uint32, u8p, C.c_uint64, P(C.c_uint64), u32p]
         L.gpzo_decompress.argtypes = [u8p, C.c_uint64, P(f32p), C.c_int, C.c_uint64]
+        L.gpzo_decompress_b.argtypes = [u8p, C.c_uint64, P(f32p), C.c_int, C.c_uint64, C.c_int]
         L.gpzo_compress_f64.argtypes = [P(C.c_void_p), C.c_uint64, C.c_int, C.c_int, P(C.c_double), C.c_int,
                                         u8p, C.c_uint64, P(C.c_uint64), u32p, P(C.c_double)]
         dp = P(C.c_double)
@@ -98,8 +103,8 @@ def params_rel(rel, x):
     return p
 
 
-def bound_size(n, n_fields):
-    return int(lib().gpzo_bound_size(n, n_fields))
+def bound_size(n, n_fields, block=1024):
+    return int(lib().gpzo_bound_size_b(n, n_fields, block))
 
 
 def _params_array(params):
@@ -180,18 +185,19 @@ def unpack_fixed(words, length, w):
     return out
 
 
-def compress(fields, eb, mode=0, seg_bits=3, want_perm=True):
-    """Compress [F, n] float32 -> (stream bytes as np.uint8, perm or None)."""
+def compress(fields, eb, mode=0, seg_bits=3, want_perm=True, block=1024):
+    """Compress [F, n] float32 -> (stream bytes as np.uint8, perm or None);
+    block: the block size (256, 512, 1024 -- the paper's -- or 2048)."""
     x = _as_fields(fields)
     F, n = x.shape
     ebs = np.ascontiguousarray(np.broadcast_to(np.asarray(eb, dtype=np.float64), (F,)))
-    cap = bound_size(n, F)
+    cap = bound_size(n, F, block)
     out = np.zeros(max(cap, 4), dtype=np.uint8)
     size = C.c_uint64(0)
     perm = np.zeros(n, dtype=np.uint32) if want_perm else None
-    rc = lib().gpzo_compress(_field_ptrs(x), n, F, mode, _ptr(ebs, C.c_double), seg_bits,
-                             _ptr(out, C.c_uint8), cap, C.byref(size),
-                             _ptr(perm, C.c_uint32) if want_perm else None)
+    rc = lib().gpzo_compress_b(_field_ptrs(x), n, F, mode, _ptr(ebs, C.c_double), seg_bits, block,
+                               _ptr(out, C.c_uint8), cap, C.byref(size),
+                               _ptr(perm, C.c_uint32) if want_perm else None)
     if rc != OK:
         raise RuntimeError("gpzo_compress failed: %d" % rc)
     return out[:size.value].copy(), perm
@@ -245,11 +251,12 @@ def compress_f64_status(fields, eb, mode=0, seg_bits=3):
                                    C.byref(size), None, None)
 
 
-def decompress(stream, n_fields, n):
-    """Stream bytes -> [F, n] float32 in block-sorted order."""
+def decompress(stream, n_fields, n, any_block=False):
+    """Stream bytes -> [F, n] float32 in block-sorted order (any_block: also
+    streams of a block size other than 1024, which gpzo_compress_b writes)."""
     s = np.ascontiguousarray(stream, dtype=np.uint8)
     out = np.zeros((n_fields, n), dtype=np.float32)
-    rc = lib().gpzo_decompress(_ptr(s, C.c_uint8), s.size, _field_ptrs(out), n_fields, n)
+    rc = lib().gpzo_decompress_b(_ptr(s, C.c_uint8), s.size, _field_ptrs(out), n_fields, n, 1 if any_block else 0)
     if rc != OK:
         raise RuntimeError("gpzo_decompress failed: %d" % rc)
     return out
