@@ -123,6 +123,9 @@ uint64_t gpz_decompress_workspace_size(void);
  *   d_ws/ws_size: workspace (256-byte aligned) of at least
  *                 gpz_compress_workspace_size(n, F) bytes, or NULL to let the
  *                 library allocate and free it (the call then synchronises).
+ *                 Such workspaces come from the library's stream-ordered
+ *                 pool on the current device, which keeps the freed memory
+ *                 for later calls (see gpz_release_pooled_memory).
  * The stream is identical for every launch configuration and device. */
 gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_params* p,
                         void* d_out, uint64_t out_capacity, uint64_t* d_out_size,
@@ -180,8 +183,8 @@ gpz_status gpz_noalloc_sync_status(void* stream);
  *                 fp32 values in the stream's block-sorted order.
  *   n_fields, n:  must match the stream header, else GPZ_ERR_CORRUPT.
  *   d_ws/ws_size: workspace of gpz_decompress_workspace_size() bytes, or
- *                 NULL (the call then allocates, synchronises and returns the
- *                 device-side status).
+ *                 NULL (the call then allocates from the library's pool,
+ *                 synchronises and returns the device-side status).
  * A stream that fails a format check sets GPZ_ERR_CORRUPT in the workspace
  * status; the kernels never read outside [d_in, d_in + in_size) and never
  * write outside the n values of each output field. */
@@ -325,6 +328,19 @@ int gpz_stage_times(const char** names, float* total_ms, int* launches, int max)
 
 /* Kernel launches enqueued by this process since the last reset. */
 uint64_t gpz_launch_count(int reset);
+
+/* The library's workspace pool (the paper has no counterpart).  Calls given
+ * no workspace (gpz_compress, gpz_decompress, gpz_compress_aos, ... with
+ * d_ws = NULL) allocate it, stream-ordered, from a memory pool that the
+ * library creates on the current device at the first such call.  The pool
+ * keeps memory that calls have freed, so that later calls map no new pages;
+ * it holds at most what the calls running at the same time needed.
+ * gpz_pooled_bytes returns the bytes the current device's pool holds (0
+ * before its first use).  gpz_release_pooled_memory synchronises the current
+ * device and returns the pool's unused memory to the driver: GPZ_OK, or
+ * GPZ_ERR_CUDA. */
+uint64_t gpz_pooled_bytes(void);
+gpz_status gpz_release_pooled_memory(void);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,47 @@ namespace gpz {
 namespace host {
 StageTimer g_timer;
 std::atomic<uint64_t> g_launches{0};
+
+// The library's workspace pools, one per device, created at first use.  The
+// release threshold keeps freed memory in the pool, so that a call after the
+// first maps no new pages; gpz_release_pooled_memory hands it back.
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t pool_of_current(cudaMemPool_t* out, bool create) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (!g_pools[dev] && create) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = pool_of_current(&pool, true);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
 }  // namespace host
 }  // namespace gpz
 
@@ -419,6 +460,22 @@ gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fi
         if (rc == GPZ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = GPZ_ERR_CUDA;
     }
     return rc;
+}
+
+uint64_t gpz_pooled_bytes(void) {
+    cudaMemPool_t pool = nullptr;
+    if (gpz::host::pool_of_current(&pool, false) != cudaSuccess || !pool) return 0;
+    uint64_t v = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) != cudaSuccess) return 0;
+    return v;
+}
+
+gpz_status gpz_release_pooled_memory(void) {
+    cudaMemPool_t pool = nullptr;
+    if (gpz::host::pool_of_current(&pool, false) != cudaSuccess) return GPZ_ERR_CUDA;
+    if (!pool) return GPZ_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GPZ_ERR_CUDA;
+    return cuda_status(cudaMemPoolTrimTo(pool, 0));
 }
 
 }  // extern "C"

@@ -103,9 +103,13 @@ inline bool injected_alloc_failure() {
         if (g_fail_allocs.compare_exchange_weak(k, k - 1)) return true;
     return false;
 }
+// Workspaces of calls given none come from the library's own stream-ordered
+// pool on the current device (gpz_api.cu), which keeps freed memory for the
+// next call instead of returning it to the driver at every synchronisation.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
 inline cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
     if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
-    return cudaMallocAsync(p, bytes, s);
+    return pool_malloc_async(p, bytes, s);
 }
 inline cudaError_t dev_malloc(void** p, size_t bytes) {
     if (injected_alloc_failure()) return cudaErrorMemoryAllocation;

@@ -9,8 +9,10 @@
 //     bulk copy per field, completing on an mbarrier (the few values of a
 //     ragged last block beyond a multiple of four are loaded by plain loads);
 //   - threads 0..F-1 derive their field's constants (minimum, code width,
-//     segment split, record offset) once, into shared memory, from the block
-//     extremes of the range pass (relative bound) or from the tile;
+//     segment split, record offset) once, into shared memory: with a
+//     relative bound from the block extremes of the range pass, loaded with
+//     the field's step constants in one round trip while the tile is in
+//     flight; otherwise from the tile;
 //   - each thread quantises its 4 particles of every field from the tile;
 //   - once every value is quantised the tile is dead, and the encoded
 //     block's staging words are assembled in the same bytes, then written to
@@ -49,7 +51,7 @@ struct TileField {
 
 struct TileShared {
     uint64_t bar;                       // mbarrier of the tile's bulk copies
-    uint32_t kmin[kMaxFields], kmax[kMaxFields];
+    uint32_t kmin[kMaxFields], kmax[kMaxFields];  // the block's extremes (absolute bound)
     TileField fc[kMaxFields];
     // bit 0: a non-finite value; bit 1: a value needs a fallback candidate;
     // bit 2: a code reaches 2^23 (general path); bit 3: some field's first
@@ -71,6 +73,32 @@ __device__ __forceinline__ FieldParams field_params(const QseArgs& a, int f) {
     for (int k = 1; k < F; ++k)
         if (k == f) p = a.params[k];
     return p;
+}
+
+// Field t's constants for the block from its extremes (order keys), by
+// thread t: q0 = floor(fma(x - min, 1/s, 1/2)) is monotone in x, so when
+// every value keeps its first candidate the largest code is q0 of the block
+// maximum.  P is the number of position fields.
+template <int P>
+__device__ __forceinline__ void field_constants(uint32_t kmin, uint32_t kmax, const FieldParams& p, int G, int t,
+                                                TileShared& S) {
+    uint32_t bits;
+    bool big, exact;
+    block_field_width(kmin, kmax, p, bits, big, exact);
+    const float m0 = from_order_key(kmin);
+    TileField c;
+    c.mn = m0 == 0.0f ? 0.0f : m0;  // a zero minimum is stored as +0
+    c.inv = p.inv;
+    c.s = p.s;
+    c.ebchk = p.ebchk;
+    c.bits = bits;
+    const uint32_t g = t < P ? min((uint32_t)G, bits) : 0u;
+    c.o = t < P ? bits - g : 0u;
+    c.wf = t < P ? c.o : bits;
+    c.ks = g;  // this field's segId bits for now; the key shifts follow in every thread
+    S.fc[t] = c;
+    if (big) atomicOr(&S.flags, kTfBig);
+    if (!exact) atomicOr(&S.flags, kTfVerify);
 }
 
 }  // namespace
@@ -111,11 +139,15 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
 #pragma unroll
         for (int k = 0; k < kMaxBins / 64; ++k) h32[lane + 32 * k] = 0u;
     }
+    __syncwarp();  // S.flags cleared (thread 0) before threads 0..F-1 of warp 0 set bits in it
     if (t < F) {
         if (PRE) {  // from the range pass; (0, 0) marks a non-finite value
             const uint2 e = __ldg(a.bext + (size_t)b * F + t);
-            S.kmin[t] = e.x;
-            S.kmax[t] = e.y;
+            const FieldParams p = a.d_params[t];  // loaded with the extremes: one round trip
+            if (e.x == 0u)
+                atomicOr(&S.flags, kTfNonFinite);
+            else
+                field_constants<P>(e.x, e.y, p, a.G, t, S);
         } else {
             S.kmin[t] = 0xffffffffu;
             S.kmax[t] = 0u;
@@ -152,32 +184,11 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
         __syncthreads();  // 1b: the extremes
     }
 
-    // ---- 2. field constants (thread f): q0 = floor(fma(x - min, 1/s, 1/2))
-    // is monotone in x, so when every value keeps its first candidate the
-    // largest code is q0 of the block maximum
-    if (t < F && PRE && S.kmin[t] == 0u) {
-        atomicOr(&S.flags, kTfNonFinite);
-    } else if (t < F && !(S.flags & kTfNonFinite)) {
-        const FieldParams p = field_params<F>(a, t);
-        uint32_t bits;
-        bool big, exact;
-        block_field_width(S.kmin[t], S.kmax[t], p, bits, big, exact);
-        const float m0 = from_order_key(S.kmin[t]);
-        TileField c;
-        c.mn = m0 == 0.0f ? 0.0f : m0;  // a zero minimum is stored as +0
-        c.inv = p.inv;
-        c.s = p.s;
-        c.ebchk = p.ebchk;
-        c.bits = bits;
-        const uint32_t g = t < P ? min((uint32_t)a.G, bits) : 0u;
-        c.o = t < P ? bits - g : 0u;
-        c.wf = t < P ? c.o : bits;
-        c.ks = g;  // this field's segId bits for now; the key shifts follow below
-        S.fc[t] = c;
-        if (big) atomicOr(&S.flags, kTfBig);
-        if (!exact) atomicOr(&S.flags, kTfVerify);
-    }
-    __syncthreads();  // 2: the field constants
+    // ---- 2. field constants (thread f) from the tile's extremes
+    // (with a relative bound this was done before barrier 1)
+    if (t < F && !PRE && !(S.flags & kTfNonFinite))
+        field_constants<P>(S.kmin[t], S.kmax[t], field_params<F>(a, t), a.G, t, S);
+    if constexpr (!PRE) __syncthreads();  // 2: the field constants
     uint32_t flags = S.flags;
     if (flags & kTfNonFinite) {
         if (PRE && !mbar_wait_bounded(&S.bar, 0, a.status)) return;  // no copy may outlive the CTA

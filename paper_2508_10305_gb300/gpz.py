@@ -128,6 +128,10 @@ def _load():
     L.gpz_stage_times.restype = C.c_int
     L.gpz_launch_count.argtypes = [C.c_int]
     L.gpz_launch_count.restype = u64
+    L.gpz_pooled_bytes.argtypes = []
+    L.gpz_pooled_bytes.restype = u64
+    L.gpz_release_pooled_memory.argtypes = []
+    L.gpz_release_pooled_memory.restype = C.c_int
     # failure-injection hooks (include/gpz_test.h)
     L.gpz_test_fail_next_allocations.argtypes = [C.c_int]
     L.gpz_test_fail_next_allocations.restype = C.c_int
@@ -345,6 +349,16 @@ def gpz_stage_times(max_stages=8):
 
 def gpz_launch_count(reset=False):
     return int(lib.gpz_launch_count(1 if reset else 0))
+
+
+def gpz_pooled_bytes():
+    """Bytes held by the library's workspace pool on the current device."""
+    return int(lib.gpz_pooled_bytes())
+
+
+def gpz_release_pooled_memory():
+    """Synchronise the current device and return the pool's unused memory."""
+    return int(lib.gpz_release_pooled_memory())
 
 
 def gpz_test_fail_next_allocations(count):
