@@ -23,6 +23,11 @@
 // kernel is latency-bound (instruction issue waits on shared memory, warp
 // collectives and barriers), so residency is what pays.
 //
+// With a relative bound the block's extremes come from the range pass and
+// must bound the block's values (they are exact there): codes are monotone in
+// the value, so every code then fits the width derived from the maximum, and
+// every key stays below 2^keybits, which the histogram's indexing relies on.
+//
 // Blocks the fast path cannot take (a value needing a fallback candidate, a
 // code >= 2^23, a record > 128 bits) go to the general kernel's list; blocks
 // with a non-finite value or no gain are stored raw -- both exactly as in
