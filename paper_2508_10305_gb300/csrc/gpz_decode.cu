@@ -3,8 +3,10 @@
 //
 // One CTA of 256 threads per 1024-particle block; thread t rebuilds sorted
 // positions 4t..4t+3.  Per CTA:
-//   1. warp 0 checks the stream header, the block's table entries and the
-//      block header;
+//   1. the block's table entries (one round trip), then its words after the
+//      block header by one bulk copy into shared memory (an mbarrier with a
+//      bounded wait), while warp 0 checks the stream header, the table
+//      entries and the block header;
 //   2. raw block: copy the stored values;
 //   3. encoded block: every thread extracts two deltas and two counts
 //      (fixed-length, one funnel shift each); a CTA-wide prefix sum gives

@@ -150,7 +150,10 @@ struct DecCore {  // everything a block's decoding keeps in shared memory but it
 };
 
 struct DecShared : DecCore {
-    alignas(16) uint32_t stage[kDecStageWords + kDecStagePad];  // the block's words after its header
+    uint64_t bar;  // the staging bulk copy
+    // the block's words after its header, from word `shift` (the source's
+    // offset from a 16-byte boundary, 0..3)
+    alignas(16) uint32_t stage[kDecStageWords + kDecStagePad + 4];
 };
 
 // Codes of fields F-1 .. 0 of four records, consumed from the least
@@ -458,9 +461,11 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
     const uint32_t* blk = Sw + payload_start + off;
     const uint32_t nw = end - off;
     // round trip 2: warp 0 fetches the stream header, the block header and the
-    // steps (all in bounds once the block is inside the stream), and every
-    // warp stages the block's words after its header in shared memory (all of
-    // them when they fit; the deltas and counts always fit)
+    // steps (all in bounds once the block is inside the stream), and the
+    // block's words after its header are staged in shared memory (all of them
+    // when they fit; the deltas and counts always fit) by one bulk copy that
+    // thread 0 issues, its last few words by plain loads where the copy's
+    // 16-byte units would reach past the stream
     uint32_t hv = 0, bw = 0;
     float step = 0.0f;
     if (w == 0) {
@@ -468,14 +473,29 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
         if (inside && (uint32_t)lane < min(hdr, nw)) bw = __ldg(blk + lane);
         if (header_fits && lane < F) step = __uint_as_float(__ldg(Sw + kHeaderWords + 2 * lane + 1));
     }
+    // the copy: 16-byte units from the boundary at or below the first word,
+    // as many as end inside the stream; the words after them by plain loads
+    const uint32_t* src = blk + hdr;
+    const uint32_t shift = (uint32_t)((reinterpret_cast<uintptr_t>(src) >> 2) & 3u);
+    uint32_t nst = 0, units = 0;
     if (inside && nw > hdr) {
-        const uint32_t nst = min(nw - hdr, kDecStageWords);
-        for (uint32_t k = t; k < nst; k += kDecThreads) stage[k] = __ldg(blk + hdr + k);
+        nst = min(nw - hdr, kDecStageWords);
+        const uint64_t avail = a.total_words - (uint64_t)(src - Sw) + shift;  // words from the boundary to the stream's end
+        units = (uint32_t)(min((uint64_t)(nst + shift + 3u), avail) >> 2);
+        if (units * 4u < shift) units = 0;
     }
+    if (units && t == 0) {
+        mbar_init(&S.bar, 1);
+        mbar_arrive_expect_tx(&S.bar, units * 16u);
+        bulk_g2s(S.stage, src - shift, units * 16u, &S.bar);
+    }
+    const uint32_t kb = units ? units * 4u - shift : 0u;  // first word not in the copy
+    for (uint32_t k = kb + t; k < nst; k += kDecThreads) stage[shift + k] = __ldg(src + k);
 
     if (w == 0) decode_checks<F>(a, S, hv, bw, step, inside, b, off, end, payload_words, n_b);
     __syncthreads();
-    decode_tail<F, OUT64>(a, S, stage, blk, b, n_b);
+    if (units && !__syncthreads_and(mbar_wait_bounded(&S.bar, 0, a.status))) return;  // uniform
+    decode_tail<F, OUT64>(a, S, stage + shift, blk, b, n_b);
 }
 
 }  // namespace gpz
