@@ -58,6 +58,7 @@ struct BatchCompressArgs {
     uint2* bext;                 // [all blocks][kMaxFields]: each block's extremes from the range items
                                  // (a chunk's blocks from block_base * kMaxFields, b * F + f), or nullptr
     int pre;                     // the group's blocks read their extremes from bext (relative bounds)
+    int tile;                    // every chunk's fields 16-byte aligned: the shared-memory tile kernel
     uint32_t* temp;
     uint32_t* sizes;             // [all blocks] words per block
     uint32_t* general_list;      // [the group's blocks] global block ids left to the general kernel

@@ -7,6 +7,7 @@
 // chunk's stream is the one a call of its own produces.
 #include "gpz_batch.cuh"
 #include "gpz_qse_block.cuh"
+#include "gpz_qse_tile.cuh"
 
 namespace gpz {
 
@@ -171,6 +172,24 @@ __global__ void __launch_bounds__(kThreads, 5) gpz_batch_compress_kernel(BatchCo
         qse_block_fast<F, true, SlotBlock, kCmTemp, PRE>(A, dsm, S, idx);
     else
         qse_block_fast<F, false, SlotBlock, kCmTemp, PRE>(A, dsm, S, idx);
+}
+
+// The same with the shared-memory tile body (gpz_qse_tile.cuh): groups whose
+// chunks all have 16-byte aligned fields.
+template <int F, bool PRE>
+__global__ void __launch_bounds__(kThreads, 6) gpz_batch_tile_kernel(BatchCompressArgs g) {
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ __align__(8) TileShared S;
+    __shared__ QseArgs A;
+    __shared__ uint32_t slot[2];  // block within its chunk, global block id
+    const uint32_t gb = g.block_first + blockIdx.x;
+    load_chunk_args(g, __ldg(g.block_map + gb), gb, A, slot);
+    __syncthreads();
+    const SlotBlock idx{slot};
+    if ((uint64_t)(idx.b() + 1) * kBlock <= A.n)
+        qse_block_tile<F, true, PRE>(A, dsm, S, idx);
+    else
+        qse_block_tile<F, false, PRE>(A, dsm, S, idx);
 }
 
 // Blocks the fast path left to the general one (rare); the grid walks the
@@ -376,6 +395,14 @@ bool prepare_f() {
                                 (int)qse_fast_smem_bytes()) == cudaSuccess &&
            cudaFuncSetAttribute(gpz_batch_compress_kernel<F, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 100) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_tile_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem_bytes(F)) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_tile_kernel<F, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                100) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_tile_kernel<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem_bytes(F)) == cudaSuccess &&
+           cudaFuncSetAttribute(gpz_batch_tile_kernel<F, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                100) == cudaSuccess &&
            cudaFuncSetAttribute(gpz_batch_general_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)qse_smem_bytes(F)) == cudaSuccess;
 }
@@ -398,6 +425,10 @@ template <int F>
 void launch_f(const BatchCompressArgs& a, int grid, cudaStream_t s, bool general) {
     if (general)
         gpz_batch_general_kernel<F><<<grid, kThreads, qse_smem_bytes(F), s>>>(a);
+    else if (a.tile && a.pre)
+        gpz_batch_tile_kernel<F, true><<<grid, kThreads, tile_smem_bytes(F), s>>>(a);
+    else if (a.tile)
+        gpz_batch_tile_kernel<F, false><<<grid, kThreads, tile_smem_bytes(F), s>>>(a);
     else if (a.pre)
         gpz_batch_compress_kernel<F, true><<<grid, kThreads, qse_fast_smem_bytes(), s>>>(a);
     else

@@ -166,12 +166,14 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
             BatchGroup g{};
             g.F = ch.F;
             g.pre = pre;
+            g.bulk = 1;
             g.first = k;
             g.block_first = (uint32_t)blocks;
             c.groups.push_back(g);
         }
         BatchGroup& g = c.groups.back();
         ++g.count;
+        g.bulk = g.bulk && ch.bulk_ok;
         ch.block_base = (uint32_t)blocks;
         ch.temp_base = temp;
         blocks += ch.nblocks;
@@ -303,6 +305,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
         a.general_list = reinterpret_cast<uint32_t*>(ws + L.list) + g.block_first;
         a.general_count = ctrl + k;
         a.pre = g.pre && a.bext != nullptr;
+        a.tile = g.bulk;
         if (g.range_items > 0) {
             if (launch_batch_range(a, s) != cudaSuccess) return GPZ_ERR_CUDA;
             rec.mark("batch_range");

@@ -21,6 +21,7 @@ namespace host {
 struct BatchGroup {
     int F;
     int pre;                            // relative-bound chunks: block extremes from the range items
+    int bulk;                           // every chunk's fields 16-byte aligned: the tile kernel
     uint32_t first, count;              // plan positions of the group's chunks
     uint32_t range_first, range_items;  // the group's range items
     uint32_t block_first, blocks;       // the group's blocks
