@@ -9,6 +9,7 @@
 #include "gpz.h"
 #include "gpz_host.hpp"
 #include "gpz_internal.cuh"
+#include "gpz_qse_tile.cuh"
 
 using namespace gpz;
 using namespace gpz::host;
@@ -130,7 +131,8 @@ __device__ __forceinline__ float aos_from_order_key(uint32_t k) {
 // extremes over the non-NaN values; the last CTA folds the CTAs' partials
 // into the per-field constants.  The outputs are those of the range pass of
 // gpz_compress, in the same places of its workspace, so compression then
-// skips that pass and its read of the fields.
+// skips that pass and its read of the fields.  With soa == nullptr the
+// kernel is the range pass alone (compression then reads the records).
 template <int F>
 __global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float* __restrict__ aos,
                                                                     float* __restrict__ soa, uint64_t n,
@@ -190,7 +192,9 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float*
                 }
             }
         }
-        if (vec && cnt == kAosTile) {
+        if (!soa) {
+            // the range pass alone
+        } else if (vec && cnt == kAosTile) {
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 const float* row = tile + f * (kAosTile + 1);
@@ -239,6 +243,51 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float*
         }
         __syncthreads();
     }
+}
+
+// Compression straight from 16-byte aligned interleaved records: the tile
+// kernel's body with the block's records as its tile (one bulk copy of
+// 1024 F contiguous values), so no structure-of-arrays copy is made.
+template <int F, bool PRE>
+__global__ void __launch_bounds__(kThreads, 6) gpz_qse_tile_aos_kernel(QseArgs a) {
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ __align__(8) TileShared S;
+    if ((uint64_t)(blockIdx.x + 1) * kBlock <= a.n)
+        qse_block_tile<F, true, PRE, GridBlock, true>(a, dsm, S, GridBlock{});
+    else
+        qse_block_tile<F, false, PRE, GridBlock, true>(a, dsm, S, GridBlock{});
+}
+
+template <int F, bool PRE>
+cudaError_t launch_qse_tile_aos_fp(const QseArgs& a, cudaStream_t s) {
+    const size_t smem = tile_smem_bytes(F);
+    auto kern = gpz_qse_tile_aos_kernel<F, PRE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nblocks, kThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_qse_general(a, s);
+}
+
+cudaError_t launch_qse_tile_aos(const QseArgs& a, cudaStream_t s) {
+    if (a.nblocks == 0) return cudaSuccess;
+    const bool pre = a.bext != nullptr;
+    switch (a.F) {
+#define GPZ_CASE(FF) \
+    case FF: return pre ? launch_qse_tile_aos_fp<FF, true>(a, s) : launch_qse_tile_aos_fp<FF, false>(a, s);
+        GPZ_CASE(1)
+        GPZ_CASE(2)
+        GPZ_CASE(3)
+        GPZ_CASE(4)
+        GPZ_CASE(5)
+        GPZ_CASE(6)
+        GPZ_CASE(7)
+        GPZ_CASE(8)
+#undef GPZ_CASE
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int F>
@@ -347,11 +396,17 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
     const uint64_t ld = soa_ld(n);
     gpz_status rc = GPZ_OK;
     bool range_done = false;
+    // 16-byte aligned records go straight to the tile kernel (no
+    // structure-of-arrays copy); otherwise, or with fused compaction, they are
+    // transposed first
+    const bool direct = (reinterpret_cast<uintptr_t>(d_aos) & 15u) == 0 &&
+                        (p->flags & GPZ_FLAG_FUSED_COMPACTION) == 0u;
     if (n > 0) {
         Recorder rec(s);
         rec.begin(1);
         if (p->mode == GPZ_EB_REL) {
-            // the transpose also does the range pass, into the compression workspace
+            // the range pass over the records (with the transpose when there is
+            // one), into the compression workspace
             const RangeTargets rt = compress_range_targets(n, F);
             RangeArgs ra{};
             ra.n = n;
@@ -363,19 +418,21 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
             ra.bext = reinterpret_cast<uint2*>(ws + rt.bext);
             rc = cuda_status(cudaMemsetAsync(ws + rt.ctrl, 0, 64, s));
             const unsigned grid = transpose_grid(n);  // <= kRangeCtasMax CTAs: their partials fit
-            if (rc == GPZ_OK) rc = cuda_status(launch_transpose_range(d_aos, soa, n, F, ld, grid, ra, s));
+            if (rc == GPZ_OK)
+                rc = cuda_status(launch_transpose_range(d_aos, direct ? nullptr : soa, n, F, ld, grid, ra, s));
             range_done = rc == GPZ_OK;
-        } else {
+            if (rc == GPZ_OK) rec.mark(direct ? "aos_range" : "aos");
+        } else if (!direct) {
             rc = cuda_status(launch_transpose(true, d_aos, soa, n, F, ld, transpose_grid(n), s));
+            if (rc == GPZ_OK) rec.mark("aos");
         }
-        if (rc == GPZ_OK) rec.mark("aos");
     }
     if (rc == GPZ_OK) {
         const float* fields[kMaxFields];
-        for (int f = 0; f < F; ++f) fields[f] = soa + (uint64_t)f * ld;
+        for (int f = 0; f < F; ++f) fields[f] = direct ? d_aos + f : soa + (uint64_t)f * ld;
         // the compression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
         rc = compress_impl(fields, n, p, d_out, out_capacity, d_out_size, h_out_size, d_perm, ws, cws, stream,
-                           range_done);
+                           range_done, direct && n > 0 ? d_aos : nullptr);
     }
     if (own) {  // as gpz_compress without a workspace: synchronise and return the device-side status
         if (rc == GPZ_OK) {

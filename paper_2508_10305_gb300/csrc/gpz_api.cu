@@ -233,7 +233,8 @@ RangeTargets compress_range_targets(uint64_t n, int F) {
 // fields anyway, and are neither cleared nor recomputed.
 gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
                          uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
-                         void* d_ws, uint64_t ws_size, void* stream, bool range_done) {
+                         void* d_ws, uint64_t ws_size, void* stream, bool range_done,
+                         const float* interleaved) {
     if (!p || !d_out || !aligned(d_out, 4)) return GPZ_ERR_INVALID_ARG;
     const int F = p->n_fields;
     if (F < 1 || F > kMaxFields || p->seg_bits < 0 || p->seg_bits > kMaxSegBits ||
@@ -285,11 +286,16 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
             for (int f = 0; f < F; ++f) hp[f] = finalise(p->eb[f]);
         bool vec_ok = true;
         for (int f = 0; f < F && n > 0; ++f) vec_ok = vec_ok && aligned(d_fields[f], 16);
+        if (interleaved) vec_ok = aligned(interleaved, 16);
         const bool fused = (p->flags & GPZ_FLAG_FUSED_COMPACTION) != 0u;
         // the shared-memory tile kernel takes 16-byte aligned fields and derives
         // each block's widths itself; the register kernel reads them from the
         // block-info pass (relative bound)
         const bool tile = vec_ok && !fused;
+        if (interleaved && (!tile || (rel && !range_done))) {  // the caller's side of the contract
+            rc = GPZ_ERR_INVALID_ARG;
+            break;
+        }
 
         if (rel) {
             RangeArgs ra{};
@@ -329,6 +335,7 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
         qa.F = F;
         qa.G = p->seg_bits;
         qa.bulk_ok = vec_ok ? 1 : 0;
+        qa.interleaved = interleaved ? 1 : 0;
         qa.d_params = rel ? d_params : nullptr;
         qa.bext = rel ? reinterpret_cast<const uint2*>(ws + L.bext) : nullptr;
         qa.binfo = rel && !tile ? reinterpret_cast<const unsigned long long*>(ws + L.binfo) : nullptr;

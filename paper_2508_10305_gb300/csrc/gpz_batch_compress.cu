@@ -37,6 +37,7 @@ __device__ __forceinline__ void load_chunk_args(const BatchCompressArgs& g, uint
         A.F = ch->F;
         A.G = ch->G;
         A.bulk_ok = ch->bulk_ok;
+        A.interleaved = 0;
         A.d_params = nullptr;
         A.bext = g.pre ? g.bext + (size_t)ch->block_base * kMaxFields : nullptr;
         A.binfo = nullptr;  // the fused kernel derives the widths from the extremes

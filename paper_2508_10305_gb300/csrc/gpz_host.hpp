@@ -128,9 +128,13 @@ RangeTargets compress_range_targets(uint64_t n, int F);
 constexpr int kRangeCtasMax = 152 * 8;  // partials held for this many CTAs
 
 // gpz_compress, optionally with the range pass already done (gpz_api.cu).
+// With `interleaved` (16-byte aligned F-field records, d_fields[f] =
+// interleaved + f) the tile kernel reads the records themselves; a relative
+// bound then needs the range pass done.
 gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_params* p, void* d_out,
                          uint64_t out_capacity, uint64_t* d_out_size, uint64_t* h_out_size, uint32_t* d_perm,
-                         void* d_ws, uint64_t ws_size, void* stream, bool range_done);
+                         void* d_ws, uint64_t ws_size, void* stream, bool range_done,
+                         const float* interleaved = nullptr);
 
 }  // namespace host
 

@@ -63,6 +63,7 @@ struct QseArgs {
     int F;
     int G;
     int bulk_ok;                // every field pointer 16-byte aligned: stage tiles with bulk copies
+    int interleaved;            // fields[0] holds F-field records: field f of particle i at fields[0][i * F + f]
     FieldParams params[kMaxFields];
     const FieldParams* d_params; // device constants (relative bound) or nullptr
     const uint2* bext;          // each block's extremes from the range pass, or nullptr
@@ -354,6 +355,7 @@ cudaError_t launch_qse_direct(const QseArgs& a, cudaStream_t s);  // the same wi
 cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
 cudaError_t launch_qse_tile(const QseArgs& a, cudaStream_t s);    // shared-memory tile kernel (16-byte aligned fields)
+cudaError_t launch_qse_tile_aos(const QseArgs& a, cudaStream_t s); // the same on interleaved records (16-byte aligned)
 cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
                               unsigned long long* binfo, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s, unsigned grid = 0);  // grid 0: one CTA per tile

@@ -110,10 +110,18 @@ __device__ __forceinline__ void write_raw(const QseArgs& a, uint32_t b, int n_b,
     const uint64_t first = (uint64_t)b * kBlock;
     uint32_t* out = a.temp + (size_t)b * a.slot_words;
     if (t == 0) out[0] = 1u;
+    if (a.interleaved) {  // value k of the block's records is field k % F of particle k / F
+        const float* src = a.fields[0] + first * F;
+        for (int k = t; k < F * n_b; k += kThreads) {
+            const int i = k / F, f = k - i * F;
+            out[1 + f * n_b + i] = __float_as_uint(__ldg(src + k));
+        }
+    } else {
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const float* src = a.fields[f] + first;
-        for (int i = t; i < n_b; i += kThreads) out[1 + f * n_b + i] = __float_as_uint(__ldg(src + i));
+        for (int f = 0; f < F; ++f) {
+            const float* src = a.fields[f] + first;
+            for (int i = t; i < n_b; i += kThreads) out[1 + f * n_b + i] = __float_as_uint(__ldg(src + i));
+        }
     }
     if (a.perm)
         for (int i = t; i < n_b; i += kThreads) a.perm[first + i] = (uint32_t)(first + i);
@@ -161,9 +169,12 @@ __device__ __forceinline__ void qse_block_general(const QseArgs& a, uint8_t* dsm
     for (int r = 0; r < 4; ++r) valid[r] = FULL || (128 * w + 32 * r + lane < n_b);
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-        const float* src = a.fields[f] + first + 128 * w + lane;
+        // separate fields, or interleaved records (stride F)
+        const uint64_t stride = a.interleaved ? (uint64_t)F : 1u;
+        const float* src = a.interleaved ? a.fields[0] + (first + 128 * w + lane) * F + f
+                                         : a.fields[f] + first + 128 * w + lane;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r) : 0.0f;
+        for (int r = 0; r < 4; ++r) x[f][r] = valid[r] ? __ldcs(src + 32 * r * stride) : 0.0f;
     }
     FieldParams prm[F];
 #pragma unroll

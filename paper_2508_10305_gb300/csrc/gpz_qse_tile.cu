@@ -62,6 +62,7 @@ cudaError_t launch_qse_tile_fp(const QseArgs& a, cudaStream_t s) {
 cudaError_t launch_qse_tile(const QseArgs& a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
     if (!a.bulk_ok) return cudaErrorInvalidValue;
+    if (a.interleaved) return launch_qse_tile_aos(a, s);  // gpz_aos.cu
     const bool pre = a.bext != nullptr;
     switch (a.F) {
 #define GPZ_CASE(FF) \

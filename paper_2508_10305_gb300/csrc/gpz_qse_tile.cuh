@@ -81,14 +81,18 @@ __device__ __forceinline__ void field_constants(uint32_t kmin, uint32_t kmax, co
 
 }  // namespace
 
-template <int F, bool FULL, bool PRE, class Idx>
+// AOS: the input is interleaved records (a.interleaved); the tile then holds
+// the block's records as they are in memory, value (f, i) at i * F + f.
+template <int F, bool FULL, bool PRE, class Idx, bool AOS = false>
 __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, TileShared& S, Idx idx) {
     constexpr int P = F < 3 ? F : 3;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t b = idx.b();  // the block within its array
     const uint64_t first = (uint64_t)b * kBlock;
     const int n_b = FULL ? kBlock : (int)(a.n - first);
-    float* tile = reinterpret_cast<float*>(dsm);                             // [F][1024] input
+    float* tile = reinterpret_cast<float*>(dsm);                             // [F][1024] input ([1024][F] if AOS)
+    // position of value (f, i) of the block in the tile
+    auto at = [](int f, int i) { return AOS ? i * F + f : f * kBlock + i; };
     uint32_t* stage = reinterpret_cast<uint32_t*>(dsm);                      // the encoded block, later
     uint16_t* hist = reinterpret_cast<uint16_t*>(dsm + tile_region_bytes(F)); // [8][512] per-warp histograms
     uint16_t* uniq = hist + kWarps * kMaxBins;                               // [512]
@@ -97,18 +101,29 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
 
     // ---- 1. the tile: one bulk copy per field (thread 0); the ragged tail
     // of a last block by plain loads; the block's extremes
-    const uint32_t nvec = (uint32_t)n_b & ~3u;  // values moved in 16-byte units
+    // values moved in 16-byte units: per field, or of the whole run of records
+    const uint32_t nvec = AOS ? ((uint32_t)(F * n_b) & ~3u) : ((uint32_t)n_b & ~3u);
     if (t == 0) {
         mbar_init(&S.bar, 1);
-        mbar_arrive_expect_tx(&S.bar, (uint32_t)F * nvec * 4u);
-        if (nvec)
+        mbar_arrive_expect_tx(&S.bar, (AOS ? 1u : (uint32_t)F) * nvec * 4u);
+        if (nvec) {
+            if (AOS) {
+                bulk_g2s(tile, a.fields[0] + first * F, nvec * 4u, &S.bar);
+            } else {
 #pragma unroll
-            for (int f = 0; f < F; ++f) bulk_g2s(tile + f * kBlock, a.fields[f] + first, nvec * 4u, &S.bar);
+                for (int f = 0; f < F; ++f) bulk_g2s(tile + f * kBlock, a.fields[f] + first, nvec * 4u, &S.bar);
+            }
+        }
         S.flags = 0u;
         S.maxcnt = 0u;
         S.maxdelta = 0u;
     }
-    if (!FULL && t < 4 * F) {
+    if (AOS) {
+        if (!FULL && t < 4) {
+            const int k = (int)nvec + t;
+            if (k < F * n_b) tile[k] = __ldcs(a.fields[0] + first * F + k);
+        }
+    } else if (!FULL && t < 4 * F) {
         const int f = t >> 2, i = (int)nvec + (t & 3);
         if (i < n_b) tile[f * kBlock + i] = __ldcs(a.fields[f] + first + i);
     }
@@ -145,7 +160,7 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 if (valid[r]) {
-                    const float x = tile[f * kBlock + 128 * w + 32 * r + lane];
+                    const float x = tile[at(f, 128 * w + 32 * r + lane)];
                     probe = __fmaf_rn(x, 0.0f, probe);
                     lo = fminf(lo, x);
                     hi = fmaxf(hi, x);
@@ -215,7 +230,7 @@ __device__ __forceinline__ void qse_block_tile(const QseArgs& a, uint8_t* dsm, T
             p.ebchk = c.ebchk;
             float x[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) x[r] = tile[f * kBlock + 128 * w + 32 * r + lane];
+            for (int r = 0; r < 4; ++r) x[r] = tile[at(f, 128 * w + 32 * r + lane)];
             const uint32_t ks = f < P ? kshift[f < P ? f : 0] : 0u;
             if (!verify) {
                 if (!wide)

@@ -117,3 +117,42 @@ def test_aos_without_workspace(gpz, oracle):
     bad[0] ^= 1
     st = gpz.lib.gpz_decompress_aos(bad.data_ptr(), h.value, rec.data_ptr(), F, n, None, 0, None)
     assert st == gpz.ERR_CORRUPT
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_aos_forms_and_general_path(gpz, oracle, offset, flags, mode):
+    """Both routes of gpz_compress_aos give the oracle's stream: 16-byte
+    aligned records read by the tile kernel itself, and (4-byte aligned
+    records, or fused compaction) records transposed first.  The array mixes
+    blocks of every path: encoded, raw (NaN) and general (codes of 2^23 or
+    more, from one block spanning a much wider range)."""
+    import ctypes as C
+    rng = np.random.default_rng(31 + offset + 2 * flags + 4 * mode)
+    F, n = 4, 6 * 1024 + 77
+    x = gen("clustered", F, n, rng)
+    x[:, 1024:2048] = (rng.random((F, 1024)) * 4e4).astype(np.float32)  # wide block
+    x[2, 3000] = np.nan                                                # raw block
+    eb = 1e-3 if mode == 0 else 1e-7
+    buf = torch.zeros(offset + n * F + 4, dtype=torch.float32, device="cuda")
+    buf[offset:offset + n * F] = torch.from_numpy(np.ascontiguousarray(x.T).reshape(-1)).cuda()
+    xa = buf[offset:offset + n * F]
+    params = gpz.make_params(F, eb, mode, 3, flags)
+    cap = gpz.gpz_bound_size(n, F)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    h = C.c_uint64(0)
+    need = gpz.gpz_compress_aos_workspace_size(n, F)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    st = gpz.lib.gpz_compress_aos(xa.data_ptr(), n, C.byref(params), out.data_ptr(), cap, None, C.byref(h),
+                                  perm.data_ptr(), ws.data_ptr(), need, None)
+    assert st == gpz.OK
+    rs, rp = oracle.compress(x, eb, mode, 3)
+    assert h.value == rs.size and np.array_equal(out[:h.value].cpu().numpy(), rs)
+    assert np.array_equal(perm.cpu().numpy().astype(np.uint32), rp)
+    w = rs.view(np.uint32)
+    nb = (n + 1023) // 1024
+    table = w[16 + 2 * F:16 + 2 * F + nb + 1]
+    modes = [int(w[16 + 2 * F + nb + 1 + table[b]]) for b in range(nb)]
+    assert any(m & 1 for m in modes)  # a raw block is among them
