@@ -219,14 +219,17 @@ gpz_status gpz_inspect(const void* h_header, uint64_t len, uint64_t* n, int* n_f
 
 /* Interleaved (array-of-structures) input and output: particle i's fields at
  * d_aos[i*F .. i*F+F-1], the layout of LAS-style point records (4-byte
- * aligned).  A transpose kernel moves the records to structure-of-arrays
- * form in the workspace before compression (and back after decompression),
- * around gpz_compress / gpz_decompress, so the stream is the one gpz_compress
- * writes for the same values, and decompressed particle j (block-sorted
- * order) is d_aos[j*F ..].
+ * aligned).  The stream is the one gpz_compress writes for the same values,
+ * and decompressed particle j (block-sorted order) is d_aos[j*F ..].
+ * Compression reads 16-byte aligned records directly; records only 4-byte
+ * aligned, or calls with GPZ_FLAG_FUSED_COMPACTION, are first transposed into
+ * structure-of-arrays form in the workspace.  Decompression writes the
+ * records directly.
  *   d_ws/ws_size: workspace (256-byte aligned) of at least
- *       gpz_compress_aos_workspace_size(n, F) / gpz_decompress_aos_workspace_size(n, F)
- *       bytes (4*n*F more than the ordinary calls), or NULL to let the library
+ *       gpz_compress_aos_workspace_size(n, F) bytes (4*n*F more than
+ *       gpz_compress needs, for the transposed copy) /
+ *       gpz_decompress_aos_workspace_size(n, F) bytes (what gpz_decompress
+ *       needs, rounded up to 256), or NULL to let the library
  *       allocate and free it (the call then synchronises and returns the
  *       device-side status).  With a workspace, gpz_sync_status(d_ws) reads the
  *       device-side status as for the ordinary calls.

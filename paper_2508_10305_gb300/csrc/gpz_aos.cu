@@ -1,15 +1,20 @@
 // gpz_aos.cu -- interleaved (array-of-structures) input and output: particle
 // i's fields at aos[i*F .. i*F+F-1], the layout of LAS-style point records.
-// A transpose kernel moves the records to structure-of-arrays form in the
-// workspace before compression (and back after decompression), around the
-// ordinary entry points, so the stream is the one gpz_compress writes for the
-// same values.  Both transposes are HBM-bound copies staged through shared
-// memory: one CTA per tile of 1024 particles, contiguous reads of the tile's
-// records and contiguous writes of each field's run (or the reverse).
+// The stream is the one gpz_compress writes for the same values.
+//   - Compression of 16-byte aligned records: the tile kernel's body takes a
+//     block's 1024 F contiguous values as its tile (one bulk copy), and a
+//     relative bound's range pass reads the records; no copy is made.
+//     Records only 4-byte aligned (or with fused compaction) are first
+//     transposed into structure-of-arrays form in the workspace, the range
+//     pass folded into the transpose (one CTA per tile of 1024 particles,
+//     staged through shared memory).
+//   - Decompression: the block decoder stores each value at its place in the
+//     records (field f of sorted position j at aos[j*F + f]).
 #include "gpz.h"
 #include "gpz_host.hpp"
 #include "gpz_internal.cuh"
 #include "gpz_qse_tile.cuh"
+#include "gpz_decode_block.cuh"
 
 using namespace gpz;
 using namespace gpz::host;
@@ -64,64 +69,6 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_to_soa_kernel(const float
         }
         __syncthreads();
     }
-}
-
-// aos[i * F + f] = soa[f * ld + i] for i < n
-template <int F>
-__global__ void __launch_bounds__(kAosThreads) gpz_soa_to_aos_kernel(const float* __restrict__ soa,
-                                                                     float* __restrict__ aos, uint64_t n,
-                                                                     uint64_t ld, bool vec) {
-    __shared__ float tile[(kAosTile + 1) * F];
-    const uint64_t ntiles = (n + kAosTile - 1) / kAosTile;
-    for (uint64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-        const uint64_t first = tl * kAosTile;
-        const int cnt = (int)min((uint64_t)kAosTile, n - first);
-        const int words = cnt * F;
-        float* dst = aos + first * (uint64_t)F;
-        if (vec && cnt == kAosTile) {  // whole tile, 16-byte aligned on both sides
-#pragma unroll
-            for (int f = 0; f < F; ++f) {
-                const int i = 4 * threadIdx.x;
-                const float4 v = __ldcs(reinterpret_cast<const float4*>(soa + (uint64_t)f * ld + first + i));
-                float* row = tile + f * (kAosTile + 1);
-                row[i] = v.x;
-                row[i + 1] = v.y;
-                row[i + 2] = v.z;
-                row[i + 3] = v.w;
-            }
-            __syncthreads();
-            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int k4 = threadIdx.x; k4 < kAosTile * F / 4; k4 += kAosThreads) {
-                float e[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int k = 4 * k4 + c, i = k / F, f = k - i * F;
-                    e[c] = tile[f * (kAosTile + 1) + i];
-                }
-                __stcs(d4 + k4, make_float4(e[0], e[1], e[2], e[3]));
-            }
-        } else {
-#pragma unroll
-            for (int f = 0; f < F; ++f)
-                for (int i = threadIdx.x; i < cnt; i += kAosThreads)
-                    tile[f * (kAosTile + 1) + i] = __ldcs(soa + (uint64_t)f * ld + first + i);
-            __syncthreads();
-            for (int k = threadIdx.x; k < words; k += kAosThreads) {
-                const int i = k / F, f = k - i * F;
-                dst[k] = tile[f * (kAosTile + 1) + i];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ uint32_t aos_order_key(float x) {  // unsigned order = numeric order
-    const uint32_t u = __float_as_uint(x);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float aos_from_order_key(uint32_t k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
 // The interleaved-to-fields transpose that also does the relative bound's
@@ -185,10 +132,10 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float*
             const bool nonfinite = __any_sync(0xffffffffu, probe != probe);
             if (lane == 0) {
                 ra.bext[tl * (uint64_t)F + warp] =
-                    nonfinite ? make_uint2(0u, 0u) : make_uint2(aos_order_key(lo), aos_order_key(hi));
+                    nonfinite ? make_uint2(0u, 0u) : make_uint2(order_key(lo), order_key(hi));
                 if (lo <= hi) {  // some value is not NaN
-                    atomicMin(&s_lo[warp], aos_order_key(lo));
-                    atomicMax(&s_hi[warp], aos_order_key(hi));
+                    atomicMin(&s_lo[warp], order_key(lo));
+                    atomicMax(&s_hi[warp], order_key(hi));
                 }
             }
         }
@@ -214,7 +161,7 @@ __global__ void __launch_bounds__(kAosThreads) gpz_aos_range_kernel(const float*
         const uint32_t kl = s_lo[tid], kh = s_hi[tid];
         const bool any = kl != 0xffffffffu || kh != 0u;
         ra.partials[(size_t)blockIdx.x * F + tid] =
-            any ? make_float2(aos_from_order_key(kl), aos_from_order_key(kh)) : make_float2(INFINITY, -INFINITY);
+            any ? make_float2(from_order_key(kl), from_order_key(kh)) : make_float2(INFINITY, -INFINITY);
     }
     if (tid == 0) {
         __threadfence();
@@ -290,6 +237,32 @@ cudaError_t launch_qse_tile_aos(const QseArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// Decompression into interleaved records: the block decoder stages the
+// block's values in record order in shared memory and writes the block's
+// records with contiguous stores (4-byte aligned records; 16-byte stores
+// when they are 16-byte aligned).
+template <int F>
+__global__ void __launch_bounds__(kDecThreads, 8) gpz_decompress_aos_kernel(DecArgs a) {
+    __shared__ DecSharedRec<F> S;
+    decode_block<F, DecGridBlock, false, true, DecSharedRec<F>>(a, S, DecGridBlock{});
+}
+
+cudaError_t launch_decompress_aos(const DecArgs& a, cudaStream_t s) {
+    if (a.nblocks == 0) return cudaSuccess;
+    switch (a.F) {
+        case 1: gpz_decompress_aos_kernel<1><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 2: gpz_decompress_aos_kernel<2><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 3: gpz_decompress_aos_kernel<3><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 4: gpz_decompress_aos_kernel<4><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 5: gpz_decompress_aos_kernel<5><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 6: gpz_decompress_aos_kernel<6><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 7: gpz_decompress_aos_kernel<7><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        case 8: gpz_decompress_aos_kernel<8><<<a.nblocks, kDecThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int F>
 cudaError_t launch_transpose_range_f(const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
                                      const RangeArgs& ra, cudaStream_t s) {
@@ -314,30 +287,27 @@ cudaError_t launch_transpose_range(const float* src, float* dst, uint64_t n, int
 }
 
 template <int F>
-cudaError_t launch_transpose_f(bool to_soa, const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
+cudaError_t launch_transpose_f(const float* src, float* dst, uint64_t n, uint64_t ld, unsigned grid,
                                cudaStream_t s) {
     // 16-byte accesses when both bases are 16-byte aligned: a whole tile of the
     // interleaved array starts at a multiple of 1024 F floats, a field of the
     // other at a multiple of ld (a multiple of 4) plus a multiple of 1024
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && ld % 4 == 0;
-    if (to_soa)
-        gpz_aos_to_soa_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec);
-    else
-        gpz_soa_to_aos_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec);
+    gpz_aos_to_soa_kernel<F><<<grid, kAosThreads, 0, s>>>(src, dst, n, ld, vec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose(bool to_soa, const float* src, float* dst, uint64_t n, int F, uint64_t ld,
+cudaError_t launch_transpose(const float* src, float* dst, uint64_t n, int F, uint64_t ld,
                              unsigned grid, cudaStream_t s) {
     switch (F) {
-        case 1: return launch_transpose_f<1>(to_soa, src, dst, n, ld, grid, s);
-        case 2: return launch_transpose_f<2>(to_soa, src, dst, n, ld, grid, s);
-        case 3: return launch_transpose_f<3>(to_soa, src, dst, n, ld, grid, s);
-        case 4: return launch_transpose_f<4>(to_soa, src, dst, n, ld, grid, s);
-        case 5: return launch_transpose_f<5>(to_soa, src, dst, n, ld, grid, s);
-        case 6: return launch_transpose_f<6>(to_soa, src, dst, n, ld, grid, s);
-        case 7: return launch_transpose_f<7>(to_soa, src, dst, n, ld, grid, s);
-        case 8: return launch_transpose_f<8>(to_soa, src, dst, n, ld, grid, s);
+        case 1: return launch_transpose_f<1>(src, dst, n, ld, grid, s);
+        case 2: return launch_transpose_f<2>(src, dst, n, ld, grid, s);
+        case 3: return launch_transpose_f<3>(src, dst, n, ld, grid, s);
+        case 4: return launch_transpose_f<4>(src, dst, n, ld, grid, s);
+        case 5: return launch_transpose_f<5>(src, dst, n, ld, grid, s);
+        case 6: return launch_transpose_f<6>(src, dst, n, ld, grid, s);
+        case 7: return launch_transpose_f<7>(src, dst, n, ld, grid, s);
+        case 8: return launch_transpose_f<8>(src, dst, n, ld, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -370,8 +340,9 @@ uint64_t gpz_compress_aos_workspace_size(uint64_t n, int n_fields) {
 }
 
 uint64_t gpz_decompress_aos_workspace_size(uint64_t n, int n_fields) {
+    (void)n;
     if (n_fields < 1 || n_fields > kMaxFields) return 0;
-    return align_up(gpz_decompress_workspace_size(), kAosAlign) + soa_bytes(n, n_fields);
+    return align_up(gpz_decompress_workspace_size(), kAosAlign);
 }
 
 gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p, void* d_out,
@@ -423,7 +394,7 @@ gpz_status gpz_compress_aos(const float* d_aos, uint64_t n, const gpz_params* p,
             range_done = rc == GPZ_OK;
             if (rc == GPZ_OK) rec.mark(direct ? "aos_range" : "aos");
         } else if (!direct) {
-            rc = cuda_status(launch_transpose(true, d_aos, soa, n, F, ld, transpose_grid(n), s));
+            rc = cuda_status(launch_transpose(d_aos, soa, n, F, ld, transpose_grid(n), s));
             if (rc == GPZ_OK) rec.mark("aos");
         }
     }
@@ -454,47 +425,15 @@ gpz_status gpz_decompress_aos(const void* d_in, uint64_t in_size, float* d_aos, 
     if (n_fields < 1 || n_fields > kMaxFields) return GPZ_ERR_INVALID_ARG;
     const int F = n_fields;
     if (n > 0 && (!d_aos || (reinterpret_cast<uintptr_t>(d_aos) & 3u))) return GPZ_ERR_INVALID_ARG;
-    const uint64_t need = gpz_decompress_aos_workspace_size(n, F);
-    cudaStream_t s = (cudaStream_t)stream;
-    bool own = false;
     if (d_ws) {
-        if (ws_size < need) return GPZ_ERR_CAPACITY;
+        if (ws_size < gpz_decompress_aos_workspace_size(n, F)) return GPZ_ERR_CAPACITY;
         if (reinterpret_cast<uintptr_t>(d_ws) % kAosAlign) return GPZ_ERR_INVALID_ARG;
-    } else {
-        if (dev_malloc_async(&d_ws, need, s) != cudaSuccess) return GPZ_ERR_OOM;
-        if (cudaMemsetAsync(d_ws, 0, 4, s) != cudaSuccess) {
-            cudaFreeAsync(d_ws, s);
-            return GPZ_ERR_CUDA;
-        }
-        own = true;
     }
-    uint8_t* ws = static_cast<uint8_t*>(d_ws);
-    const uint64_t dws = align_up(gpz_decompress_workspace_size(), kAosAlign);
-    float* soa = reinterpret_cast<float*>(ws + dws);
-    const uint64_t ld = soa_ld(n);
+    // the values go straight to their records; without a workspace the call
+    // allocates one, synchronises and returns the device-side status
     float* fields[kMaxFields];
-    for (int f = 0; f < F; ++f) fields[f] = soa + (uint64_t)f * ld;
-    // the decompression workspace sits at the start, so gpz_sync_status(d_ws) reads its status
-    gpz_status rc = gpz_decompress(d_in, in_size, fields, F, n, ws, dws, stream);
-    if (rc == GPZ_OK && n > 0) {
-        Recorder rec(s);
-        rec.begin(1);
-        rc = cuda_status(launch_transpose(false, soa, d_aos, n, F, ld, transpose_grid(n), s));
-        if (rc == GPZ_OK) rec.mark("aos");
-    }
-    if (own) {
-        if (rc == GPZ_OK) {
-            uint32_t st = 0;
-            if (cudaMemcpyAsync(&st, d_ws, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                rc = GPZ_ERR_CUDA;
-            else if (st != 0)
-                rc = (gpz_status)st;
-        }
-        cudaFreeAsync(d_ws, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess && rc == GPZ_OK) rc = GPZ_ERR_CUDA;
-    }
-    return rc;
+    for (int f = 0; f < F; ++f) fields[f] = n ? d_aos + f : nullptr;
+    return decompress_impl(d_in, in_size, fields, F, n, d_ws, d_ws ? ws_size : 0, stream, n ? d_aos : nullptr);
 }
 
 }  // extern "C"

@@ -424,6 +424,16 @@ gpz_status gpz_compress(const float* const* d_fields, uint64_t n, const gpz_para
 
 gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fields, int F, uint64_t n,
                           void* d_ws, uint64_t ws_size, void* stream) {
+    return decompress_impl(d_in, in_size, d_fields, F, n, d_ws, ws_size, stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace gpz {
+namespace host {
+
+gpz_status decompress_impl(const void* d_in, uint64_t in_size, float* const* d_fields, int F, uint64_t n,
+                           void* d_ws, uint64_t ws_size, void* stream, float* interleaved) {
     if (!d_in || !aligned(d_in, 4) || F < 1 || F > kMaxFields) return GPZ_ERR_INVALID_ARG;
     if (n > 0) {
         if (!d_fields) return GPZ_ERR_INVALID_ARG;
@@ -452,6 +462,8 @@ gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fi
         da.stream = static_cast<const uint32_t*>(d_in);
         da.total_words = in_size / 4;
         for (int f = 0; f < F; ++f) da.out[f] = n ? d_fields[f] : nullptr;
+        if (interleaved) da.out[0] = interleaved;  // d_fields[f] = interleaved + f
+        da.interleaved = interleaved ? 1 : 0;
         da.n = n;
         da.F = F;
         da.nblocks = (uint32_t)nb;
@@ -468,6 +480,11 @@ gpz_status gpz_decompress(const void* d_in, uint64_t in_size, float* const* d_fi
     }
     return rc;
 }
+
+}  // namespace host
+}  // namespace gpz
+
+extern "C" {
 
 uint64_t gpz_pooled_bytes(void) {
     cudaMemPool_t pool = nullptr;

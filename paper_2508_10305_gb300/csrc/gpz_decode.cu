@@ -36,6 +36,7 @@ cudaError_t launch_dec_f(const DecArgs& a, cudaStream_t s) {
 
 cudaError_t launch_decompress(const DecArgs& a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
+    if (a.interleaved) return launch_decompress_aos(a, s);  // gpz_aos.cu
     switch (a.F) {
         case 1: return launch_dec_f<1>(a, s);
         case 2: return launch_dec_f<2>(a, s);

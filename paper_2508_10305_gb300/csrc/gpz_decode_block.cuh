@@ -87,13 +87,33 @@ __device__ __forceinline__ void store4(float* out, uint64_t first, const uint32_
     }
 }
 
+// Interleaved output: a block's values in record order in shared memory,
+// value (j, f) at word j * F + f + j / 8 (the padding word every eight
+// records spreads a warp's four-apart records over the banks).
+template <int F>
+__device__ __forceinline__ int rec_slot(int j, int f) { return j * F + f + (j >> 3); }
+template <int F>
+constexpr uint32_t rec_words() { return (uint32_t)(kBlock * F + kBlock / 8); }
+
+// store4's values, for records j .. j + 3 of field f, into that staging.
+template <int F>
+__device__ __forceinline__ void store4_rec(float* recs, int j, int f, const uint32_t* qv, uint32_t bits, float s,
+                                           float mn, int left) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float q = bits <= 23u ? small_u2f(qv[e]) : __uint2float_rn(qv[e]);
+        if (e < left) recs[rec_slot<F>(j + e, f)] = __fmaf_rn(q, s, mn);
+    }
+}
+
 // Records wider than 128 bits (rare): every code is read field by field from
 // the stream itself; the block header is re-read here so that the common path
 // passes nothing through memory.
-template <int F, bool OUT64 = false>
+template <int F, bool OUT64 = false, bool AOS = false>
 __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* blk, uint32_t rwords_off,
                                          uint32_t rwords, uint32_t W, uint32_t G, int j0, int n_b, uint64_t first,
-                                         uint32_t key0, uint32_t key1, uint32_t key2, uint32_t key3) {
+                                         uint32_t key0, uint32_t key1, uint32_t key2, uint32_t key3,
+                                         float* recs = nullptr) {
     constexpr int P = F < 3 ? F : 3;
     const uint32_t* R = blk + rwords_off;
     const uint32_t key[4] = {key0, key1, key2, key3};
@@ -133,7 +153,10 @@ __device__ __forceinline__ void decode_wide(const DecArgs& a, const uint32_t* bl
             }
             qv[e] = f < P ? (code | (((key[e] >> kacc[f]) & gm) << wfv[f])) : code;
         }
-        store4<OUT64>(a.out[f], first + j0, qv, bf, sf, mnf, n_b - j0);
+        if (AOS)
+            store4_rec<F>(recs, j0, f, qv, bf, sf, mnf, n_b - j0);
+        else
+            store4<OUT64>(a.out[f], first + j0, qv, bf, sf, mnf, n_b - j0);
     }
 }
 
@@ -156,15 +179,25 @@ struct DecShared : DecCore {
     alignas(16) uint32_t stage[kDecStageWords + kDecStagePad + 4];
 };
 
+// The same for interleaved output: the stage also takes the block's values
+// in record order once its words are consumed.
+constexpr uint32_t cmax(uint32_t x, uint32_t y) { return x > y ? x : y; }
+template <int F>
+struct DecSharedRec : DecCore {
+    uint64_t bar;
+    alignas(16) uint32_t stage[cmax(kDecStageWords + kDecStagePad + 4, 4 + rec_words<F>())];
+};
+
 // Codes of fields F-1 .. 0 of four records, consumed from the least
 // significant end: field F-1 sits at bit 0 of the record and field 0 at the
 // top.  rr[e] holds record e in its low bits (two words when W <= 64, else
 // four); after each field the record is shifted right by the field's width
 // and the key right by the axis' segId bits.  q = segId * 2^o + segOffset for
 // a position axis, the whole code otherwise.
-template <int F, bool WIDE, bool OUT64 = false>
+template <int F, bool WIDE, bool OUT64 = false, bool AOS = false>
 __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4][4], uint32_t (&key)[4],
-                                              const DecCore& L, uint64_t first, int left) {
+                                              const DecCore& L, uint64_t first, int left, float* recs = nullptr,
+                                              int jl = 0) {
     constexpr int P = F < 3 ? F : 3;
 #pragma unroll
     for (int f = F - 1; f >= 0; --f) {
@@ -191,7 +224,10 @@ __device__ __forceinline__ void decode_fields(const DecArgs& a, uint32_t (&rr)[4
             }
         }
         const float2 ms = L.ms[f];
-        store4<OUT64>(a.out[f], first, qv, lay.w, ms.y, ms.x, left);
+        if (AOS)
+            store4_rec<F>(recs, jl, f, qv, lay.w, ms.y, ms.x, left);
+        else
+            store4<OUT64>(a.out[f], first, qv, lay.w, ms.y, ms.x, left);
     }
 }
 
@@ -286,8 +322,36 @@ __device__ __forceinline__ void decode_checks(const DecArgs& a, DecCore& S, uint
 // Decode a block whose constants warp 0 has published in S (after a
 // barrier): stage holds the block's words after its header, blk the block in
 // the stream (read directly for raw blocks and records wider than 128 bits).
-template <int F, bool OUT64 = false>
-__device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const uint32_t* stage,
+// The block's values, staged in record order (rec_slot), to out[0] with
+// contiguous 16-byte stores when the records are 16-byte aligned (every
+// thread, after the values are staged).
+template <int F>
+__device__ __forceinline__ void store_records(const DecArgs& a, const float* recs, uint32_t b, int n_b) {
+    __syncthreads();  // every value is staged
+    const int t = threadIdx.x, total = n_b * F;
+    float* dst = a.out[0] + (uint64_t)b * kBlock * F;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        for (int k = 4 * t; k < total; k += 4 * kDecThreads) {
+            float v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = (k + c) / F;
+                v[c] = k + c < total ? recs[k + c + (j >> 3)] : 0.0f;  // rec_slot(j, (k + c) - j F)
+            }
+            if (k + 4 <= total)
+                __stcs(reinterpret_cast<float4*>(dst + k), make_float4(v[0], v[1], v[2], v[3]));
+            else
+                for (int c = 0; c < 4 && k + c < total; ++c) dst[k + c] = v[c];
+        }
+    } else {
+        for (int k = t; k < total; k += kDecThreads) dst[k] = recs[k + ((k / F) >> 3)];
+    }
+}
+
+// AOS: the values go to interleaved records at out[0]; `stage` must then
+// hold rec_words<F>() words.
+template <int F, bool OUT64 = false, bool AOS = false>
+__device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, uint32_t* stage,
                                             const uint32_t* blk, uint32_t b, int n_b) {
     uint16_t* uniq = S.uniq;
     uint32_t* mask = S.mask;
@@ -301,6 +365,14 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
 
     // ---- 2. raw block
     if (S.raw) {
+        if (AOS) {  // field-major in the stream: gather each record's fields
+            float* dst = a.out[0] + (uint64_t)b * kBlock * F;
+            for (int k = t; k < n_b * F; k += kDecThreads) {
+                const int j = k / F, f = k - j * F;
+                dst[k] = __uint_as_float(__ldg(blk + 1 + f * n_b + j));
+            }
+            return;
+        }
 #pragma unroll
         for (int f = 0; f < F; ++f)
             for (int i = t; i < n_b; i += kDecThreads)
@@ -308,6 +380,8 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
                 const float v = __uint_as_float(__ldg(blk + 1 + f * n_b + i));
                 if (OUT64)
                     reinterpret_cast<double*>(a.out[f])[(uint64_t)b * kBlock + i] = (double)v;
+                else if (AOS)
+                    a.out[0][((uint64_t)b * kBlock + i) * F + f] = v;
                 else
                     a.out[f][(uint64_t)b * kBlock + i] = v;
             }
@@ -391,20 +465,28 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
         prow = __shfl_sync(0xffffffffu, pre, src);
     }
 
-    // ---- 4. positions 4t..4t+3
+    // ---- 4. positions 4t..4t+3 (with interleaved output every thread stays
+    // for the barriers of the staging in record order)
     const int j0 = 4 * t;
-    if (j0 >= n_b) return;
-    uint32_t key[4];
+    if (!AOS && j0 >= n_b) return;
+    const bool act = j0 < n_b;
+    float* recs = reinterpret_cast<float*>(stage);  // AOS, once the stage's words are consumed
+    uint32_t key[4] = {0u, 0u, 0u, 0u};
+    if (act) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const uint32_t bit = (uint32_t)(j0 + e) & 31u;
-        int run = (int)(prow + __popc(mrow & ((2u << bit) - 1u))) - 1;
-        run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
-        key[e] = uniq[run];
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t bit = (uint32_t)(j0 + e) & 31u;
+            int run = (int)(prow + __popc(mrow & ((2u << bit) - 1u))) - 1;
+            run = run < 0 ? 0 : (run >= (int)U ? (int)U - 1 : run);
+            key[e] = uniq[run];
+        }
     }
     if (!fast) {
-        decode_wide<F, OUT64>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)b * kBlock, key[0],
-                       key[1], key[2], key[3]);
+        if (AOS) __syncthreads();  // the staged deltas and counts are consumed
+        if (act)
+            decode_wide<F, OUT64, AOS>(a, blk, hdr + dwords + cwords, rwords, W, S.G, j0, n_b, (uint64_t)b * kBlock,
+                                       key[0], key[1], key[2], key[3], recs);
+        if (AOS) store_records<F>(a, recs, b, n_b);
         return;
     }
     // records j0..j0+3 from the staged words; words past the record array
@@ -413,7 +495,7 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
     uint32_t rr[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const uint32_t p = (uint32_t)(j0 + e) * W;
+        const uint32_t p = (uint32_t)((act ? j0 : 0) + e) * W;
         const uint32_t wi = p >> 5, sh = p & 31u;
         const uint32_t x0 = sR[wi], x1 = sR[wi + 1], x2 = sR[wi + 2];
         rr[e][0] = __funnelshift_r(x0, x1, sh);
@@ -427,15 +509,21 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, const 
         }
     }
     const uint64_t first = (uint64_t)b * kBlock + j0;
-    if (wide)
-        decode_fields<F, true, OUT64>(a, rr, key, S, first, n_b - j0);
-    else
-        decode_fields<F, false, OUT64>(a, rr, key, S, first, n_b - j0);
+    if (AOS) __syncthreads();  // every record is in registers: the stage takes the values
+    if (act) {
+        if (wide)
+            decode_fields<F, true, OUT64, AOS>(a, rr, key, S, first, n_b - j0, recs, j0);
+        else
+            decode_fields<F, false, OUT64, AOS>(a, rr, key, S, first, n_b - j0, recs, j0);
+    }
+    if (AOS) store_records<F>(a, recs, b, n_b);
 }
 
 
-template <int F, class Idx, bool OUT64 = false>
-__device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx idx) {
+// AOS: out[0] receives interleaved records of F fields (Sh then a
+// DecSharedRec<F>).
+template <int F, class Idx, bool OUT64 = false, bool AOS = false, class Sh = DecShared>
+__device__ __forceinline__ void decode_block(const DecArgs& a, Sh& S, Idx idx) {
     uint32_t* stage = S.stage;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t* Sw = a.stream;
@@ -495,7 +583,7 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, DecShared& S, Idx
     if (w == 0) decode_checks<F>(a, S, hv, bw, step, inside, b, off, end, payload_words, n_b);
     __syncthreads();
     if (units && !__syncthreads_and(mbar_wait_bounded(&S.bar, 0, a.status))) return;  // uniform
-    decode_tail<F, OUT64>(a, S, stage + shift, blk, b, n_b);
+    decode_tail<F, OUT64, AOS>(a, S, stage + shift, blk, b, n_b);
 }
 
 }  // namespace gpz

@@ -136,6 +136,11 @@ gpz_status compress_impl(const float* const* d_fields, uint64_t n, const gpz_par
                          void* d_ws, uint64_t ws_size, void* stream, bool range_done,
                          const float* interleaved = nullptr);
 
+// gpz_decompress; with `interleaved` the values go to F-field records there
+// (d_fields[f] = interleaved + f, 4-byte aligned) (gpz_api.cu).
+gpz_status decompress_impl(const void* d_in, uint64_t in_size, float* const* d_fields, int F, uint64_t n,
+                           void* d_ws, uint64_t ws_size, void* stream, float* interleaved);
+
 }  // namespace host
 
 // The block decoder storing fp64 values (gpz_decode.cu): a.out[f] holds the

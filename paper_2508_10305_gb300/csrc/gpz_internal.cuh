@@ -142,6 +142,7 @@ struct DecArgs {
     int F;
     uint32_t nblocks;
     uint32_t* status;
+    int interleaved;            // out[0] receives F-field records: field f of particle i at out[0][i * F + f]
 };
 
 // The constants of one field under a relative bound rel, from the field's
@@ -356,6 +357,7 @@ cudaError_t launch_qse_general(const QseArgs& a, cudaStream_t s);
 cudaError_t launch_qse_pre(const QseArgs& a, cudaStream_t s);     // fast kernel reading a.bext
 cudaError_t launch_qse_tile(const QseArgs& a, cudaStream_t s);    // shared-memory tile kernel (16-byte aligned fields)
 cudaError_t launch_qse_tile_aos(const QseArgs& a, cudaStream_t s); // the same on interleaved records (16-byte aligned)
+cudaError_t launch_decompress_aos(const DecArgs& a, cudaStream_t s); // decompression into interleaved records
 cudaError_t launch_block_info(const uint2* bext, const FieldParams* d_params, uint32_t nblocks, int F,
                               unsigned long long* binfo, cudaStream_t s);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t s, unsigned grid = 0);  // grid 0: one CTA per tile

@@ -156,3 +156,28 @@ def test_aos_forms_and_general_path(gpz, oracle, offset, flags, mode):
     table = w[16 + 2 * F:16 + 2 * F + nb + 1]
     modes = [int(w[16 + 2 * F + nb + 1 + table[b]]) for b in range(nb)]
     assert any(m & 1 for m in modes)  # a raw block is among them
+    rec = torch.empty(n * F + 1, dtype=torch.float32, device="cuda")[offset:offset + n * F]
+    dws = gpz.gpz_decompress_aos_workspace_size(n, F)
+    dw = torch.zeros(dws, dtype=torch.uint8, device="cuda")
+    assert gpz.lib.gpz_decompress_aos(out.data_ptr(), h.value, rec.data_ptr(), F, n, dw.data_ptr(), dws, None) == gpz.OK
+    assert gpz.gpz_sync_status(dw) == gpz.OK
+    ro = oracle.decompress(rs, F, n)
+    assert np.array_equal(rec.cpu().numpy().view(np.uint32), np.ascontiguousarray(ro.T).reshape(-1).view(np.uint32))
+
+
+def test_aos_records_wider_than_128_bits(gpz, oracle):
+    """Eight fields of 19-bit codes: records of 143 bits, decoded field by
+    field from the stream, written straight into the records."""
+    rng = np.random.default_rng(77)
+    F, n = 8, 3 * 1024 + 5
+    x = (rng.random((F, n)) * 1000).astype(np.float32)
+    xa = torch.from_numpy(np.ascontiguousarray(x.T).reshape(-1)).cuda()
+    stream, _ = gpz.compress_aos(xa, F, 1e-3, 0, 3, want_perm=True)
+    rs, _ = oracle.compress(x, 1e-3, 0, 3)
+    assert np.array_equal(stream.cpu().numpy(), rs)
+    w = rs.view(np.uint32)
+    widths = [(int(w[16 + 2 * F + 4 + 1 + 1 + F + k // 4]) >> (8 * (k % 4))) & 0xff for k in range(F)]
+    assert sum(widths) - 9 > 128
+    out = gpz.decompress_aos(stream, F, n)
+    ro = oracle.decompress(rs, F, n)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), np.ascontiguousarray(ro.T).view(np.uint32))
