@@ -416,3 +416,50 @@ def test_unchecked_first_candidates_boundary(gpz, oracle):
         x = np.stack([x1, rng.permutation(x1), rng.permutation(x1)]).astype(np.float32)
         assert_parity(gpz, oracle, x, float(blk[2]), 0, 3)
         cases += 1
+
+
+@pytest.mark.parametrize("F,n", [(1, 4_290_000_000), (6, 715_000_000)])
+def test_largest_supported_arrays_sampled(gpz, oracle, F, n):
+    """The largest arrays the format addresses (blocks + F n just below 2^32
+    words; about 17 GB of input), of nearly incompressible values, so that
+    the stream passes 2^31 words: the offset table is monotone and closes at
+    the payload size, and sampled blocks -- the first, the last, and the ones
+    around the 2^31-word offset -- equal the oracle's words and decode to
+    the oracle's values.  One above the limit is refused."""
+    nb = (n + 1023) // 1024
+    assert nb + F * n < 1 << 32
+    big = gpz.make_params(F, 1e-7)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.rand((F, n), generator=g, device="cuda", dtype=torch.float32)
+    c = gpz.Compressor(n, F, 1e-7, 0, 3)
+    size = c([x[f] for f in range(F)])
+    payload = 16 + 2 * F + nb + 1
+    assert size // 4 > (1 << 31)
+    w_head = c.out[:4 * payload].view(torch.int32).cpu().numpy().view(np.uint32)
+    table = w_head[16 + 2 * F:16 + 2 * F + nb + 1].astype(np.int64)
+    assert table[0] == 0 and np.all(np.diff(table) >= 1) and table[-1] == w_head[9]
+    assert 4 * (payload + table[-1]) == size
+    d = gpz.Decompressor(n, F)
+    out = d(c.out[:size], size)
+    half = int(np.searchsorted(table + payload, 1 << 31))
+    blocks = sorted({0, 1, nb // 2, half - 2, half - 1, min(half, nb - 1), nb - 2, nb - 1})
+    params = [oracle.params_abs(1e-7) for _ in range(F)]
+    steps = np.array([p.s for p in params], np.float32)
+    for b in blocks:
+        lo, hi = b * 1024, min(n, b * 1024 + 1024)
+        xb = x[:, lo:hi].cpu().numpy()
+        ref_words, _ = oracle.encode_block(xb, 3, params)
+        a0, a1 = 4 * (payload + int(table[b])), 4 * (payload + int(table[b + 1]))
+        got = c.out[a0:a1].view(torch.int32).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, ref_words), "block %d differs" % b
+        ref_out = oracle.decode_block(ref_words, F, hi - lo, 3, steps)
+        assert np.array_equal(out[:, lo:hi].cpu().numpy().view(np.uint32), ref_out.view(np.uint32)), b
+    del c, d, out, x
+    torch.cuda.empty_cache()
+    # one particle more than the format addresses
+    n_over = n
+    while (n_over + 1023) // 1024 + F * n_over < 1 << 32:
+        n_over += 1024
+    dummy = torch.empty(16, dtype=torch.uint8, device="cuda")
+    ptrs = [dummy] * F
+    assert gpz.gpz_compress(ptrs, n_over, big, dummy, 1 << 62) == gpz.ERR_UNSUPPORTED
