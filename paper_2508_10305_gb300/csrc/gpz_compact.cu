@@ -217,7 +217,10 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_compact_kernel(Compact
             *a.d_out_size = 4ull * ((unsigned long long)a.payload_start + payload_words);
     }
     uint32_t* payload = a.stream + a.payload_start;
-    for (uint32_t b = blockIdx.x * kCompactWarps + warp; b < a.nblocks; b += nwarps) {
+    // from the last block down: the fused kernel wrote the last blocks' slots
+    // most recently, so the first reads here still find them in L2
+    for (uint32_t bi = blockIdx.x * kCompactWarps + warp; bi < a.nblocks; bi += nwarps) {
+        const uint32_t b = a.nblocks - 1u - bi;
         if (__ldcg(a.sizes + b) & kPlaced) continue;  // written into the stream by the fused kernel
         if (a.unplaced && lane == 0) atomicAdd(a.unplaced, 1u);
         const uint32_t len = __ldcg(a.table + b + 1) - __ldcg(a.table + b);  // clamped by the scan
