@@ -8,6 +8,7 @@
 #include "gpz_batch.cuh"
 #include "gpz_qse_block.cuh"
 #include "gpz_qse_tile.cuh"
+#include "gpz_copy_block.cuh"
 
 namespace gpz {
 
@@ -302,7 +303,10 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * kCompactWarps;
     const uint32_t items = a.total_blocks + a.nchunks;
-    for (uint32_t q = blockIdx.x * kCompactWarps + warp; q < items; q += nwarps) {
+    for (uint32_t qi = blockIdx.x * kCompactWarps + warp; qi < items; qi += nwarps) {
+        // the blocks from the last one down (the last slots written are the
+        // likeliest still in L2), then the chunks' headers
+        const uint32_t q = qi < a.total_blocks ? a.total_blocks - 1u - qi : qi;
         if (q < a.total_blocks) {
             const uint32_t cur = __ldg(a.block_map + q);
             const BatchChunk* ch = a.chunks + cur;
@@ -323,20 +327,7 @@ __global__ void __launch_bounds__(32 * kCompactWarps) gpz_batch_compact_kernel(B
             if (lane == 0) dst[table_start + b] = (uint32_t)rel;
             const uint32_t* src = a.temp + ch->temp_base + (uint64_t)b * batch_slot_words((int)F);
             uint32_t* out = dst + payload_start + rel;
-            const uint32_t L = (uint32_t)len;
-            for (uint32_t k0 = lane; k0 < L; k0 += 256) {  // eight words in flight per lane, the tail too
-                uint32_t v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t k = k0 + 32 * u;
-                    v[u] = k < L ? __ldcs(src + k) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t k = k0 + 32 * u;
-                    if (k < L) out[k] = v[u];
-                }
-            }
+            copy_block(src, out, (uint32_t)len, lane);  // src 16-byte aligned: slots of whole 16-byte words
         } else {
             // the chunk's stream header, constants, closing table entry and size
             const uint32_t c = q - a.total_blocks;
