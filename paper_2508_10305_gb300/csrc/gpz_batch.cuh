@@ -70,6 +70,8 @@ struct BatchMapArgs {
     const BatchChunk* chunks;
     uint32_t nchunks;
     uint32_t* block_map;         // [all blocks]
+    uint4* block_loc;            // decompression: [all blocks] (payload words, table entries b and b + 1, 0)
+                                 // read from the stream when its table lies inside it, else zeros; or nullptr
 };
 
 struct BatchScanArgs {
@@ -97,6 +99,7 @@ struct BatchCompactArgs {
 struct BatchDecompressArgs {
     const BatchChunk* chunks;    // the plan's chunk array
     const uint32_t* block_map;   // [all blocks]
+    const uint4* block_loc;      // [all blocks] as BatchMapArgs
     uint32_t block_first;        // the group's first block
     uint32_t total_blocks;       // the group's blocks
     uint32_t* chunk_status;      // [chunks] zeroed

@@ -148,6 +148,15 @@ __global__ void __launch_bounds__(256) gpz_batch_map_kernel(BatchMapArgs a) {
     const BatchChunk* ch = a.chunks + blockIdx.x;
     const uint32_t base = ch->block_base, nb = ch->nblocks;
     for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) a.block_map[base + j] = blockIdx.x;
+    if (a.block_loc) {  // decompression: each block's place, gathered where it is coalesced
+        const uint64_t table_start = kHeaderWords + 2ull * (uint64_t)ch->F;
+        const bool fits = table_start + nb + 1 <= ch->words;  // the table lies inside the stream
+        const uint32_t pw = fits ? __ldg(ch->src + 9) : 0u;
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
+            a.block_loc[base + j] = fits ? make_uint4(pw, __ldg(ch->src + table_start + j),
+                                                      __ldg(ch->src + table_start + j + 1), 0u)
+                                         : make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
 // One CTA per range item of the group.

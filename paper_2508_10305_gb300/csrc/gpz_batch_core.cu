@@ -217,6 +217,7 @@ gpz_status core_finish(BatchCore& c, const gpz_batch_config* cfg) {
     } else {
         L.zero_bytes = o;
         L.map = take(4 * blocks);
+        L.loc = take(16 * blocks);
     }
     L.total = o;
     // kernels per run: the map when there are blocks; per group the range
@@ -265,6 +266,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
         ma.chunks = dev.chunks;
         ma.nchunks = c.count();
         ma.block_map = map;
+        ma.block_loc = c.kind == 1 ? reinterpret_cast<uint4*>(ws + L.loc) : nullptr;
         if (launch_batch_map(ma, s) != cudaSuccess) return GPZ_ERR_CUDA;
         rec.mark("batch_map");
     }
@@ -274,6 +276,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
             BatchDecompressArgs a{};
             a.chunks = dev.chunks;
             a.block_map = map;
+            a.block_loc = reinterpret_cast<const uint4*>(ws + L.loc);
             a.block_first = g.block_first;
             a.total_blocks = g.blocks;
             a.chunk_status = status;

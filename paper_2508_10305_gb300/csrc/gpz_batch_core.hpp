@@ -29,7 +29,7 @@ struct BatchGroup {
 
 struct BatchLayout {  // byte offsets into the workspace
     uint64_t ctrl, status, rkeys, rdone, states, zero_bytes;
-    uint64_t map, rparams, bext, offsets, sizes, list, out_sizes, temp, total;
+    uint64_t map, loc, rparams, bext, offsets, sizes, list, out_sizes, temp, total;
 };
 
 struct BatchDevice {  // the device copy of the descriptors

@@ -9,14 +9,20 @@
 
 namespace gpz {
 
-// One CTA per block of the group.
+// One CTA per block of the group.  The map kernel has gathered every
+// block's table entries (block_loc), so a CTA needs one round trip for its
+// chunk and its place, and one for its words.
 template <int F>
 __global__ void __launch_bounds__(kDecThreads, 8) gpz_batch_decompress_kernel(BatchDecompressArgs g) {
     __shared__ DecShared S;
     __shared__ DecArgs A;
     __shared__ uint32_t s_b;  // block within its chunk
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const uint32_t gb = g.block_first + blockIdx.x;
+    // the block's place (gathered by the map kernel) in the same round trip
+    // as its chunk: lanes 0, 1, 2 of every warp take the payload size and the
+    // block's two table entries
+    const uint32_t hw_pre = lane < 3 ? __ldg(reinterpret_cast<const uint32_t*>(g.block_loc + gb) + lane) : 0u;
     const uint32_t c = __ldg(g.block_map + gb);
     const BatchChunk* ch = g.chunks + c;
     if (t < F) A.out[t] = ch->out[t];
@@ -30,7 +36,7 @@ __global__ void __launch_bounds__(kDecThreads, 8) gpz_batch_decompress_kernel(Ba
         s_b = gb - ch->block_base;
     }
     __syncthreads();
-    decode_block<F>(A, S, DecSlotBlock{&s_b});
+    decode_block<F, DecSlotBlock, false, false, DecShared, true>(A, S, DecSlotBlock{&s_b}, hw_pre);
 }
 
 cudaError_t launch_batch_decompress(const BatchDecompressArgs& a, int F, cudaStream_t s) {

@@ -521,9 +521,11 @@ __device__ __forceinline__ void decode_tail(const DecArgs& a, DecCore& S, uint32
 
 
 // AOS: out[0] receives interleaved records of F fields (Sh then a
-// DecSharedRec<F>).
-template <int F, class Idx, bool OUT64 = false, bool AOS = false, class Sh = DecShared>
-__device__ __forceinline__ void decode_block(const DecArgs& a, Sh& S, Idx idx) {
+// DecSharedRec<F>).  PREHW: lanes 0, 1, 2 of every warp pass in hw_pre the
+// words round trip 1 would load (the payload size and the block's two table
+// entries), loaded earlier by the caller.
+template <int F, class Idx, bool OUT64 = false, bool AOS = false, class Sh = DecShared, bool PREHW = false>
+__device__ __forceinline__ void decode_block(const DecArgs& a, Sh& S, Idx idx, uint32_t hw_pre = 0u) {
     uint32_t* stage = S.stage;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const uint32_t* Sw = a.stream;
@@ -540,7 +542,10 @@ __device__ __forceinline__ void decode_block(const DecArgs& a, Sh& S, Idx idx) {
     // the block safely needs
     const bool header_fits = payload_start <= a.total_words;
     uint32_t hw = 0;
-    if (header_fits && lane < 3) hw = __ldg(lane == 0 ? Sw + 9 : Sw + table_start + b + (uint32_t)(lane - 1));
+    if (PREHW)
+        hw = header_fits && lane < 3 ? hw_pre : 0u;
+    else if (header_fits && lane < 3)
+        hw = __ldg(lane == 0 ? Sw + 9 : Sw + table_start + b + (uint32_t)(lane - 1));
     const uint32_t payload_words = __shfl_sync(0xffffffffu, hw, 0);
     const uint32_t off = __shfl_sync(0xffffffffu, hw, 1);
     const uint32_t end = __shfl_sync(0xffffffffu, hw, 2);
