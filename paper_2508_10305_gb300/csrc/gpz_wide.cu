@@ -904,12 +904,12 @@ __global__ void __launch_bounds__(kWideThreads) gpz_wide_decode_kernel(WideDecAr
 template <int F>
 cudaError_t launch_wide_qse_f(const WideQseArgs& a, uint32_t nblocks, cudaStream_t s) {
     constexpr uint32_t smem = wide_smem_bytes<F>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gpz_wide_qse_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set at every launch (the attributes belong to the current device), with
+    // the largest shared-memory carveout so that three CTAs fit per SM
+    cudaError_t e = cudaFuncSetAttribute(gpz_wide_qse_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gpz_wide_qse_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     gpz_wide_qse_kernel<F><<<nblocks, kWideThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -917,14 +917,10 @@ cudaError_t launch_wide_qse_f(const WideQseArgs& a, uint32_t nblocks, cudaStream
 template <int F>
 cudaError_t launch_wide_dec_f(const WideDecArgs& a, cudaStream_t s) {
     constexpr uint32_t smem = wide_dec_smem_bytes<F>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gpz_wide_decode_kernel<F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     gpz_wide_decode_kernel<F><<<a.nblocks, kWideThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
