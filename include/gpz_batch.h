@@ -61,12 +61,15 @@ typedef struct {
  *                  slice of a field), a multiple of 1024 in 1024..2^24.  Default 65536.
  *   compact_ctas:  CTAs of the compaction launch, 8 warps each, per SM, 1..32.  Default 16.
  *   general_ctas:  CTAs per SM walking the list of general-path blocks, 1..4.  Default 2.
- *   reserved:      0. */
+ *   qse_form:      the per-block compression code of a group whose chunks all
+ *                  have 16-byte aligned fields: 1 the shared-memory tile body
+ *                  (the default), 2 the register body (other groups always
+ *                  run the register body).  The stream is the same. */
 typedef struct {
     uint32_t range_slice;
     uint32_t compact_ctas;
     uint32_t general_ctas;
-    uint32_t reserved;
+    uint32_t qse_form;
 } gpz_batch_config;
 
 typedef struct gpz_batch gpz_batch; /* opaque plan */

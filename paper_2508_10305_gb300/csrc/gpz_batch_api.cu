@@ -216,9 +216,13 @@ gpz_status gpz_batch_tune(gpz_batch* p, void* d_ws, uint64_t ws_size, uint64_t* 
     if (st != GPZ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const BatchCore& c = p->core;
-    // one parameter at a time, the others at their best so far: the range
-    // slice (relative bounds only), then the compaction grid
+    // one parameter at a time, the others at their best so far: the Q.S.E.
+    // body (when a group can take the tile body), the range slice (relative
+    // bounds only), then the compaction grid
     std::vector<std::vector<gpz_batch_config>> stages;
+    bool any_bulk = false;
+    for (const auto& g : c.groups) any_bulk = any_bulk || g.bulk;
+    if (c.kind == 0 && any_bulk) stages.push_back({{0, 0, 0, 1}, {0, 0, 0, 2}});
     if (c.kind == 0 && c.any_rel) {
         std::vector<gpz_batch_config> v;
         for (uint32_t sl : {16384u, 65536u, 262144u, 1048576u}) v.push_back({sl, 0, 0, 0});
@@ -258,6 +262,7 @@ gpz_status gpz_batch_tune(gpz_batch* p, void* d_ws, uint64_t ws_size, uint64_t* 
             gpz_batch_config cfg = base;
             if (cand.range_slice) cfg.range_slice = cand.range_slice;
             if (cand.compact_ctas) cfg.compact_ctas = cand.compact_ctas;
+            if (cand.qse_form) cfg.qse_form = cand.qse_form;
             float ms = 0.0f;
             if ((st = time_cfg(cfg, &ms)) != GPZ_OK) break;
             if (ms < best_ms) {

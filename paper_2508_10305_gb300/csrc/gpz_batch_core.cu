@@ -51,7 +51,7 @@ gpz_batch_config clamp_cfg(gpz_batch_config cfg) {
     cfg.compact_ctas = std::min<uint32_t>(cfg.compact_ctas, 32);
     if (cfg.general_ctas == 0) cfg.general_ctas = 2;
     cfg.general_ctas = std::min<uint32_t>(cfg.general_ctas, 4);
-    cfg.reserved = 0;
+    if (cfg.qse_form != 2) cfg.qse_form = 1;
     return cfg;
 }
 
@@ -308,7 +308,7 @@ gpz_status core_enqueue(const BatchCore& c, const BatchDevice& dev, uint8_t* ws,
         a.general_list = reinterpret_cast<uint32_t*>(ws + L.list) + g.block_first;
         a.general_count = ctrl + k;
         a.pre = g.pre && a.bext != nullptr;
-        a.tile = g.bulk;
+        a.tile = g.bulk && cfg.qse_form == 1;
         if (g.range_items > 0) {
             if (launch_batch_range(a, s) != cudaSuccess) return GPZ_ERR_CUDA;
             rec.mark("batch_range");

@@ -39,7 +39,7 @@ class gpz_decompress_chunk(C.Structure):
 
 class gpz_batch_config(C.Structure):
     _fields_ = [("range_slice", C.c_uint32), ("compact_ctas", C.c_uint32), ("general_ctas", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("qse_form", C.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -104,12 +104,14 @@ def test_batch_unaligned_fields(gpz, oracle):
     bc.close()
 
 
-@pytest.mark.parametrize("slice_,compact,general", [(1024, 1, 1), (4096, 4, 4), (1 << 20, 32, 2)])
-def test_batch_launch_shapes_and_graph(gpz, oracle, slice_, compact, general):
-    """Any launch shape (and the graph replays of it) gives the same bytes;
-    small slices split every relative-bound field into many range items."""
+@pytest.mark.parametrize("slice_,compact,general,form", [(1024, 1, 1, 1), (4096, 4, 4, 2), (1 << 20, 32, 2, 0),
+                                                         (65536, 16, 2, 2)])
+def test_batch_launch_shapes_and_graph(gpz, oracle, slice_, compact, general, form):
+    """Any launch shape -- either per-block compression body included -- (and
+    the graph replays of it) gives the same bytes; small slices split every
+    relative-bound field into many range items."""
     chunks = make_chunks(14, 20)
-    cfg = gpz.gpz_batch_config(slice_, compact, general, 0)
+    cfg = gpz.gpz_batch_config(slice_, compact, general, form)
     bc, streams, perms, _ = compress_batch(gpz, chunks, use_graph=True, cfg=cfg)
     assert_oracle(oracle, chunks, streams, perms)
     for _ in range(2):  # replays of the captured graph
