@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kDecThreads, 8) gpz_batch_decompress_kernel(Ba
         A.F = F;
         A.nblocks = ch->nblocks;
         A.status = g.chunk_status + c;
+        A.interleaved = 0;
         s_b = gb - ch->block_base;
     }
     __syncthreads();
